@@ -1,0 +1,377 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numpy's FFT
+and dense solver, the literal odd-extension transform of Eqs. 21-25,
+manufactured solutions, closed forms (Eqs. 27-28, TRT Poiseuille, Eq. 16
+viscosity and diffusivity), the paper's Table II, a 1-D boundary-value
+problem solved by scipy, and exact conservation.  All run on the CPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Eq. 19 ---
+def test_dft_is_eq19_numpy_convention():
+    """Eq. 19 is the unnormalised forward DFT: numpy.fft.fft computes it."""
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 5, 12, 122):
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        np.testing.assert_allclose(o.dft(x), np.fft.fft(x), rtol=0, atol=1e-11 * n)
+        np.testing.assert_allclose(o.dft(x, +1), n * np.fft.ifft(x), rtol=0, atol=1e-11 * n)
+
+
+def test_radix2_fft_equals_dft():
+    rng = np.random.default_rng(2)
+    for n in (2, 8, 64, 1024):
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        np.testing.assert_allclose(o.fft(x), np.fft.fft(x), rtol=0, atol=1e-12 * n)
+        np.testing.assert_allclose(o.fft(x, +1), n * np.fft.ifft(x), rtol=0, atol=1e-12 * n)
+
+
+def test_thomas_matches_dense_solve():
+    rng = np.random.default_rng(3)
+    n = 57
+    a = rng.uniform(0.5, 1.0, n)
+    c = rng.uniform(0.5, 1.0, n)
+    b = -(a + c) - rng.uniform(0.0, 1.0, n)
+    a[0] = 0.0
+    c[-1] = 0.0
+    A = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+    d = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    np.testing.assert_allclose(o.thomas(a, b, c, d), np.linalg.solve(A, d), rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------- Eqs. 18, 20-25 ---
+def _kx2(Nx):
+    m = np.fft.fftfreq(Nx, d=1.0 / Nx)  # signed wavenumbers, Eq. 20 reading
+    return (2 * np.pi * m / Nx) ** 2
+
+
+def _odd_extension_solve(src, wall_mode):
+    """Literal Sec. IV.3 solve: odd extension in y (Eqs. 21-22), 2-D FFT,
+    divide by -(kx^2 + 4 sin^2(ky/2)) (Eq. 25), inverse, keep the first half.
+    wall_mode 1: zeros on the extra nodes, NE = 2 Ny + 2 (Eq. 21 as printed).
+    wall_mode 0: antisymmetric about the half node, length 2 Ny."""
+    Ny, Nx = src.shape
+    if wall_mode == 1:
+        ext = np.zeros((2 * Ny + 2, Nx))
+        ext[1:Ny + 1] = src
+        ext[Ny + 2:] = -src[::-1]
+        first = slice(1, Ny + 1)
+    else:
+        ext = np.concatenate([src, -src[::-1]], axis=0)
+        first = slice(0, Ny)
+    NE = ext.shape[0]
+    S = np.fft.fft2(ext)
+    ky = 2 * np.pi * np.fft.fftfreq(NE, d=1.0 / NE) / NE
+    denom = -(_kx2(Nx)[None, :] + 4 * np.sin(ky[:, None] / 2) ** 2)
+    denom[0, 0] = 1.0  # the odd extension has no mean
+    P = S / denom
+    P[0, 0] = 0.0
+    return np.real(np.fft.ifft2(P))[first]
+
+
+@pytest.mark.parametrize("wall_mode", [0, 1])
+@pytest.mark.parametrize("shape", [(24, 16), (33, 20), (10, 122)])
+def test_poisson_equals_odd_extension_fft(wall_mode, shape):
+    """The per-mode tridiagonal solve equals the odd-extension FFT solve of
+    Eqs. 21-25 (homogeneous walls), for either wall placement."""
+    rng = np.random.default_rng(4)
+    src = rng.standard_normal(shape)
+    phi = o.poisson_general(src, wall_mode=wall_mode)
+    ref = _odd_extension_solve(src, wall_mode)
+    assert np.abs(phi - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("wall_mode", [0, 1])
+def test_poisson_wall_potential_lift(wall_mode):
+    """With phi0 on the injector the solution is the homogeneous one plus the
+    discrete-harmonic linear profile between the walls (reading: lifting)."""
+    rng = np.random.default_rng(5)
+    Ny, Nx = 30, 16
+    src = rng.standard_normal((Ny, Nx))
+    phi = o.poisson_general(src, wall_mode=wall_mode, phi_bottom=1.0, phi_top=0.0)
+    j = np.arange(Ny)
+    if wall_mode == 0:  # walls at j = -1/2 and j = Ny - 1/2
+        lin = 1.0 - (j + 0.5) / Ny
+    else:               # walls on nodes j = -1 and j = Ny
+        lin = 1.0 - (j + 1.0) / (Ny + 1)
+    ref = _odd_extension_solve(src, wall_mode) + lin[:, None]
+    assert np.abs(phi - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_poisson_discrete_manufactured_solution():
+    """Pick phi_d with wall values, apply the discrete operator (spectral x,
+    central second difference y with mirror ghosts), recover phi_d."""
+    rng = np.random.default_rng(6)
+    Ny, Nx = 40, 32
+    phi_d = rng.standard_normal((Ny, Nx))
+    lap_x = np.real(np.fft.ifft(-_kx2(Nx)[None, :] * np.fft.fft(phi_d, axis=1), axis=1))
+    ghost_lo = 2 * 1.0 - phi_d[0]
+    ghost_hi = 2 * 0.0 - phi_d[-1]
+    padded = np.vstack([ghost_lo, phi_d, ghost_hi])
+    lap_y = padded[:-2] - 2 * padded[1:-1] + padded[2:]
+    src = lap_x + lap_y
+    phi = o.poisson_general(src, wall_mode=0, phi_bottom=1.0, phi_top=0.0)
+    assert np.abs(phi - phi_d).max() <= 1e-11
+
+
+def test_poisson_continuous_second_order():
+    """phi = 1 - y/H + a sin(2 pi x/Lx) sin(pi y/H): observed order 2 in y
+    (the paper's second-order claim, Sec. IV.4), spectral in x."""
+    errs = []
+    for Ny in (16, 32, 64, 128):
+        Nx = Ny  # refine both directions together
+        H = float(Ny)
+        y = np.arange(Ny) + 0.5
+        x = np.arange(Nx)
+        Lx = float(Nx)
+        a = 0.3
+        X, Y = np.meshgrid(x, y)
+        exact = 1 - Y / H + a * np.sin(2 * np.pi * X / Lx) * np.sin(np.pi * Y / H)
+        src = -a * ((2 * np.pi / Lx) ** 2 + (np.pi / H) ** 2) * np.sin(2 * np.pi * X / Lx) * np.sin(np.pi * Y / H)
+        phi = o.poisson_general(src, wall_mode=0, phi_bottom=1.0, phi_top=0.0)
+        errs.append(np.abs(phi - exact).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 2.0) < 0.1), orders
+
+
+# ---------------------------------------------------------------- Eq. 26 ---
+def test_parameter_mapping_returns_the_groups():
+    p = o.setup(128, 104, 200, 10, 10, 4000, 0.25)
+    assert np.isclose(np.sqrt(p.eps / p.rho_ref) / p.mu_b, 10)                   # M
+    assert np.isclose(p.eps * p.dphi0 / (p.nu * p.rho_ref * p.mu_b), 200)        # T
+    assert np.isclose(p.rho0 * p.H ** 2 / (p.eps * p.dphi0), 10)                 # C
+    assert np.isclose(p.mu_b * p.dphi0 / p.Dc, 4000)                             # Fe
+    # Eq. 16 and Eq. 17
+    assert np.isclose(p.nu, (p.tau_p - 0.5) / 3)
+    assert np.isclose((p.tau_p - 0.5) * (p.tau_m - 0.5), 0.25)
+    assert np.isclose(p.Dc, (p.taug_m - 0.5) / 3)
+    assert np.isclose((p.taug_p - 0.5) * (p.taug_m - 0.5), 1e-6)
+
+
+# -------------------------------------------------- Eqs. 27-28, Table II ---
+def _table2():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table2_hydrostatic.txt"))
+            if l.strip() and not l.startswith("#")]
+    return {float(r[0]): tuple(float(v) for v in r[1:]) for r in rows}
+
+
+def test_hydrostatic_constants_table2_weak_injection():
+    """Table II, C = 0.1: rho_a = 0.218, y_a = 4.8 follow from rho_c(0) = C
+    and the unit voltage (eps = H = dphi0 = 1).  (The C = 10 column is not
+    consistent with its own Eq. 27 at y = 0 and is not used as a pin.)"""
+    rho_a, y_a, _, _ = _table2()[0.1]
+    ra, ya = o.hydrostatic(0.1, 1.0, 1.0, 1.0)
+    assert round(ra, 3) == rho_a
+    assert round(ya, 1) == y_a
+    # closed-form checks of Eqs. 27-28: Gauss law and constant current
+    y = np.linspace(0, 1, 101)
+    rc = ra / np.sqrt(y + ya)
+    E = 2 * ra * np.sqrt(y + ya)
+    np.testing.assert_allclose(np.gradient(E, y, edge_order=2), rc, rtol=1e-4)
+    np.testing.assert_allclose(rc * E, 2 * ra * ra, rtol=1e-14)
+    np.testing.assert_allclose(4 * ra / 3 * ((1 + ya) ** 1.5 - ya ** 1.5), 1.0, rtol=1e-12)
+
+
+def _hydro_run(C, Ny, nsteps, u_ion, Fe=4000.0):
+    p = o.setup(4, Ny, 200, C, 10, Fe, 0.25, u_ion=u_ion)
+    cx, cy, w, opp = o.lattice()
+    f = np.ones((9, Ny, 4)) * w[:, None, None]
+    g = np.ones((9, Ny, 4)) * w[:, None, None] * 0.5 * p.rho0  # far from the answer
+    s = o.state_from(p, f, g)
+    o.step(s, nsteps)
+    return p, o.fields(s)
+
+
+def _eL2(num, ref):
+    return np.sqrt(((num - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+@pytest.mark.parametrize("C", [0.1, 10.0])
+def test_hydrostatic_profile_vs_eqs27_28(C):
+    """Run the coupled step from a uniform half-strength charge to steady
+    state at the paper's NY = 100 and Fe = 4000; compare with Eqs. 27-28.
+    Bound: twice the e_L2 of Table II.  At C = 10 the injection layer (width
+    ~H/Fe = 0.025 cells) is not resolved, so only E is held to that bound;
+    rho_c is pinned by the resolved convergence test below."""
+    p, F = _hydro_run(C, 100, 30000, 0.01)
+    y = np.arange(100) + 0.5
+    rc_a = p.rho_a / np.sqrt(y + p.y_a)
+    E_a = 2 * p.rho_a / p.eps * np.sqrt(y + p.y_a)
+    e_E = _eL2(F["Ey"][:, 0], E_a)
+    e_rc = _eL2(F["rho_c"][:, 0], rc_a)
+    _, _, eE_tab, erc_tab = _table2()[C]
+    assert e_E <= 2 * eE_tab, e_E
+    if C < 1:
+        assert e_rc <= 2 * erc_tab, e_rc
+    else:
+        assert e_rc <= 0.1, e_rc
+
+
+def test_hydrostatic_converges_to_diffusive_bvp():
+    """Steady 1-D drift-diffusion-Poisson problem (J = rho_c mu_b E - Dc
+    rho_c', E' = rho_c/eps, rho_c(0) = rho0, phi(0) = 1, phi(H) = 0,
+    rho_c'(H) = 0) solved by scipy; the oracle's steady state converges to it
+    at second order when the injection layer is resolved (Fe = 25)."""
+    from scipy.integrate import solve_bvp
+    errs = []
+    for Ny in (32, 64, 128):
+        p, F = _hydro_run(10.0, Ny, int(8 * Ny / 0.02), 0.02, Fe=25.0)
+
+        def fun(yv, Y, par):
+            rc, E, _ = Y
+            return np.vstack([(p.mu_b * rc * E - par[0]) / p.Dc, rc / p.eps, -E])
+
+        def bc(Ya, Yb, par):
+            return np.array([Ya[0] - p.rho0, Ya[2] - 1.0, Yb[2], p.mu_b * Yb[0] * Yb[1] - par[0]])
+
+        ys = np.linspace(0, p.H, 2001)
+        guess = np.vstack([p.rho_a / np.sqrt(ys + p.y_a), 2 * p.rho_a / p.eps * np.sqrt(ys + p.y_a), 1 - ys / p.H])
+        sol = solve_bvp(fun, bc, ys, guess, p=[2 * p.mu_b * p.rho_a ** 2 / p.eps], tol=1e-10, max_nodes=200000)
+        assert sol.success
+        rc_b, E_b, _ = sol.sol(np.arange(Ny) + 0.5)
+        errs.append((np.abs(F["rho_c"][:, 0] - rc_b).max() / np.abs(rc_b).max(),
+                     np.abs(F["Ey"][:, 0] - E_b).max() / np.abs(E_b).max()))
+    e = np.array(errs)
+    orders = np.log2(e[:-1] / e[1:])
+    assert np.all(orders[-1] > 1.6), orders
+    assert e[-1].max() < 0.01
+
+
+# --------------------------------------------------- TRT fluid, Eqs. 8-17 ---
+@pytest.mark.parametrize("T,Lam", [(200, 3 / 16), (200, 0.25), (100, 1 / 12)])
+def test_poiseuille_trt_halfway_bounce_back_exact(T, Lam):
+    """Body-force-driven channel: the steady TRT solution with halfway
+    bounce-back is u(y) = F/(2 nu) [y (H - y) + (16 Lambda - 3)/12] exactly
+    (exact wall placement at Lambda = 3/16)."""
+    Ny = 16
+    Fx = 1e-6
+    p = o.setup(4, Ny, T, 10, 10, 4000, Lam, u_ion=0.01, no_force=1, ext_F=(Fx, 0))
+    cx, cy, w, opp = o.lattice()
+    f = np.ones((9, Ny, 4)) * w[:, None, None]
+    g = np.ones((9, Ny, 4)) * w[:, None, None] * p.rho0
+    s = o.state_from(p, f, g)
+    o.step(s, 60000)
+    F = o.fields(s)
+    y = np.arange(Ny) + 0.5
+    ua = Fx / (2 * p.nu) * (y * (Ny - y) + (16 * Lam - 3) / 12)
+    assert np.abs(F["ux"][:, 0] / ua - 1).max() < 1e-9
+    assert np.abs(F["uy"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("Lam", [0.25, 1 / 12])
+def test_shear_wave_viscosity_eq16_second_order(Lam):
+    """A decaying shear wave in a periodic box decays at nu k^2 with
+    nu = cs2 (tau+ - 1/2) (Eq. 16): relative error falls at order 2."""
+    cx, cy, w, opp = o.lattice()
+    rel = []
+    for L in (16, 32, 64):
+        nu = 0.1
+        p = o.setup(4, L, 100 * 0.01 * L / nu, 10, 10, 4000, Lam, u_ion=0.01,
+                    periodic_y=1, no_poisson=1, no_force=1)
+        y = np.arange(L) + 0.5
+        k = 2 * np.pi / L
+        ux = 1e-6 * np.sin(k * y)
+        f = w[:, None, None] * (1 + 3 * cx[:, None, None] * ux[None, :, None]) * np.ones((9, L, 4))
+        g = w[:, None, None] * np.ones((9, L, 4)) * p.rho0
+        s = o.state_from(p, f, g)
+        n = int(0.3 / (p.nu * k * k))
+        o.step(s, 100)
+        a0 = (o.fields(s)["ux"][:, 0] * np.sin(k * y)).sum()
+        o.step(s, n)
+        a1 = (o.fields(s)["ux"][:, 0] * np.sin(k * y)).sum()
+        rel.append(-np.log(a1 / a0) / (n * k * k) / p.nu - 1)
+    rel = np.abs(np.array(rel))
+    orders = np.log2(rel[:-1] / rel[1:])
+    assert np.all(np.abs(orders - 2) < 0.1), orders
+    assert rel[-1] < 1e-3
+
+
+# ------------------------------------------------- TRT charge, Eqs. 9-17 ---
+@pytest.mark.parametrize("drift", [0.0, 0.02])
+def test_charge_diffusivity_and_drift(drift):
+    """A sinusoidal charge wave in a periodic box with a uniform drift
+    decays at Dc k^2 (Dc = mu_b dphi0 / Fe, Eq. 26) and moves at mu_b E."""
+    cx, cy, w, opp = o.lattice()
+    rel = []
+    for L in (16, 32, 64):
+        Dc, u_ion = 0.01, 0.01
+        p = o.setup(L, 4, 200, 10, 10, u_ion * 4 / Dc, 0.25, u_ion=u_ion, periodic_y=1,
+                    no_poisson=1, no_force=1, ext_E=(drift / (u_ion * 4), 0))
+        x = np.arange(L)
+        k = 2 * np.pi / L
+        rc = 1.0 + 1e-3 * np.cos(k * x)
+        v = p.mu_b * p.ext_E[0]
+        f = w[:, None, None] * np.ones((9, 4, L))
+        g = w[:, None, None] * rc[None, None, :] * (1 + 3 * cx[:, None, None] * v) * np.ones((9, 4, L))
+        s = o.state_from(p, f, g)
+        o.step(s, 50)
+        c0 = (o.fields(s)["rho_c"][0] - 1.0) @ np.exp(-1j * k * x)
+        n_phase = max(1, int(1.0 / (k * max(drift, 1e-30)))) if drift else 0
+        if drift:
+            o.step(s, n_phase)
+            cp = (o.fields(s)["rho_c"][0] - 1.0) @ np.exp(-1j * k * x)
+            v_m = -np.angle(cp / c0) / (n_phase * k)
+            assert abs(v_m / drift - 1) < 5e-3 * (16 / L) ** 2 + 1e-4
+            c0 = cp
+        n = int(0.3 / (p.Dc * k * k))
+        o.step(s, n)
+        c1 = (o.fields(s)["rho_c"][0] - 1.0) @ np.exp(-1j * k * x)
+        rel.append(-np.log(abs(c1 / c0)) / (n * k * k) / p.Dc - 1)
+    rel = np.abs(np.array(rel))
+    assert rel[-1] < 1e-3, rel
+    assert np.log2(rel[-2] / rel[-1]) > 1.8, rel
+
+
+# ------------------------------------------------------------ conservation ---
+def test_conservation_mass_and_charge_identity():
+    """f: bounce-back and periodic streaming conserve mass exactly.  g: the
+    total charge changes by exactly injected minus collected charge."""
+    p = o.setup(32, 24, 200, 10, 10, 4000, 0.25, u_ion=0.01)
+    s = o.init_state(p, [1e-3], [0.7])
+    d = o.step(s, 300, diag=True)
+    mass, charge, q_in, q_out = d[:, 0], d[:, 1], d[:, 2], d[:, 3]
+    assert np.abs(mass / mass[0] - 1).max() < 1e-13
+    resid = charge[1:] - charge[:-1] - (q_in[:-1] - q_out[:-1])
+    assert np.abs(resid).max() < 1e-13 * charge[0]
+    drift = charge[-1] - charge[0] - (q_in[:-1] - q_out[:-1]).sum()
+    assert abs(drift) < 1e-11 * charge[0]
+
+
+# -------------------------------------------------------------- Eq. 29 ---
+def test_perturbation_divergence_free_and_wall_compatible():
+    p = o.setup(64, 52, 200, 10, 10, 4000, 0.25)
+    amp, ph = [1e-3, 5e-4], [0.4, 1.3]
+    # vanishes on both walls (y = 0 and y = H)
+    for x in (0.0, 7.3, 31.0):
+        for yw in (0.0, p.H):
+            ux, uy = o.perturbation(p, amp, ph, x, yw)
+            assert abs(ux) < 1e-18 and abs(uy) < 1e-18
+    # analytic divergence by centred differences, O(h^2) -> 0
+    for h in (1e-2, 1e-3):
+        x, y = 11.7, 20.3
+        dux = (o.perturbation(p, amp, ph, x + h, y)[0] - o.perturbation(p, amp, ph, x - h, y)[0]) / (2 * h)
+        duy = (o.perturbation(p, amp, ph, x, y + h)[1] - o.perturbation(p, amp, ph, x, y - h)[1]) / (2 * h)
+        scale = abs(o.perturbation(p, amp, ph, x, y + h)[1] - o.perturbation(p, amp, ph, x, y - h)[1]) / (2 * h)
+        assert abs(dux + duy) <= 1e-3 * h * scale / 1e-2 + 1e-20
+
+
+def test_initial_state_moments():
+    """Initial state: Eq. 5-7 moments give the hydrostatic charge (Eq. 27)
+    and the Eq. 29 velocity, and phi solves the Poisson equation."""
+    p = o.setup(32, 26, 200, 10, 10, 4000, 0.25)
+    s = o.init_state(p, [1e-3], [0.5])
+    F = o.fields(s)
+    y = np.arange(p.Ny) + 0.5
+    np.testing.assert_allclose(F["rho_c"], (p.rho_a / np.sqrt(y + p.y_a))[:, None] * np.ones(p.Nx), rtol=1e-13)
+    ux = np.array([[o.perturbation(p, [1e-3], [0.5], x, yy)[0] for x in range(p.Nx)] for yy in y])
+    # Eq. 7 with the discrete field: the stored momentum was built with the
+    # analytic force, so u differs from Eq. 29 only by (F_disc - F_h)/(2 rho)
+    assert np.abs(F["ux"] - ux).max() < 1e-3 * p.u_ion * 1e-2 + 1e-12
