@@ -1,0 +1,184 @@
+/*
+ * ehd.h -- C ABI of the GB300 library for the coupled time step of the
+ * segregated electroconvection solver of Guan & Novosselov (arXiv:1812.05711):
+ * a two-relaxation-time (TRT) D2Q9 lattice Boltzmann scheme for the fluid (f)
+ * and the space charge (g), coupled every step to a fast Poisson solver for
+ * the electric potential (FFT along the periodic x, tridiagonal in y).
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only.  Host pointers are marked "host"; the library owns
+ *     all device memory of a run.  No entry point takes ownership of a
+ *     caller's buffer.
+ *   - Every call returns an ehd_status; on failure ehd_last_error() gives a
+ *     thread-local message.  No C++ exception crosses this boundary.
+ *   - Work is enqueued on the run's CUDA stream and is asynchronous unless the
+ *     comment says the call synchronises.  A run is not thread-safe; distinct
+ *     runs may be driven from distinct host threads.
+ *   - Grids: Nx columns (periodic in x, a power of two, 16..4096), Ny node rows
+ *     (2..8192).  Node row j sits at y = j + 1/2; the injector electrode
+ *     (phi = 1, rho_c = rho0) is the wall y = 0 and the collector (phi = 0) the
+ *     wall y = H = Ny.  Host field arrays are FP64, row-major, x fastest:
+ *     [Ny][Nx] per field, [9][Ny][Nx] per population set.
+ *   - D2Q9 numbering: c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1)
+ *     c5=(1,1) c6=(-1,1) c7=(-1,-1) c8=(1,-1).
+ */
+#ifndef EHD_H
+#define EHD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ehd_run ehd_run; /* opaque, owned by the library */
+
+typedef enum {
+  EHD_OK = 0,
+  EHD_EINVAL = -1,     /* invalid argument (size, parameter, mask, pointer) */
+  EHD_ENOMEM = -2,     /* device or host allocation failed */
+  EHD_ECUDA = -3,      /* a CUDA runtime call failed */
+  EHD_EDIVERGED = -4,  /* a non-finite density or charge was produced */
+  EHD_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  EHD_EBUSY = -6       /* reserved: capacity exhausted */
+} ehd_status;
+
+/* Storage type of the populations.  F64 storage with F64 compute is the plain
+ * double-precision path of the paper (Sec. IV.4); every other combination
+ * computes in FP32 on populations stored shifted by their rest equilibrium
+ * (f_i - w_i and g_i - w_i rho_c,hydrostatic(y)). */
+typedef enum {
+  EHD_STORE_F64 = 0,
+  EHD_STORE_F32 = 1,
+  EHD_STORE_BF16 = 2,
+  EHD_STORE_F16 = 3
+} ehd_storage;
+
+typedef enum { EHD_COMPUTE_F64 = 0, EHD_COMPUTE_F32 = 1 } ehd_compute;
+
+#define EHD_MAX_PERT_MODES 16
+#define EHD_NDIAG 8
+
+/* Field mask bits for ehd_fields (output order follows the bit order). */
+#define EHD_FIELD_RHO (1u << 0)   /* fluid density, Eq. 5 */
+#define EHD_FIELD_UX (1u << 1)    /* velocity with half force, Eq. 7 */
+#define EHD_FIELD_UY (1u << 2)
+#define EHD_FIELD_RHOC (1u << 3)  /* charge density, Eq. 6 */
+#define EHD_FIELD_PHI (1u << 4)   /* electric potential, Eq. 4 */
+#define EHD_FIELD_EX (1u << 5)    /* E = -grad phi (central differences) */
+#define EHD_FIELD_EY (1u << 6)
+#define EHD_FIELD_ALL 0x7Fu
+
+typedef struct {
+  int storage;      /* ehd_storage; default EHD_STORE_F32 */
+  int compute;      /* ehd_compute; default EHD_COMPUTE_F32.  F64 compute needs
+                       F64 storage. */
+  double lambda_g;  /* charge magic parameter Lambda_g of Eq. 17; default 1e-6
+                       (Sec. IV.2) */
+  double u_ion;     /* lattice ion drift speed mu_b dphi0 / H; sets the lattice
+                       scale of the Eq. 26 groups.  Default 2e-3. */
+  int wall_mode;    /* 0: halfway walls, Poisson mirror ghost
+                       phi_{-1} = 2 phi_w - phi_0 (default).
+                       1: Dirichlet on the extra nodes j = -1, Ny (the odd
+                       extension of Eq. 21 as printed). */
+  int n_modes;      /* initial perturbation: number of x-modes of Eq. 29
+                       (mode k has k+1 periods across the channel); 0 = none */
+  double pert_amp[EHD_MAX_PERT_MODES];   /* amplitude in units of u_ion */
+  double pert_phase[EHD_MAX_PERT_MODES]; /* x-phase, radians */
+  void* stream;     /* cudaStream_t to run on; NULL = a stream the library
+                       creates and owns */
+} ehd_options;
+
+/* Fill *opt with the defaults above. */
+void ehd_default_options(ehd_options* opt);
+
+/* Create a run: map the non-dimensional groups of Eq. 26 (T, C, M, Fe) to
+ * lattice units (rho = 1, dphi0 = 1, H = Ny, mu_b = u_ion H), set the TRT rates
+ * of Eqs. 16-17 (nu from tau+, D_c from tau_g-, Lambda for the fluid as given,
+ * Lambda_g from opt), allocate the device state and initialise it to the
+ * hydrostatic profile of Eqs. 27-28 plus the Eq. 29 perturbation, then solve
+ * phi (ehd_poisson).  Synchronises the stream.
+ * Errors: EHD_EINVAL for a bad size or non-positive T, C, M, Fe, Lambda,
+ * lambda_g, u_ion, tau+ > 50 or an unsupported storage/compute pair;
+ * EHD_ENOMEM, EHD_ECUDA.  *out is NULL on failure. */
+ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe,
+                      double Lambda, const ehd_options* opt, ehd_run** out);
+
+/* Solve the Poisson equation (Eq. 4; discretised as Eqs. 18-20 with the
+ * Dirichlet walls of Table I) for phi from the current charge density
+ * rho_c = sum_i g_i (Eq. 6): real FFT of every row, one tridiagonal solve per
+ * wavenumber (the mean mode in FP64), inverse FFT.  Asynchronous. */
+ehd_status ehd_poisson(ehd_run* run);
+
+/* Advance n >= 0 coupled steps (Eqs. 5-17, Table I).  Per step: E = -grad phi;
+ * fused fluid TRT collision with the electric force -rho_c grad phi (Eq. 7
+ * half-force velocity, Eqs. 8, 10, 12, 13, 15); charge TRT collision with the
+ * drift u + mu_b E (Eqs. 9, 11, 14); streaming with halfway bounce-back of f
+ * on both walls, anti-bounce-back injection of rho0 and zero-gradient outflow
+ * of g; then the Poisson solve for the new charge.  Asynchronous; a
+ * non-finite density or charge is reported by the next synchronising call. */
+ehd_status ehd_step(ehd_run* run, long n);
+
+/* Instrumented stepping: advance n steps with one launch per kernel (no
+ * graph) and CUDA events on the run's stream around each phase; the paper has
+ * no counterpart (measurement only).  host ms_out[EHD_NPROFILE]: summed
+ * milliseconds of [0] the fused collide-stream kernel, [1] the wall-flux
+ * reduction, [2] the Poisson solve (forward FFT, tridiagonal modes, inverse
+ * FFT), [3] whole steps, [4] = n.  Synchronises. */
+#define EHD_NPROFILE 5
+ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
+
+/* Copy fields of the current state to host_out (host, FP64, caller-owned,
+ * popcount(mask) * Ny * Nx doubles, one [Ny][Nx] plane per set bit in bit
+ * order).  Synchronises the stream.  EHD_EINVAL for mask == 0, a mask bit
+ * above EHD_FIELD_ALL or host_out == NULL. */
+ehd_status ehd_fields(ehd_run* run, unsigned mask, double* host_out);
+
+/* Diagnostics of the current state, FP64 reductions on the device
+ * (host out[EHD_NDIAG]): total mass sum rho, total charge sum rho_c, charge
+ * injected and collected since creation (sums of the wall fluxes of every
+ * step), kinetic energy sum rho |u|^2 / 2, max |u_y|, max |u|, step count.
+ * Synchronises; EHD_EDIVERGED if the state holds a non-finite value. */
+ehd_status ehd_diagnostics(ehd_run* run, double* out);
+
+/* Replace the populations (host, FP64 [9][Ny][Nx] each) and re-solve phi.
+ * For shifted storages the values are shifted and rounded on the device.
+ * Synchronises.  The step counter and flux sums are kept. */
+ehd_status ehd_load(ehd_run* run, const double* f_host, const double* g_host);
+
+/* Copy the populations out (host, FP64 [9][Ny][Nx] each, unshifted).
+ * Either pointer may be NULL.  Synchronises. */
+ehd_status ehd_save(ehd_run* run, double* f_host, double* g_host);
+
+/* Lattice parameters of a run (host out[16]): Nx, Ny, H, mu_b, eps, nu, rho0,
+ * D_c, tau+, tau-, tau_g+, tau_g-, rho_a, y_a, storage, compute. */
+ehd_status ehd_params(ehd_run* run, double* out);
+
+/* Device bytes a run of this size and storage holds (for admission). */
+ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes);
+
+/* Block the host until the run's stream is idle; EHD_EDIVERGED if a step has
+ * produced a non-finite density or charge. */
+ehd_status ehd_sync(ehd_run* run);
+
+/* The cudaStream_t the run enqueues on. */
+void* ehd_stream(ehd_run* run);
+
+/* Free the run and its device memory (synchronises first).  NULL is a no-op. */
+void ehd_destroy(ehd_run* run);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* ehd_last_error(void);
+
+/* Route the library's device allocations through caller functions (e.g. a
+ * framework's caching allocator).  alloc returns a device pointer aligned to
+ * 256 bytes or NULL; free releases it.  Pass NULLs to return to cudaMalloc.
+ * Affects runs created afterwards. */
+ehd_status ehd_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
+                             void (*free_fn)(void* ptr, void* ctx), void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EHD_H */

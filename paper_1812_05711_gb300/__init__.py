@@ -1,0 +1,317 @@
+"""GB300 electroconvection step (arXiv:1812.05711) -- Python binding.
+
+Thin ctypes marshalling over the C ABI in ``include/ehd.h`` (library
+``libehd.so``, CUDA kernels for sm_103a).  Every step of the method runs in
+those kernels; this module only converts arguments.  There is no CPU path:
+if the library cannot be loaded, importing the functions raises.
+
+PyTorch is used for device memory only: :func:`use_torch_allocator` routes the
+library's device allocations through the PyTorch caching allocator, and
+:class:`Run` gives each run its own ``torch.cuda.Stream``.
+
+The module-level functions carry the C names (``ehd_create``,
+``ehd_poisson``, ``ehd_step``, ``ehd_fields``, ...) and the same argument
+order; numpy arrays are passed for host buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+FIELDS = ("rho", "ux", "uy", "rho_c", "phi", "Ex", "Ey")
+FIELD_BITS = {name: 1 << i for i, name in enumerate(FIELDS)}
+FIELD_ALL = 0x7F
+NDIAG = 8
+DIAG_NAMES = ("mass", "charge", "q_in", "q_out", "kinetic", "max_uy", "max_u", "step")
+PARAM_NAMES = ("Nx", "Ny", "H", "mu_b", "eps", "nu", "rho0", "Dc", "tau_p", "tau_m",
+               "taug_p", "taug_m", "rho_a", "y_a", "storage", "compute")
+STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+COMPUTE = {"f64": 0, "f32": 1}
+MAX_PERT_MODES = 16
+
+STATUS = {0: "EHD_OK", -1: "EHD_EINVAL", -2: "EHD_ENOMEM", -3: "EHD_ECUDA",
+          -4: "EHD_EDIVERGED", -5: "EHD_ETIMEOUT", -6: "EHD_EBUSY"}
+
+
+class EhdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("storage", ctypes.c_int), ("compute", ctypes.c_int),
+        ("lambda_g", ctypes.c_double), ("u_ion", ctypes.c_double),
+        ("wall_mode", ctypes.c_int), ("n_modes", ctypes.c_int),
+        ("pert_amp", ctypes.c_double * MAX_PERT_MODES),
+        ("pert_phase", ctypes.c_double * MAX_PERT_MODES),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libehd.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if _build.stale():
+            _build.build()
+        L = ctypes.CDLL(_build.LIB)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        L.ehd_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.ehd_default_options.restype = None
+        L.ehd_create.argtypes = [ip, ip] + [ctypes.c_double] * 5 + [ctypes.POINTER(Options), ctypes.POINTER(vp)]
+        L.ehd_poisson.argtypes = [vp]
+        L.ehd_step.argtypes = [vp, ctypes.c_long]
+        L.ehd_step_profile.argtypes = [vp, ctypes.c_long, dp]
+        L.ehd_fields.argtypes = [vp, ctypes.c_uint, dp]
+        L.ehd_diagnostics.argtypes = [vp, dp]
+        L.ehd_load.argtypes = [vp, dp, dp]
+        L.ehd_save.argtypes = [vp, dp, dp]
+        L.ehd_params.argtypes = [vp, dp]
+        L.ehd_footprint.argtypes = [ip, ip, ip, ctypes.POINTER(ctypes.c_size_t)]
+        L.ehd_sync.argtypes = [vp]
+        L.ehd_stream.argtypes = [vp]
+        L.ehd_stream.restype = vp
+        L.ehd_destroy.argtypes = [vp]
+        L.ehd_destroy.restype = None
+        L.ehd_last_error.restype = ctypes.c_char_p
+        L.ehd_set_allocator.argtypes = [vp, vp, vp]
+        for name in ("ehd_create", "ehd_poisson", "ehd_step", "ehd_step_profile", "ehd_fields", "ehd_diagnostics",
+                     "ehd_load", "ehd_save", "ehd_params", "ehd_footprint", "ehd_sync",
+                     "ehd_set_allocator"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise EhdError(status, lib().ehd_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous float64 array")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------- allocator (torch)
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_torch_blocks: dict = {}
+_torch_lock = threading.Lock()
+_callbacks = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _callbacks
+    if not enable:
+        _check(lib().ehd_set_allocator(None, None, None))
+        _callbacks = None
+        return
+    import torch
+
+    def _alloc(nbytes, ctx):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=torch.cuda.current_device())
+        except RuntimeError:
+            return None
+        with _torch_lock:
+            _torch_blocks[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(ptr, ctx):
+        with _torch_lock:
+            _torch_blocks.pop(int(ptr), None)
+
+    _callbacks = (_ALLOC_T(_alloc), _FREE_T(_free))
+    _check(lib().ehd_set_allocator(ctypes.cast(_callbacks[0], ctypes.c_void_p),
+                                   ctypes.cast(_callbacks[1], ctypes.c_void_p), None))
+
+
+# ------------------------------------------------------- C-named functions
+def ehd_default_options() -> Options:
+    o = Options()
+    lib().ehd_default_options(ctypes.byref(o))
+    return o
+
+
+def ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt: Options | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ehd_create(int(Nx), int(Ny), float(T), float(C), float(M), float(Fe), float(Lambda),
+                            ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def ehd_poisson(h):
+    _check(lib().ehd_poisson(h))
+
+
+def ehd_step(h, n: int):
+    _check(lib().ehd_step(h, int(n)))
+
+
+def ehd_step_profile(h, n: int) -> dict:
+    out = np.zeros(5)
+    _check(lib().ehd_step_profile(h, int(n), _dp(out)))
+    return {"collide_stream_ms": out[0], "flux_ms": out[1], "poisson_ms": out[2], "step_ms": out[3],
+            "steps": int(out[4])}
+
+
+def ehd_fields(h, mask: int, out: np.ndarray):
+    _check(lib().ehd_fields(h, int(mask), _dp(out)))
+
+
+def ehd_diagnostics(h, out: np.ndarray):
+    _check(lib().ehd_diagnostics(h, _dp(out)))
+
+
+def ehd_load(h, f: np.ndarray, g: np.ndarray):
+    _check(lib().ehd_load(h, _dp(f), _dp(g)))
+
+
+def ehd_save(h, f: np.ndarray | None, g: np.ndarray | None):
+    _check(lib().ehd_save(h, _dp(f) if f is not None else None, _dp(g) if g is not None else None))
+
+
+def ehd_params(h, out: np.ndarray):
+    _check(lib().ehd_params(h, _dp(out)))
+
+
+def ehd_footprint(Nx, Ny, storage) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().ehd_footprint(int(Nx), int(Ny), int(storage), ctypes.byref(b)))
+    return b.value
+
+
+def ehd_sync(h):
+    _check(lib().ehd_sync(h))
+
+
+def ehd_stream(h) -> int:
+    return lib().ehd_stream(h) or 0
+
+
+def ehd_destroy(h):
+    lib().ehd_destroy(h)
+
+
+def ehd_last_error() -> str:
+    return lib().ehd_last_error().decode()
+
+
+# ------------------------------------------------------------ convenience
+def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
+                 amp=(), phase=(), stream=None) -> Options:
+    o = ehd_default_options()
+    o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    if compute is None:
+        compute = "f64" if o.storage == 0 and storage == "f64" else "f32"
+    o.compute = COMPUTE[compute] if isinstance(compute, str) else int(compute)
+    o.lambda_g = float(lambda_g)
+    o.u_ion = float(u_ion)
+    o.wall_mode = int(wall_mode)
+    amp, phase = list(amp), list(phase)
+    if len(amp) != len(phase) or len(amp) > MAX_PERT_MODES:
+        raise ValueError("amp and phase must have the same length <= 16")
+    o.n_modes = len(amp)
+    for k, (a, p) in enumerate(zip(amp, phase)):
+        o.pert_amp[k] = float(a)
+        o.pert_phase[k] = float(p)
+    o.stream = stream
+    return o
+
+
+class Run:
+    """One channel run on the current CUDA device.
+
+    ``storage``: "f64" (with FP64 compute: the plain double-precision path),
+    "f32", "bf16", "f16" (FP32 compute on shifted populations); ``compute``
+    may force "f32" on FP64 storage.  ``amp``/``phase``: Eq. 29 x-modes.
+    """
+
+    def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
+                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True):
+        self.Nx, self.Ny = int(Nx), int(Ny)
+        self._stream_obj = None
+        if stream is None and torch_stream:
+            import torch
+            self._stream_obj = torch.cuda.Stream()
+            stream = self._stream_obj.cuda_stream
+        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream)
+        self.handle = ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt)
+
+    # lifecycle
+    def close(self):
+        if getattr(self, "handle", None):
+            ehd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # operations
+    def step(self, n: int = 1):
+        ehd_step(self.handle, n)
+        return self
+
+    def poisson(self):
+        ehd_poisson(self.handle)
+
+    def sync(self):
+        ehd_sync(self.handle)
+
+    def fields(self, names=FIELDS) -> dict:
+        names = list(names)
+        mask = 0
+        for n in names:
+            mask |= FIELD_BITS[n]
+        order = [n for n in FIELDS if FIELD_BITS[n] & mask]
+        out = np.empty((len(order), self.Ny, self.Nx))
+        ehd_fields(self.handle, mask, out)
+        return {n: out[i] for i, n in enumerate(order)}
+
+    def diagnostics(self) -> dict:
+        out = np.empty(NDIAG)
+        ehd_diagnostics(self.handle, out)
+        return dict(zip(DIAG_NAMES, out.tolist()))
+
+    def params(self) -> dict:
+        out = np.empty(16)
+        ehd_params(self.handle, out)
+        return dict(zip(PARAM_NAMES, out.tolist()))
+
+    def load(self, f: np.ndarray, g: np.ndarray):
+        ehd_load(self.handle, np.ascontiguousarray(f, dtype=np.float64), np.ascontiguousarray(g, dtype=np.float64))
+
+    def save(self):
+        f = np.empty((9, self.Ny, self.Nx))
+        g = np.empty((9, self.Ny, self.Nx))
+        ehd_save(self.handle, f, g)
+        return f, g

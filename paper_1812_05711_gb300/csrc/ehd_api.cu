@@ -1,0 +1,718 @@
+// ehd_api.cu -- host side of the C ABI declared in include/ehd.h: parameter
+// mapping (Eq. 26 groups -> lattice units, TRT rates of Eqs. 16-17), the
+// hydrostatic constants (Eqs. 27-28), device memory of a run, the per-run CUDA
+// graph of the time step, and the field / diagnostics / checkpoint calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ehd.h"
+#include "ehd_dev.cuh"
+
+using namespace ehd;
+
+namespace {
+
+thread_local std::string g_err;
+
+ehd_status fail(ehd_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define EHD_CK(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(EHD_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Allocator {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int kGraphSteps = 16;  // steps per captured graph (even: buffer parity)
+
+size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
+
+}  // namespace
+
+struct ehd_run {
+  int device = 0;
+  int Nx = 0, Ny = 0, P = 0, Mh = 0, log2Nx = 0;
+  int storage = 1, compute = 1, wall_mode = 0;
+  bool real_f64 = false;
+  size_t rsz = 4;  // sizeof compute real
+  // lattice parameters
+  double T = 0, C = 0, M = 0, Fe = 0, Lambda = 0, Lambda_g = 0, u_ion = 0;
+  double H = 0, mub = 0, eps = 0, nu = 0, rho0 = 0, Dc = 0, phi0 = 1.0;
+  double tau_p = 0, tau_m = 0, taug_p = 0, taug_m = 0, rho_a = 0, y_a = 0, sf = 0;
+  // device state
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Allocator al;
+  std::vector<void*> blocks;
+  void* f[2] = {nullptr, nullptr};
+  void* g[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* dphi = nullptr;
+  double* phibar = nullptr;
+  void* Ebar = nullptr;
+  void* spec = nullptr;
+  double* spec0 = nullptr;
+  void* rfac = nullptr;
+  double* rfac0 = nullptr;
+  void* tw = nullptr;
+  float* rch = nullptr;
+  double* flux_part = nullptr;
+  int nxb = 0;
+  double* small = nullptr;  // [0] q_in sum, [1] q_out sum, [2..7] last reduction
+  int* err = nullptr;
+  double* red_part = nullptr;
+  int rows = 1;
+  long step = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+void* run_alloc(ehd_run* r, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (r->al.alloc) {
+    p = r->al.alloc(bytes, r->al.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) r->blocks.push_back(p);
+  return p;
+}
+
+void run_free(ehd_run* r, void* p) {
+  if (!p) return;
+  auto it = std::find(r->blocks.begin(), r->blocks.end(), p);
+  if (it != r->blocks.end()) r->blocks.erase(it);
+  if (r->al.free_fn)
+    r->al.free_fn(p, r->al.ctx);
+  else
+    cudaFree(p);
+}
+
+// (H + ya)^{3/2} - ya^{3/2} = H ((H + ya) + sqrt((H + ya) ya) + ya) / (sqrt(H + ya) + sqrt(ya))
+double hydro_gap(double ya, double H) {
+  const double a = H + ya, sa = std::sqrt(a), sb = std::sqrt(ya);
+  return H * (a + sa * sb + ya) / (sa + sb);
+}
+
+// Eqs. 27-28 with rho_c(0) = rho0 and int_0^H E dy = dphi0:
+// rho_a = rho0 sqrt(ya), (4 rho_a / 3 eps) gap(ya) = dphi0.  Bisection on ln ya.
+bool hydrostatic(double rho0, double eps, double H, double dphi0, double* rho_a, double* ya) {
+  auto resid = [&](double lya) {
+    const double y = std::exp(lya);
+    return 4.0 * rho0 * std::sqrt(y) / (3.0 * eps) * hydro_gap(y, H) - dphi0;
+  };
+  double lo = std::log(H) - 46.0, hi = std::log(H) + 46.0;  // ~1e-20 H .. 1e20 H
+  if (!(resid(lo) < 0.0) || !(resid(hi) > 0.0)) return false;
+  for (int it = 0; it < 300; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (resid(mid) > 0.0)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  *ya = std::exp(0.5 * (lo + hi));
+  *rho_a = rho0 * std::sqrt(*ya);
+  return true;
+}
+
+ehd_status upload(ehd_run* r, void* dst, const void* src, size_t bytes) {
+  EHD_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, r->stream));
+  EHD_CK(cudaStreamSynchronize(r->stream));  // src is a temporary host vector
+  return EHD_OK;
+}
+
+StepArgs step_args(const ehd_run* r, int cur) {
+  StepArgs a{};
+  a.Nx = r->Nx;
+  a.Ny = r->Ny;
+  a.P = r->P;
+  a.plane = (long long)r->Ny * r->P;
+  a.fin = r->f[cur];
+  a.gin = r->g[cur];
+  a.fout = r->f[1 - cur];
+  a.gout = r->g[1 - cur];
+  a.dphi = r->dphi;
+  a.Ebar = r->Ebar;
+  a.rch = r->rch;
+  a.flux_part = r->flux_part;
+  a.err = r->err;
+  a.wp = 1.0 / r->tau_p;
+  a.wm = 1.0 / r->tau_m;
+  a.gwp = 1.0 / r->taug_p;
+  a.gwm = 1.0 / r->taug_m;
+  a.mub = r->mub;
+  a.rho0 = r->rho0;
+  a.sf = r->sf;
+  a.wall_mode = r->wall_mode;
+  return a;
+}
+
+PoissonArgs poisson_args(const ehd_run* r, int cur) {
+  PoissonArgs a{};
+  a.Nx = r->Nx;
+  a.Ny = r->Ny;
+  a.P = r->P;
+  a.Mh = r->Mh;
+  a.log2Nx = r->log2Nx;
+  a.gin = r->g[cur];
+  a.plane = (long long)r->Ny * r->P;
+  a.rch = r->rch;
+  a.inv_eps = 1.0 / r->eps;
+  a.spec = r->spec;
+  a.spec0 = r->spec0;
+  a.rfac = r->rfac;
+  a.rfac0 = r->rfac0;
+  a.tw = r->tw;
+  a.dphi = r->dphi;
+  a.phibar = r->phibar;
+  a.Ebar = r->Ebar;
+  a.phi0 = r->phi0;
+  a.wall_mode = r->wall_mode;
+  return a;
+}
+
+FieldArgs field_args(const ehd_run* r) {
+  FieldArgs a{};
+  a.Nx = r->Nx;
+  a.Ny = r->Ny;
+  a.P = r->P;
+  a.plane = (long long)r->Ny * r->P;
+  a.f = r->f[r->cur];
+  a.g = r->g[r->cur];
+  a.dphi = r->dphi;
+  a.phibar = r->phibar;
+  a.Ebar = r->Ebar;
+  a.rch = r->rch;
+  a.sf = r->sf;
+  a.mub = r->mub;
+  a.wall_mode = r->wall_mode;
+  return a;
+}
+
+// One coupled step from buffer `cur`: K4 collide+stream, K5 wall fluxes, then
+// the Poisson solve (K1-K3) of the new charge.
+cudaError_t enqueue_step(ehd_run* r, int cur) {
+  const StepArgs sa = step_args(r, cur);
+  cudaError_t e = launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_flux_reduce(r->flux_part, r->nxb, r->small, r->stream);
+  if (e != cudaSuccess) return e;
+  return launch_poisson(poisson_args(r, 1 - cur), r->storage, r->real_f64, r->stream);
+}
+
+ehd_status build_graph(ehd_run* r, int cur) {
+  cudaGraph_t g = nullptr;
+  EHD_CK(cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  int c = cur;
+  for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+    e = enqueue_step(r, c);
+    c = 1 - c;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(r->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(EHD_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&r->graph[cur], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(EHD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return EHD_OK;
+}
+
+ehd_status check_err(ehd_run* r) {
+  int h = 0;
+  EHD_CK(cudaMemcpyAsync(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
+  EHD_CK(cudaStreamSynchronize(r->stream));
+  if (h) return fail(EHD_EDIVERGED, "non-finite density or charge in the state");
+  return EHD_OK;
+}
+
+ehd_status destroy_quiet(ehd_run* r) {
+  if (!r) return EHD_OK;
+  DeviceGuard dg(r->device);
+  if (r->stream) cudaStreamSynchronize(r->stream);
+  for (int k = 0; k < 2; ++k)
+    if (r->graph[k]) cudaGraphExecDestroy(r->graph[k]);
+  std::vector<void*> bl = r->blocks;
+  for (void* p : bl) run_free(r, p);
+  if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
+  delete r;
+  return EHD_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void ehd_default_options(ehd_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->storage = EHD_STORE_F32;
+  o->compute = EHD_COMPUTE_F32;
+  o->lambda_g = 1e-6;
+  o->u_ion = 2e-3;
+  o->wall_mode = 0;
+  o->n_modes = 0;
+  o->stream = nullptr;
+}
+
+const char* ehd_last_error(void) { return g_err.c_str(); }
+
+ehd_status ehd_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(EHD_EINVAL, "alloc and free must both be set or both NULL");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free_fn = free_fn;
+  g_alloc.ctx = ctx;
+  return EHD_OK;
+}
+
+ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
+  if (!bytes) return fail(EHD_EINVAL, "bytes is NULL");
+  if (Nx < 16 || Nx > 4096 || (Nx & (Nx - 1)) || Ny < 2 || Ny > 8192 || storage < 0 || storage > 3)
+    return fail(EHD_EINVAL, "unsupported size or storage");
+  const size_t P = (size_t)((Nx + 31) / 32 * 32), Mh = (size_t)Nx / 2 + 1;
+  const size_t rs = (storage == 0) ? 8 : 4;  // worst case for the compute type
+  size_t b = 4 * 9 * (size_t)Ny * P * storage_bytes(storage);  // f, g ping-pong
+  b += (size_t)Ny * P * rs;                                    // dphi
+  b += (size_t)Ny * Mh * 2 * rs + Mh * (size_t)Ny * rs;        // spectrum, pivots
+  b += (size_t)Ny * (8 + 8 + 8 + rs + 4) + (size_t)Nx * rs;    // per-row, twiddles
+  b += 64 * 1024;                                              // small buffers
+  *bytes = b;
+  return EHD_OK;
+}
+
+ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, double Lambda, const ehd_options* opt,
+                      ehd_run** out) {
+  if (!out) return fail(EHD_EINVAL, "out is NULL");
+  *out = nullptr;
+  ehd_options o;
+  ehd_default_options(&o);
+  if (opt) o = *opt;
+  if (Nx < 16 || Nx > 4096 || (Nx & (Nx - 1)))
+    return fail(EHD_EINVAL, "Nx must be a power of two in [16, 4096] (got %d)", Nx);
+  if (Ny < 2 || Ny > 8192) return fail(EHD_EINVAL, "Ny must be in [2, 8192] (got %d)", Ny);
+  if (!(T > 0) || !(C > 0) || !(M > 0) || !(Fe > 0) || !(Lambda > 0))
+    return fail(EHD_EINVAL, "T, C, M, Fe and Lambda must be positive");
+  if (!(o.lambda_g > 0) || !(o.u_ion > 0)) return fail(EHD_EINVAL, "lambda_g and u_ion must be positive");
+  if (o.storage < 0 || o.storage > 3) return fail(EHD_EINVAL, "storage must be 0..3");
+  if (o.compute != EHD_COMPUTE_F64 && o.compute != EHD_COMPUTE_F32) return fail(EHD_EINVAL, "compute must be 0 or 1");
+  if (o.compute == EHD_COMPUTE_F64 && o.storage != EHD_STORE_F64)
+    return fail(EHD_EINVAL, "FP64 compute needs FP64 storage");
+  if (o.wall_mode != 0 && o.wall_mode != 1) return fail(EHD_EINVAL, "wall_mode must be 0 or 1");
+  if (o.n_modes < 0 || o.n_modes > EHD_MAX_PERT_MODES) return fail(EHD_EINVAL, "n_modes out of range");
+
+  ehd_run* r = new ehd_run();
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    r->al = g_alloc;
+  }
+  if (cudaGetDevice(&r->device) != cudaSuccess) {
+    delete r;
+    return fail(EHD_ECUDA, "no CUDA device");
+  }
+  r->Nx = Nx;
+  r->Ny = Ny;
+  r->P = (Nx + 31) / 32 * 32;
+  r->Mh = Nx / 2 + 1;
+  while ((1 << r->log2Nx) < Nx) ++r->log2Nx;
+  r->storage = o.storage;
+  r->compute = o.compute;
+  r->real_f64 = (o.compute == EHD_COMPUTE_F64);
+  r->rsz = r->real_f64 ? 8 : 4;
+  r->wall_mode = o.wall_mode;
+  r->T = T, r->C = C, r->M = M, r->Fe = Fe, r->Lambda = Lambda, r->Lambda_g = o.lambda_g, r->u_ion = o.u_ion;
+  // Eq. 26 with rho = 1, dphi0 = 1, H = Ny and mu_b = u_ion H / dphi0
+  r->H = (double)Ny;
+  r->mub = o.u_ion * r->H;
+  r->eps = M * M * r->mub * r->mub;        // M = sqrt(eps / rho) / mu_b
+  r->nu = r->eps / (T * r->mub);           // T = eps dphi0 / (mu mu_b)
+  r->rho0 = C * r->eps / (r->H * r->H);    // C = rho0 H^2 / (eps dphi0)
+  r->Dc = r->mub / Fe;                     // Fe = mu_b dphi0 / Dc
+  // Eqs. 16-17 (dt = 1, cs2 = 1/3): nu from the symmetric fluid rate; the
+  // charge flux relaxes with the antisymmetric rate, which carries Dc
+  r->tau_p = 3.0 * r->nu + 0.5;
+  r->tau_m = 0.5 + Lambda / (r->tau_p - 0.5);
+  r->taug_m = 3.0 * r->Dc + 0.5;
+  r->taug_p = 0.5 + o.lambda_g / (r->taug_m - 0.5);
+  if (r->tau_p > 50.0 || r->tau_m > 50.0 || r->taug_p > 50.0 || r->taug_m > 50.0) {
+    ehd_status st0 = fail(EHD_EINVAL, "relaxation time above 50 (tau+ %.3g, tau- %.3g, tau_g+ %.3g, tau_g- %.3g)",
+                          r->tau_p, r->tau_m, r->taug_p, r->taug_m);
+    delete r;
+    return st0;
+  }
+  if (!hydrostatic(r->rho0, r->eps, r->H, 1.0, &r->rho_a, &r->y_a)) {
+    delete r;
+    return fail(EHD_EINVAL, "hydrostatic profile has no solution");
+  }
+  const bool shifted = !r->real_f64;
+  r->sf = shifted ? 1.0 : 0.0;
+
+  DeviceGuard dg(r->device);
+  ehd_status st = EHD_OK;
+  if (o.stream) {
+    r->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete r;
+      return fail(EHD_ECUDA, "stream creation failed");
+    }
+    r->own_stream = true;
+  }
+  if (poisson_set_attributes() != cudaSuccess) {
+    destroy_quiet(r);
+    return fail(EHD_ECUDA, "cudaFuncSetAttribute failed");
+  }
+
+  const size_t plane = (size_t)Ny * r->P;
+  const size_t sb = storage_bytes(r->storage);
+  for (int k = 0; k < 2; ++k) {
+    r->f[k] = run_alloc(r, 9 * plane * sb);
+    r->g[k] = run_alloc(r, 9 * plane * sb);
+  }
+  r->dphi = run_alloc(r, plane * r->rsz);
+  r->phibar = static_cast<double*>(run_alloc(r, Ny * sizeof(double)));
+  r->Ebar = run_alloc(r, Ny * r->rsz);
+  r->spec = run_alloc(r, (size_t)Ny * r->Mh * 2 * r->rsz);
+  r->spec0 = static_cast<double*>(run_alloc(r, Ny * sizeof(double)));
+  r->rfac = run_alloc(r, (size_t)r->Mh * Ny * r->rsz);
+  r->rfac0 = static_cast<double*>(run_alloc(r, Ny * sizeof(double)));
+  r->tw = run_alloc(r, (size_t)(Nx / 2) * 2 * r->rsz);
+  if (shifted) r->rch = static_cast<float*>(run_alloc(r, Ny * sizeof(float)));
+  r->nxb = step_flux_blocks(Nx);
+  r->flux_part = static_cast<double*>(run_alloc(r, 2 * r->nxb * sizeof(double)));
+  r->small = static_cast<double*>(run_alloc(r, 16 * sizeof(double) + 64));
+  r->red_part = static_cast<double*>(run_alloc(r, (size_t)reduce_state_blocks() * 6 * sizeof(double)));
+  bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->phibar && r->Ebar && r->spec && r->spec0 &&
+            r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part;
+  if (!ok) {
+    destroy_quiet(r);
+    return fail(EHD_ENOMEM, "device allocation failed");
+  }
+  r->err = reinterpret_cast<int*>(r->small + 16);
+  // rows per CTA of K4: keep >= ~4 CTAs per SM
+  {
+    const long long xb = (Nx + 127) / 128;
+    long long rows = xb * Ny / 608;
+    r->rows = (int)std::max(1LL, std::min(8LL, rows));
+  }
+
+  // ---- host tables: twiddles, Thomas pivots, shifts, initial profiles
+  {
+    std::vector<double> twd((size_t)Nx);  // interleaved re, im for k < Nx/2
+    for (int k = 0; k < Nx / 2; ++k) {
+      const double ang = 2.0 * kPi * (double)k / (double)Nx;
+      twd[2 * k] = std::cos(ang);
+      twd[2 * k + 1] = -std::sin(ang);
+    }
+    std::vector<double> piv((size_t)r->Mh * Ny);
+    for (int m = 0; m < r->Mh; ++m) {
+      const double kx = 2.0 * kPi * (double)m / (double)Nx;
+      const double diag = -(2.0 + kx * kx);
+      const double corner = diag - (r->wall_mode == 0 ? 1.0 : 0.0);
+      double prev = 0.0;
+      for (int j = 0; j < Ny; ++j) {
+        const double b = (j == 0 || j == Ny - 1) ? corner : diag;
+        const double beta = (j == 0) ? b : b - prev;
+        prev = 1.0 / beta;
+        piv[(size_t)m * Ny + j] = prev;
+      }
+    }
+    if (r->real_f64) {
+      st = upload(r, r->tw, twd.data(), twd.size() * 8);
+      if (st == EHD_OK) st = upload(r, r->rfac, piv.data(), piv.size() * 8);
+    } else {
+      std::vector<float> twf(twd.begin(), twd.end()), pivf(piv.begin(), piv.end());
+      st = upload(r, r->tw, twf.data(), twf.size() * 4);
+      if (st == EHD_OK) st = upload(r, r->rfac, pivf.data(), pivf.size() * 4);
+    }
+    if (st == EHD_OK) st = upload(r, r->rfac0, piv.data(), Ny * sizeof(double));
+    if (st != EHD_OK) {
+      destroy_quiet(r);
+      return st;
+    }
+  }
+  {
+    const int nx = Nx;
+    std::vector<double> rho_h(Ny), rc_h(Ny), Eh(Ny), sY(Ny), cY(Ny), Sx(nx, 0.0), Cy(nx, 0.0);
+    std::vector<float> rchf(Ny);
+    const double Fh = 2.0 * r->rho_a * r->rho_a / r->eps;  // rho_c E of Eqs. 27-28, constant
+    for (int j = 0; j < Ny; ++j) {
+      const double y = j + 0.5, s = std::sqrt(y + r->y_a);
+      rc_h[j] = r->rho_a / s;                       // Eq. 27
+      Eh[j] = 2.0 * r->rho_a / r->eps * s;           // Eq. 28
+      rho_h[j] = 1.0 + 3.0 * Fh * (y - 0.5 * r->H);  // cs2 d rho / dy = F
+      sY[j] = std::sin(2.0 * kPi * y / r->H);
+      cY[j] = std::cos(2.0 * kPi * y / r->H);
+      rchf[j] = (float)rc_h[j];
+    }
+    // Eq. 29 with x, y scaled by H (Lx = Nx / H, Ly = 1), amplitude a u_ion
+    const double Lx = (double)Nx / r->H;
+    for (int k = 0; k < o.n_modes; ++k) {
+      const double mk = k + 1.0, a = o.pert_amp[k] * o.u_ion;
+      for (int x = 0; x < nx; ++x) {
+        const double arg = 2.0 * kPi * mk * (double)x / (double)Nx + o.pert_phase[k];
+        Sx[x] += a * (Lx / mk) * std::sin(arg);
+        Cy[x] += a * std::cos(arg);
+      }
+    }
+    std::vector<double> pack;
+    pack.insert(pack.end(), rho_h.begin(), rho_h.end());
+    pack.insert(pack.end(), rc_h.begin(), rc_h.end());
+    pack.insert(pack.end(), Eh.begin(), Eh.end());
+    pack.insert(pack.end(), sY.begin(), sY.end());
+    pack.insert(pack.end(), cY.begin(), cY.end());
+    pack.insert(pack.end(), Sx.begin(), Sx.end());
+    pack.insert(pack.end(), Cy.begin(), Cy.end());
+    double* dpack = static_cast<double*>(run_alloc(r, pack.size() * sizeof(double)));
+    if (!dpack) {
+      destroy_quiet(r);
+      return fail(EHD_ENOMEM, "device allocation failed");
+    }
+    st = upload(r, dpack, pack.data(), pack.size() * sizeof(double));
+    if (st == EHD_OK && shifted) st = upload(r, r->rch, rchf.data(), Ny * sizeof(float));
+    if (st == EHD_OK) {
+      const double* p = dpack;
+      cudaError_t e = cudaMemsetAsync(r->small, 0, 16 * sizeof(double) + 64, r->stream);
+      if (e == cudaSuccess)
+        e = launch_init(p, p + Ny, p + 2 * Ny, p + 3 * Ny, p + 4 * Ny, p + 5 * Ny, p + 5 * Ny + nx, Fh, r->mub,
+                        r->f[0], r->g[0], r->storage, Nx, Ny, r->P, r->rch, r->sf, r->stream);
+      if (e == cudaSuccess) e = launch_poisson(poisson_args(r, 0), r->storage, r->real_f64, r->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+      if (e != cudaSuccess) st = fail(EHD_ECUDA, "initialisation: %s", cudaGetErrorString(e));
+    }
+    run_free(r, dpack);
+    if (st != EHD_OK) {
+      destroy_quiet(r);
+      return st;
+    }
+  }
+  *out = r;
+  return EHD_OK;
+}
+
+ehd_status ehd_poisson(ehd_run* r) {
+  if (!r) return fail(EHD_EINVAL, "run is NULL");
+  DeviceGuard dg(r->device);
+  EHD_CK(launch_poisson(poisson_args(r, r->cur), r->storage, r->real_f64, r->stream));
+  return EHD_OK;
+}
+
+ehd_status ehd_step(ehd_run* r, long n) {
+  if (!r) return fail(EHD_EINVAL, "run is NULL");
+  if (n < 0) return fail(EHD_EINVAL, "negative step count");
+  DeviceGuard dg(r->device);
+  while (n >= kGraphSteps) {
+    if (!r->graph[r->cur]) {
+      ehd_status st = build_graph(r, r->cur);
+      if (st != EHD_OK) return st;
+    }
+    EHD_CK(cudaGraphLaunch(r->graph[r->cur], r->stream));
+    n -= kGraphSteps;
+    r->step += kGraphSteps;
+  }
+  for (; n > 0; --n) {
+    EHD_CK(enqueue_step(r, r->cur));
+    r->cur = 1 - r->cur;
+    r->step += 1;
+  }
+  return EHD_OK;
+}
+
+ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
+  if (!r || !ms_out) return fail(EHD_EINVAL, "NULL argument");
+  if (n < 0) return fail(EHD_EINVAL, "negative step count");
+  DeviceGuard dg(r->device);
+  for (int k = 0; k < EHD_NPROFILE; ++k) ms_out[k] = 0.0;
+  if (n == 0) return EHD_OK;
+  // events: per step, before K4, after K4, after K5, after the Poisson solve
+  std::vector<cudaEvent_t> ev((size_t)4 * n, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  for (long t = 0; t < n && e == cudaSuccess; ++t) {
+    const StepArgs sa = step_args(r, r->cur);
+    e = cudaEventRecord(ev[4 * t], r->stream);
+    if (e == cudaSuccess) e = launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 1], r->stream);
+    if (e == cudaSuccess) e = launch_flux_reduce(r->flux_part, r->nxb, r->small, r->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 2], r->stream);
+    if (e == cudaSuccess) e = launch_poisson(poisson_args(r, 1 - r->cur), r->storage, r->real_f64, r->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 3], r->stream);
+    if (e == cudaSuccess) {
+      r->cur = 1 - r->cur;
+      r->step += 1;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  for (long t = 0; t < n && e == cudaSuccess; ++t) {
+    float a = 0, b = 0, c = 0, d = 0;
+    e = cudaEventElapsedTime(&a, ev[4 * t], ev[4 * t + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * t + 1], ev[4 * t + 2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&c, ev[4 * t + 2], ev[4 * t + 3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&d, ev[4 * t], ev[4 * t + 3]);
+    ms_out[0] += a;
+    ms_out[1] += b;
+    ms_out[2] += c;
+    ms_out[3] += d;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e != cudaSuccess) return fail(EHD_ECUDA, "ehd_step_profile: %s", cudaGetErrorString(e));
+  ms_out[4] = (double)n;
+  return check_err(r);
+}
+
+ehd_status ehd_fields(ehd_run* r, unsigned mask, double* host_out) {
+  if (!r) return fail(EHD_EINVAL, "run is NULL");
+  if (mask == 0 || (mask & ~EHD_FIELD_ALL)) return fail(EHD_EINVAL, "invalid field mask 0x%x", mask);
+  if (!host_out) return fail(EHD_EINVAL, "host_out is NULL");
+  DeviceGuard dg(r->device);
+  int nf = 0;
+  for (int b = 0; b < 7; ++b) nf += (mask >> b) & 1;
+  const size_t n = (size_t)r->Nx * r->Ny;
+  double* dev = static_cast<double*>(run_alloc(r, nf * n * sizeof(double)));
+  if (!dev) return fail(EHD_ENOMEM, "device allocation failed");
+  cudaError_t e = launch_fields(field_args(r), r->storage, r->real_f64, mask, dev, r->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, dev, nf * n * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  run_free(r, dev);
+  if (e != cudaSuccess) return fail(EHD_ECUDA, "ehd_fields: %s", cudaGetErrorString(e));
+  return check_err(r);
+}
+
+ehd_status ehd_diagnostics(ehd_run* r, double* out) {
+  if (!r || !out) return fail(EHD_EINVAL, "NULL argument");
+  DeviceGuard dg(r->device);
+  EHD_CK(launch_reduce_state(field_args(r), r->storage, r->real_f64, r->red_part, reduce_state_blocks(),
+                             r->small + 2, r->err, r->stream));
+  double h[8];
+  EHD_CK(cudaMemcpyAsync(h, r->small, 8 * sizeof(double), cudaMemcpyDeviceToHost, r->stream));
+  EHD_CK(cudaStreamSynchronize(r->stream));
+  out[0] = h[2];  // mass
+  out[1] = h[3];  // charge
+  out[2] = h[0];  // injected since creation
+  out[3] = h[1];  // collected since creation
+  out[4] = h[4];  // kinetic energy
+  out[5] = h[5];  // max |u_y|
+  out[6] = h[6];  // max |u|
+  out[7] = (double)r->step;
+  return check_err(r);
+}
+
+ehd_status ehd_load(ehd_run* r, const double* f_host, const double* g_host) {
+  if (!r || !f_host || !g_host) return fail(EHD_EINVAL, "NULL argument");
+  DeviceGuard dg(r->device);
+  const size_t n = (size_t)r->Nx * r->Ny, plane = (size_t)r->Ny * r->P;
+  const size_t sb = storage_bytes(r->storage);
+  double* stage = static_cast<double*>(run_alloc(r, n * sizeof(double)));
+  if (!stage) return fail(EHD_ENOMEM, "device allocation failed");
+  static const double w[9] = {kW0, kW1, kW1, kW1, kW1, kW2, kW2, kW2, kW2};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(stage, f_host + i * n, n * sizeof(double), cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess)
+      e = launch_load_plane(stage, static_cast<char*>(r->f[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
+                            r->P, 0.0, nullptr, r->sf * w[i], r->stream);
+  }
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(stage, g_host + i * n, n * sizeof(double), cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess)
+      e = launch_load_plane(stage, static_cast<char*>(r->g[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
+                            r->P, w[i], r->rch, 0.0, r->stream);
+  }
+  if (e == cudaSuccess) e = launch_poisson(poisson_args(r, r->cur), r->storage, r->real_f64, r->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  run_free(r, stage);
+  if (e != cudaSuccess) return fail(EHD_ECUDA, "ehd_load: %s", cudaGetErrorString(e));
+  return EHD_OK;
+}
+
+ehd_status ehd_save(ehd_run* r, double* f_host, double* g_host) {
+  if (!r) return fail(EHD_EINVAL, "run is NULL");
+  DeviceGuard dg(r->device);
+  const size_t n = (size_t)r->Nx * r->Ny, plane = (size_t)r->Ny * r->P;
+  const size_t sb = storage_bytes(r->storage);
+  double* stage = static_cast<double*>(run_alloc(r, n * sizeof(double)));
+  if (!stage) return fail(EHD_ENOMEM, "device allocation failed");
+  static const double w[9] = {kW0, kW1, kW1, kW1, kW1, kW2, kW2, kW2, kW2};
+  cudaError_t e = cudaSuccess;
+  for (int set = 0; set < 2; ++set) {
+    double* host = set == 0 ? f_host : g_host;
+    if (!host) continue;
+    const void* base = set == 0 ? r->f[r->cur] : r->g[r->cur];
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
+      e = launch_save_plane(static_cast<const char*>(base) + i * plane * sb, stage, r->storage, r->Nx, r->Ny, r->P,
+                            set == 0 ? 0.0 : w[i], set == 0 ? nullptr : r->rch, set == 0 ? r->sf * w[i] : 0.0,
+                            r->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host + i * n, stage, n * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  run_free(r, stage);
+  if (e != cudaSuccess) return fail(EHD_ECUDA, "ehd_save: %s", cudaGetErrorString(e));
+  return EHD_OK;
+}
+
+ehd_status ehd_params(ehd_run* r, double* out) {
+  if (!r || !out) return fail(EHD_EINVAL, "NULL argument");
+  const double v[16] = {(double)r->Nx, (double)r->Ny, r->H,      r->mub,    r->eps,  r->nu,
+                        r->rho0,       r->Dc,         r->tau_p,  r->tau_m,  r->taug_p, r->taug_m,
+                        r->rho_a,      r->y_a,        (double)r->storage, (double)r->compute};
+  std::memcpy(out, v, sizeof v);
+  return EHD_OK;
+}
+
+ehd_status ehd_sync(ehd_run* r) {
+  if (!r) return fail(EHD_EINVAL, "run is NULL");
+  DeviceGuard dg(r->device);
+  return check_err(r);
+}
+
+void* ehd_stream(ehd_run* r) { return r ? static_cast<void*>(r->stream) : nullptr; }
+
+void ehd_destroy(ehd_run* r) { destroy_quiet(r); }
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// ehd_dev.cuh -- device-side types shared by the kernels and the host code of
+// the GB300 electroconvection library (D2Q9 TRT lattice Boltzmann for fluid f
+// and charge g, FFT/tridiagonal Poisson solve; arXiv:1812.05711).
+//
+// Memory layout of one run in HBM (all planes row-major, x fastest, rows
+// padded to a pitch P that is a multiple of 32 elements = 128 B for FP32):
+//   f[2], g[2]   population ping-pong buffers, [9][Ny][P] of the storage type
+//   dphi         potential minus its row mean, [Ny][P] of the compute type R
+//   phibar       row mean of the potential (the m = 0 mode), [Ny] FP64
+//   Ebar         mean-mode field E_y per row, [Ny] of R
+//   spec         half spectrum of every row, [Ny][Mh] complex R, Mh = Nx/2+1
+//   spec0        mean-mode right-hand side / solution, [Ny] FP64
+//   rfac         reciprocal Thomas pivots, mode-major [Mh][Ny] of R
+//   rfac0        the same for m = 0, [Ny] FP64
+//   tw           twiddles exp(-2 pi i k / Nx), k < Nx/2, complex R
+//   rch          per-row charge shift (hydrostatic rho_c rounded to FP32), [Ny]
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ehd {
+
+// D2Q9 numbering: c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1)
+// c5=(1,1) c6=(-1,1) c7=(-1,-1) c8=(1,-1); weights 4/9, 1/9, 1/36.
+constexpr double kW0 = 4.0 / 9.0;
+constexpr double kW1 = 1.0 / 9.0;
+constexpr double kW2 = 1.0 / 36.0;
+
+// ------------------------------------------------------------ storage ---
+template <class S> struct Store;
+template <> struct Store<double> {
+  template <class R> __device__ __forceinline__ static R ld(const double* p) { return (R)__ldg(p); }
+  template <class R> __device__ __forceinline__ static void st(double* p, R v) { *p = (double)v; }
+  template <class R> __device__ __forceinline__ static R rt(R v) { return v; }
+};
+template <> struct Store<float> {
+  template <class R> __device__ __forceinline__ static R ld(const float* p) { return (R)__ldg(p); }
+  template <class R> __device__ __forceinline__ static void st(float* p, R v) { *p = (float)v; }
+  template <class R> __device__ __forceinline__ static R rt(R v) { return (R)(float)v; }
+};
+template <> struct Store<__nv_bfloat16> {
+  template <class R> __device__ __forceinline__ static R ld(const __nv_bfloat16* p) {
+    return (R)__bfloat162float(__ldg(p));
+  }
+  template <class R> __device__ __forceinline__ static void st(__nv_bfloat16* p, R v) {
+    *p = __float2bfloat16_rn((float)v);
+  }
+  template <class R> __device__ __forceinline__ static R rt(R v) {
+    return (R)__bfloat162float(__float2bfloat16_rn((float)v));
+  }
+};
+template <> struct Store<__half> {
+  template <class R> __device__ __forceinline__ static R ld(const __half* p) { return (R)__half2float(__ldg(p)); }
+  template <class R> __device__ __forceinline__ static void st(__half* p, R v) { *p = __float2half_rn((float)v); }
+  template <class R> __device__ __forceinline__ static R rt(R v) { return (R)__half2float(__float2half_rn((float)v)); }
+};
+
+template <class R> struct Cplx { R re, im; };
+
+// ----------------------------------------------------------- kernel args ---
+struct StepArgs {
+  int Nx, Ny, P;
+  long long plane;           // elements per population plane (Ny * P)
+  const void* fin;
+  const void* gin;
+  void* fout;
+  void* gout;
+  const void* dphi;          // R [Ny][P]
+  const void* Ebar;          // R [Ny]
+  const float* rch;          // [Ny] charge shift, nullptr for unshifted storage
+  double* flux_part;         // [2][nxb] per-CTA injected / collected charge
+  int* err;                  // bit 0: non-finite density or charge
+  double wp, wm, gwp, gwm;   // omega+, omega-, omega_g+, omega_g-
+  double mub, rho0, sf;      // ion mobility, injected density, f shift (1 or 0)
+  int wall_mode;
+};
+
+struct PoissonArgs {
+  int Nx, Ny, P, Mh, log2Nx;
+  const void* gin;           // populations g (storage type), [9][Ny][P]
+  long long plane;
+  const float* rch;          // charge shift or nullptr
+  double inv_eps;            // 1 / eps
+  void* spec;                // complex R [Ny][Mh]
+  double* spec0;             // [Ny]
+  const void* rfac;          // R [Mh][Ny]
+  const double* rfac0;       // [Ny]
+  const void* tw;            // complex R [Nx/2]
+  void* dphi;                // R [Ny][P]
+  double* phibar;            // [Ny]
+  void* Ebar;                // R [Ny]
+  double phi0;               // injector potential (collector is 0)
+  int wall_mode;
+};
+
+struct FieldArgs {
+  int Nx, Ny, P;
+  long long plane;
+  const void* f;
+  const void* g;
+  const void* dphi;
+  const double* phibar;
+  const void* Ebar;
+  const float* rch;
+  double sf, mub;
+  int wall_mode;
+};
+
+// Launchers (defined in the .cu files); storage: 0 F64, 1 F32, 2 BF16, 3 F16;
+// real_f64: compute type (true = double).
+cudaError_t launch_step(const StepArgs& a, int storage, bool real_f64, int rows_per_cta, cudaStream_t s);
+int step_flux_blocks(int Nx);
+cudaError_t launch_flux_reduce(const double* part, int nxb, double* acc, cudaStream_t s);
+cudaError_t launch_poisson(const PoissonArgs& a, int storage, bool real_f64, cudaStream_t s);
+cudaError_t poisson_set_attributes();
+cudaError_t launch_fields(const FieldArgs& a, int storage, bool real_f64, unsigned mask, double* out,
+                          cudaStream_t s);
+cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, double* part, int nblk,
+                                double* out, int* err, cudaStream_t s);
+int reduce_state_blocks();
+cudaError_t launch_load_plane(const double* src, void* dst, int storage, int Nx, int Ny, int P, double shift_w,
+                              const float* rch, double sconst, cudaStream_t s);
+cudaError_t launch_save_plane(const void* src, double* dst, int storage, int Nx, int Ny, int P, double shift_w,
+                              const float* rch, double sconst, cudaStream_t s);
+cudaError_t launch_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY,
+                        const double* cY, const double* Sx, const double* Cy, double Fh, double mub,
+                        void* f, void* g, int storage, int Nx, int Ny, int P, const float* rch, double sf,
+                        cudaStream_t s);
+
+}  // namespace ehd

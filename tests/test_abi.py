@@ -1,0 +1,69 @@
+"""The C ABI library loads and exports every entry point include/ehd.h
+declares; host-side argument validation (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1812_05711_gb300 as ehd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ehd_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ctypes.CDLL(ehd.library_path() if os.path.exists(ehd.library_path()) else ehd.lib()._name)
+    names = _declared()
+    assert {"ehd_create", "ehd_poisson", "ehd_step", "ehd_fields"} <= names
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("args,msg", [
+    ((100, 80, 200, 10, 10, 4000, 0.25), "power of two"),
+    ((8, 80, 200, 10, 10, 4000, 0.25), "power of two"),
+    ((128, 1, 200, 10, 10, 4000, 0.25), "Ny"),
+    ((128, 104, -1, 10, 10, 4000, 0.25), "positive"),
+    ((128, 104, 200, 0, 10, 4000, 0.25), "positive"),
+    ((128, 104, 200, 10, 10, 4000, 0.0), "positive"),
+])
+def test_create_rejects_invalid_arguments(args, msg):
+    with pytest.raises(ehd.EhdError) as ei:
+        ehd.ehd_create(*args)
+    assert ei.value.status == -1 and msg in str(ei.value)
+
+
+def test_create_rejects_bad_options():
+    o = ehd.make_options("f32", "f64")
+    with pytest.raises(ehd.EhdError) as ei:
+        ehd.ehd_create(128, 104, 200, 10, 10, 4000, 0.25, o)
+    assert "FP64 compute needs FP64 storage" in str(ei.value)
+    o = ehd.make_options("f32", u_ion=-1.0)
+    with pytest.raises(ehd.EhdError):
+        ehd.ehd_create(128, 104, 200, 10, 10, 4000, 0.25, o)
+
+
+def test_footprint_scales_with_storage():
+    b64 = ehd.ehd_footprint(2048, 1680, 0)
+    b32 = ehd.ehd_footprint(2048, 1680, 1)
+    b16 = ehd.ehd_footprint(2048, 1680, 2)
+    assert b64 > b32 > b16
+    # populations dominate: 4 buffers of 9 planes
+    assert b32 >= 4 * 9 * 2048 * 1680 * 4
+    with pytest.raises(ehd.EhdError):
+        ehd.ehd_footprint(100, 10, 1)
+
+
+def test_default_options():
+    o = ehd.ehd_default_options()
+    assert o.storage == 1 and o.compute == 1 and o.lambda_g == 1e-6 and o.u_ion == 2e-3

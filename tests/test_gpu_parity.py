@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Error measure (scale-normalised max norm): for every field the largest
+absolute difference divided by the field's physical scale -- rho: 1,
+u: u_ion, rho_c: rho0, phi: dphi0 = 1, E: dphi0 / H.  Bars: plain FP64
+<= 1e-12 after 1000 steps; FP32 compute on shifted FP32 storage <= 2e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+
+gpu = pytest.mark.gpu
+
+
+def _ehd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1812_05711_gb300 as ehd
+    return ehd
+
+
+def _scales(p):
+    return {"rho": 1.0, "ux": p.u_ion, "uy": p.u_ion, "rho_c": p.rho0, "phi": 1.0,
+            "Ex": 1.0 / p.H, "Ey": 1.0 / p.H}
+
+
+def _errors(p, gpu_fields, ora_fields):
+    sc = _scales(p)
+    return {k: float(np.abs(gpu_fields[k] - ora_fields[k]).max() / sc[k]) for k in gpu_fields}
+
+
+def _pair(w, storage="f64", compute=None, u_ion=2e-3, wall_mode=0):
+    ehd = _ehd()
+    p = o.setup(w.Nx, w.Ny, w.T, w.C, w.M, w.Fe, w.Lambda, u_ion=u_ion, wall_mode=wall_mode)
+    s = o.init_state(p, w.amp, w.phase)
+    run = ehd.Run(*w.args(), storage=storage, compute=compute, u_ion=u_ion, wall_mode=wall_mode,
+                  amp=w.amp, phase=w.phase)
+    return ehd, p, s, run
+
+
+@gpu
+def test_initial_state_and_poisson_match_oracle():
+    w = wl.plain_fp64_channel()
+    ehd, p, s, run = _pair(w)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) < 1e-13, e
+    par = run.params()
+    for k in ("mu_b", "eps", "nu", "rho0", "Dc", "tau_p", "tau_m", "taug_p", "taug_m", "rho_a", "y_a"):
+        assert par[k] == pytest.approx(getattr(p, k), rel=1e-13), k
+
+
+@gpu
+def test_fp64_parity_1000_steps_channel_128x104():
+    w = wl.plain_fp64_channel()
+    ehd, p, s, run = _pair(w)
+    run.step(1000)
+    o.step(s, 1000)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, e
+
+
+@gpu
+def test_fp32_shifted_parity_1000_steps_channel_128x104():
+    w = wl.plain_fp64_channel()
+    ehd, p, s, run = _pair(w, storage="f32")
+    run.step(1000)
+    o.step(s, 1000)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 2e-5, e
+
+
+@gpu
+@pytest.mark.parametrize("Nx,Ny", [(16, 2), (16, 3), (256, 41), (512, 37)])
+def test_fp64_parity_ragged_and_edge_sizes(Nx, Ny):
+    """Several 128-column tiles, a ragged row tail, the smallest grids."""
+    a, ph = wl.roll(11, 1e-3)
+    w = wl.Workload("ragged", Nx, Ny, 180.0, amp=a, phase=ph)
+    ehd, p, s, run = _pair(w, u_ion=5e-3)
+    run.step(40)
+    o.step(s, 40)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, e
+
+
+@gpu
+def test_fp64_parity_node_walls():
+    w = wl.small_channel(64, seed=12)
+    ehd, p, s, run = _pair(w, wall_mode=1)
+    run.step(100)
+    o.step(s, 100)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, e
+
+
+@gpu
+def test_fp64_parity_from_loaded_random_state():
+    """Arbitrary (far from equilibrium) populations loaded through ehd_load."""
+    ehd = _ehd()
+    Nx, Ny = 64, 40
+    p = o.setup(Nx, Ny, 190, 10, 10, 4000, 0.25, u_ion=5e-3)
+    cx, cy, w, opp = o.lattice()
+    f = wl.random_populations(Nx, Ny, 21, 1.0, 0.05) * w[:, None, None]
+    g = wl.random_populations(Nx, Ny, 22, p.rho0, 0.3) * w[:, None, None]
+    s = o.state_from(p, f, g)
+    run = ehd.Run(Nx, Ny, 190, 10, 10, 4000, 0.25, storage="f64", u_ion=5e-3)
+    run.load(f, g)
+    e0 = _errors(p, run.fields(), o.fields(s))
+    assert max(e0.values()) < 1e-13, e0
+    run.step(25)
+    o.step(s, 25)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, e
+    f2, g2 = run.save()
+    np.testing.assert_allclose(f2, s.f, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(g2, s.g, rtol=0, atol=1e-15 * p.rho0)
+
+
+@gpu
+def test_load_save_roundtrip_exact_fp64():
+    ehd = _ehd()
+    Nx, Ny = 32, 26
+    f = wl.random_populations(Nx, Ny, 31, 0.1, 0.2)
+    g = wl.random_populations(Nx, Ny, 32, 0.001, 0.2)
+    run = ehd.Run(Nx, Ny, 200, 10, 10, 4000, 0.25, storage="f64")
+    run.load(f, g)
+    f2, g2 = run.save()
+    assert np.array_equal(f, f2) and np.array_equal(g, g2)
+
+
+@gpu
+def test_graph_replay_bitwise_equals_single_launches():
+    """16 steps replayed from the captured CUDA graph equal 16 single steps."""
+    ehd = _ehd()
+    w = wl.small_channel(64, seed=13)
+    r1 = ehd.Run(*w.args(), storage="f64", amp=w.amp, phase=w.phase)
+    r2 = ehd.Run(*w.args(), storage="f64", amp=w.amp, phase=w.phase)
+    r1.step(16)
+    for _ in range(16):
+        r2.step(1)
+    a, b = r1.save(), r2.save()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(r1.fields()["phi"], r2.fields()["phi"])
+
+
+@gpu
+def test_conservation_mass_and_charge_identity_gpu():
+    ehd = _ehd()
+    w = wl.small_channel(128, seed=14)
+    for storage in ("f64", "f32"):
+        run = ehd.Run(*w.args(), storage=storage, amp=w.amp, phase=w.phase, u_ion=5e-3)
+        d0 = run.diagnostics()
+        prev = d0
+        for _ in range(20):
+            run.step(1)
+            d = run.diagnostics()
+            resid = (d["charge"] - prev["charge"]) - ((d["q_in"] - prev["q_in"]) - (d["q_out"] - prev["q_out"]))
+            tol = 1e-13 if storage == "f64" else 1e-6
+            assert abs(resid) <= tol * d0["charge"], (storage, resid)
+            prev = d
+        assert abs(d["mass"] / d0["mass"] - 1) <= (1e-14 if storage == "f64" else 1e-6)
+        assert d["step"] == 20
+
+
+@gpu
+def test_oracle_diagnostics_match_gpu_fluxes():
+    w = wl.small_channel(64, seed=15)
+    ehd, p, s, run = _pair(w, u_ion=5e-3)
+    run.step(30)
+    d = o.step(s, 30, diag=True)
+    g = run.diagnostics()
+    assert g["q_in"] == pytest.approx(d[:, 2].sum(), rel=1e-11)
+    assert g["q_out"] == pytest.approx(d[:, 3].sum(), rel=1e-11)
+    F = o.fields(s)
+    assert g["charge"] == pytest.approx(F["rho_c"].sum(), rel=1e-13)
+    assert g["mass"] == pytest.approx(F["rho"].sum(), rel=1e-14)
+
+
+@gpu
+@pytest.mark.parametrize("storage,compute,bound", [("f64", "f32", 2e-5), ("bf16", "f32", 5e-2), ("f16", "f32", 5e-3)])
+def test_storage_variants_error_vs_oracle(storage, compute, bound):
+    """FP32 compute on shifted FP64 / BF16 / FP16 storage: errors are finite and
+    within loose, storage-dependent bounds (measured errors are reported by
+    the benchmark)."""
+    w = wl.plain_fp64_channel()
+    ehd, p, s, run = _pair(w, storage=storage, compute=compute)
+    run.step(200)
+    o.step(s, 200)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert all(np.isfinite(v) for v in e.values())
+    assert max(e.values()) <= bound, e
+
+
+@gpu
+def test_non_finite_state_is_reported():
+    """A NaN loaded on the host is detected by the step kernel and reported
+    as EHD_EDIVERGED by the next synchronising call."""
+    ehd = _ehd()
+    Nx, Ny = 32, 26
+    _, _, wts, _ = o.lattice()
+    f = np.ones((9, Ny, Nx)) * wts[:, None, None]
+    g = np.ones((9, Ny, Nx)) * wts[:, None, None] * 1e-3
+    f[3, 5, 7] = np.nan
+    run = ehd.Run(Nx, Ny, 200, 10, 10, 4000, 0.25, storage="f32")
+    run.load(f, g)
+    run.step(2)
+    with pytest.raises(ehd.EhdError) as ei:
+        run.sync()
+    assert ei.value.status == -4
+
+
+@gpu
+def test_full_size_fp32_two_steps_vs_oracle():
+    """2048 x 1680 in the benchmark's launch configuration: two coupled steps
+    against two oracle steps on the whole grid."""
+    w = wl.large_channel()
+    ehd, p, s, run = _pair(w, storage="f32")
+    run.step(2)
+    o.step(s, 2)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 2e-5, e
