@@ -400,9 +400,12 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     }
     r->own_stream = true;
   }
-  if (poisson_set_attributes() != cudaSuccess) {
-    destroy_quiet(r);
-    return fail(EHD_ECUDA, "cudaFuncSetAttribute failed");
+  {
+    const cudaError_t e = poisson_set_attributes();
+    if (e != cudaSuccess) {
+      destroy_quiet(r);
+      return fail(EHD_ECUDA, "setting the shared-memory limit of the Poisson kernels: %s", cudaGetErrorString(e));
+    }
   }
 
   const size_t plane = (size_t)Ny * r->P;

@@ -279,14 +279,26 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class K>
+cudaError_t allow_max_dynamic_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 template <class S, class R>
 cudaError_t set_attrs_t() {
-  const int mx = 227 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_rows_fwd<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaError_t e = allow_max_dynamic_smem(k_rows_fwd<S, R>);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_modes<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  e = allow_max_dynamic_smem(k_modes<R>);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_rows_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return allow_max_dynamic_smem(k_rows_inv<R>);
 }
 
 }  // namespace

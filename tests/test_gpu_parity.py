@@ -113,9 +113,10 @@ def test_fp64_parity_from_loaded_random_state():
     o.step(s, 25)
     e = _errors(p, run.fields(), o.fields(s))
     assert max(e.values()) <= 1e-12, e
+    # populations themselves: a few ulps of reassociation per step
     f2, g2 = run.save()
-    np.testing.assert_allclose(f2, s.f, rtol=0, atol=1e-15)
-    np.testing.assert_allclose(g2, s.g, rtol=0, atol=1e-15 * p.rho0)
+    np.testing.assert_allclose(f2, s.f, rtol=0, atol=1e-13 * np.abs(s.f).max())
+    np.testing.assert_allclose(g2, s.g, rtol=0, atol=1e-13 * np.abs(s.g).max())
 
 
 @gpu
