@@ -164,6 +164,35 @@ ehd_status ehd_sync(ehd_run* run);
 /* The cudaStream_t the run enqueues on. */
 void* ehd_stream(ehd_run* run);
 
+/* Poisson solve on caller-owned device buffers that allocates no device
+ * memory.  The paper has no counterpart; this exists for callers that cannot
+ * call cudaMalloc while they run -- a process whose device memory is all
+ * reserved up front by a framework's own pool, or a latency-critical loop
+ * that cannot accept the implicit device synchronisation of cudaMalloc and
+ * cudaFree.  It solves the same discrete problem as ehd_poisson
+ * (d2/dx2 spectral, second differences in y, phi = phi0 at the injector
+ * wall and 0 at the collector, wall placement per wall_mode as in
+ * ehd_options) for the charge density the caller passes:
+ *   rhoc  device, FP32, [Ny][Nx] row-major, read only
+ *   phi   device, FP32, [Ny][Nx] row-major, written (the full potential)
+ *   eps   lattice permittivity (the equation is lap phi = -rho_c / eps)
+ *   stream  cudaStream_t to enqueue on (NULL = the legacy default stream).
+ * Every intermediate (half spectrum, Thomas pivots, twiddles, FP64 mean
+ * profile) lives in one fixed 8 MiB __device__ array inside the library;
+ * every GPU that loads the library holds it until the process exits.  Sizes
+ * whose intermediates do not fit (beyond about 1024 x 840 nodes; Nx a power
+ * of two up to 2048, Ny up to 4096) return EHD_EINVAL with a message, as do
+ * NULL pointers and eps <= 0.  The first call on a device, with that device
+ * current, looks up the array's device address and builds the tables for
+ * the sizes given; make that first call before any stream capture.  Later
+ * calls rebuild the tables only when Nx, Ny or wall_mode change.  All calls
+ * share the one array and it keeps the last call's contents (each call
+ * writes everything it reads, so nothing needs clearing): calls that
+ * overlap on the GPU, e.g. on two streams, race.  Asynchronous. */
+ehd_status ehd_poisson_noalloc(int Nx, int Ny, double eps, double phi0,
+                               int wall_mode, const float* rhoc, float* phi,
+                               void* stream);
+
 /* Free the run and its device memory (synchronises first).  NULL is a no-op. */
 void ehd_destroy(ehd_run* run);
 

@@ -92,6 +92,8 @@ def lib():
         L.ehd_destroy.restype = None
         L.ehd_last_error.restype = ctypes.c_char_p
         L.ehd_set_allocator.argtypes = [vp, vp, vp]
+        L.ehd_poisson_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ip, vp, vp, vp]
+        L.ehd_poisson_noalloc.restype = ctypes.c_int
         for name in ("ehd_create", "ehd_poisson", "ehd_step", "ehd_step_profile", "ehd_fields", "ehd_diagnostics",
                      "ehd_load", "ehd_save", "ehd_params", "ehd_footprint", "ehd_sync",
                      "ehd_set_allocator"):
@@ -199,6 +201,14 @@ def ehd_footprint(Nx, Ny, storage) -> int:
     b = ctypes.c_size_t()
     _check(lib().ehd_footprint(int(Nx), int(Ny), int(storage), ctypes.byref(b)))
     return b.value
+
+
+def ehd_poisson_noalloc(Nx, Ny, eps, phi0, wall_mode, rhoc_ptr: int, phi_ptr: int, stream: int = 0):
+    """Poisson solve on caller-owned device buffers (FP32 [Ny][Nx]) that
+    allocates no device memory; see include/ehd.h."""
+    _check(lib().ehd_poisson_noalloc(int(Nx), int(Ny), float(eps), float(phi0), int(wall_mode),
+                                     ctypes.c_void_p(rhoc_ptr), ctypes.c_void_p(phi_ptr),
+                                     ctypes.c_void_p(stream) if stream else None))
 
 
 def ehd_sync(h):

@@ -282,6 +282,11 @@ ehd_status destroy_quiet(ehd_run* r) {
 
 }  // namespace
 
+namespace ehd {
+// Lets other translation units of the library report through ehd_last_error.
+void set_error(const char* msg) { g_err = msg; }
+}  // namespace ehd
+
 // ======================================================================= ABI
 extern "C" {
 
