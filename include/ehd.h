@@ -87,6 +87,11 @@ typedef struct {
   double pert_phase[EHD_MAX_PERT_MODES]; /* x-phase, radians */
   void* stream;     /* cudaStream_t to run on; NULL = a stream the library
                        creates and owns */
+  int step_kernel;  /* 0: march form -- a warp walks a slab of rows, pulls the
+                       populations through registers and writes the new
+                       charge density itself (default); 1: one thread per
+                       node, push form, charge density summed by a separate
+                       kernel.  Same results up to rounding order. */
 } ehd_options;
 
 /* Fill *opt with the defaults above. */
@@ -122,9 +127,11 @@ ehd_status ehd_step(ehd_run* run, long n);
 /* Instrumented stepping: advance n steps with one launch per kernel (no
  * graph) and CUDA events on the run's stream around each phase; the paper has
  * no counterpart (measurement only).  host ms_out[EHD_NPROFILE]: summed
- * milliseconds of [0] the fused collide-stream kernel, [1] the wall-flux
- * reduction, [2] the Poisson solve (forward FFT, tridiagonal modes, inverse
- * FFT), [3] whole steps, [4] = n.  Synchronises. */
+ * milliseconds of [0] the fused collide-stream kernel, [1] the charge-moment
+ * kernel (0 when the step kernel writes the charge itself), [2] the Poisson
+ * solve (forward FFT, tridiagonal modes, inverse FFT; the FP64 mean mode runs
+ * beside them on a second stream and is joined before the event), [3] whole
+ * steps, [4] = n.  Synchronises. */
 #define EHD_NPROFILE 5
 ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 

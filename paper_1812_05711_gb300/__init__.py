@@ -52,6 +52,7 @@ class Options(ctypes.Structure):
         ("pert_amp", ctypes.c_double * MAX_PERT_MODES),
         ("pert_phase", ctypes.c_double * MAX_PERT_MODES),
         ("stream", ctypes.c_void_p),
+        ("step_kernel", ctypes.c_int),
     ]
 
 
@@ -173,7 +174,7 @@ def ehd_step(h, n: int):
 def ehd_step_profile(h, n: int) -> dict:
     out = np.zeros(5)
     _check(lib().ehd_step_profile(h, int(n), _dp(out)))
-    return {"collide_stream_ms": out[0], "flux_ms": out[1], "poisson_ms": out[2], "step_ms": out[3],
+    return {"collide_stream_ms": out[0], "charge_ms": out[1], "poisson_ms": out[2], "step_ms": out[3],
             "steps": int(out[4])}
 
 
@@ -229,7 +230,7 @@ def ehd_last_error() -> str:
 
 # ------------------------------------------------------------ convenience
 def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
-                 amp=(), phase=(), stream=None) -> Options:
+                 amp=(), phase=(), stream=None, step_kernel=0) -> Options:
     o = ehd_default_options()
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if compute is None:
@@ -246,6 +247,7 @@ def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mo
         o.pert_amp[k] = float(a)
         o.pert_phase[k] = float(p)
     o.stream = stream
+    o.step_kernel = int(step_kernel)
     return o
 
 
@@ -258,14 +260,14 @@ class Run:
     """
 
     def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
-                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True):
+                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=0):
         self.Nx, self.Ny = int(Nx), int(Ny)
         self._stream_obj = None
         if stream is None and torch_stream:
             import torch
             self._stream_obj = torch.cuda.Stream()
             stream = self._stream_obj.cuda_stream
-        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream)
+        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel)
         self.handle = ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt)
 
     # lifecycle

@@ -55,7 +55,7 @@ size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 
 
 struct ehd_run {
   int device = 0;
-  int Nx = 0, Ny = 0, P = 0, Mh = 0, log2Nx = 0;
+  int Nx = 0, Ny = 0, P = 0, Mh = 0, Mp = 0, log2Nx = 0;
   int storage = 1, compute = 1, wall_mode = 0;
   bool real_f64 = false;
   size_t rsz = 4;  // sizeof compute real
@@ -66,18 +66,21 @@ struct ehd_run {
   // device state
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;        // second stream for the FP64 mean mode
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void* rhoc = nullptr;               // charge plane [Ny][P] of the compute type
   Allocator al;
   std::vector<void*> blocks;
   void* f[2] = {nullptr, nullptr};
   void* g[2] = {nullptr, nullptr};
   int cur = 0;
   void* dphi = nullptr;
-  double* phibar = nullptr;
+  void* phibar = nullptr;
   void* Ebar = nullptr;
   void* spec = nullptr;
-  double* spec0 = nullptr;
+  void* spec0 = nullptr;
   void* rfac = nullptr;
-  double* rfac0 = nullptr;
+  void* rfac0 = nullptr;
   void* tw = nullptr;
   float* rch = nullptr;
   double* flux_part = nullptr;
@@ -85,7 +88,10 @@ struct ehd_run {
   double* small = nullptr;  // [0] q_in sum, [1] q_out sum, [2..7] last reduction
   int* err = nullptr;
   double* red_part = nullptr;
-  int rows = 1;
+  int rows = 1;        // rows per CTA of the node-parallel step kernel
+  int step_kernel = 0; // 0 march form, 1 node-parallel push form
+  int slab_rows = 4;   // rows per warp slab of the march form
+  int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
@@ -183,19 +189,21 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.rho0 = r->rho0;
   a.sf = r->sf;
   a.wall_mode = r->wall_mode;
+  a.rhoc_out = r->rhoc;
+  a.slab_rows = r->slab_rows;
+  a.nstrips = r->nstrips;
   return a;
 }
 
-PoissonArgs poisson_args(const ehd_run* r, int cur) {
+PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   PoissonArgs a{};
   a.Nx = r->Nx;
   a.Ny = r->Ny;
   a.P = r->P;
   a.Mh = r->Mh;
+  a.Mp = r->Mp;
   a.log2Nx = r->log2Nx;
-  a.gin = r->g[cur];
-  a.plane = (long long)r->Ny * r->P;
-  a.rch = r->rch;
+  a.rhoc = r->rhoc;
   a.inv_eps = 1.0 / r->eps;
   a.spec = r->spec;
   a.spec0 = r->spec0;
@@ -207,7 +215,18 @@ PoissonArgs poisson_args(const ehd_run* r, int cur) {
   a.Ebar = r->Ebar;
   a.phi0 = r->phi0;
   a.wall_mode = r->wall_mode;
+  a.flux_part = with_flux ? r->flux_part : nullptr;
+  a.nflux = r->nxb;
+  a.flux_acc = r->small;
   return a;
+}
+
+// Charge plane of buffer `cur`, then phi (the Poisson solve).
+cudaError_t enqueue_poisson(ehd_run* r, int cur, bool with_flux) {
+  cudaError_t e = launch_rhoc(r->g[cur], (long long)r->Ny * r->P, r->storage, r->real_f64, r->Nx, r->Ny, r->P,
+                              r->rch, r->rhoc, r->stream);
+  if (e != cudaSuccess) return e;
+  return launch_poisson(poisson_args(r, with_flux), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
 }
 
 FieldArgs field_args(const ehd_run* r) {
@@ -228,15 +247,20 @@ FieldArgs field_args(const ehd_run* r) {
   return a;
 }
 
-// One coupled step from buffer `cur`: K4 collide+stream, K5 wall fluxes, then
-// the Poisson solve (K1-K3) of the new charge.
+// One coupled step from buffer `cur`: collide+stream with the wall-flux
+// partials, then the Poisson solve of the new charge (which also adds the
+// fluxes to the FP64 totals).  The march form writes the new charge itself;
+// the node-parallel form needs the separate charge-moment kernel.
 cudaError_t enqueue_step(ehd_run* r, int cur) {
   const StepArgs sa = step_args(r, cur);
+  if (r->step_kernel == 0) {
+    cudaError_t e = launch_march(sa, r->storage, r->real_f64, r->stream);
+    if (e != cudaSuccess) return e;
+    return launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
+  }
   cudaError_t e = launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
   if (e != cudaSuccess) return e;
-  e = launch_flux_reduce(r->flux_part, r->nxb, r->small, r->stream);
-  if (e != cudaSuccess) return e;
-  return launch_poisson(poisson_args(r, 1 - cur), r->storage, r->real_f64, r->stream);
+  return enqueue_poisson(r, 1 - cur, true);
 }
 
 ehd_status build_graph(ehd_run* r, int cur) {
@@ -273,6 +297,10 @@ ehd_status destroy_quiet(ehd_run* r) {
   if (r->stream) cudaStreamSynchronize(r->stream);
   for (int k = 0; k < 2; ++k)
     if (r->graph[k]) cudaGraphExecDestroy(r->graph[k]);
+  if (r->side) cudaStreamSynchronize(r->side);
+  if (r->ev_fork) cudaEventDestroy(r->ev_fork);
+  if (r->ev_join) cudaEventDestroy(r->ev_join);
+  if (r->side) cudaStreamDestroy(r->side);
   std::vector<void*> bl = r->blocks;
   for (void* p : bl) run_free(r, p);
   if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
@@ -347,6 +375,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_EINVAL, "FP64 compute needs FP64 storage");
   if (o.wall_mode != 0 && o.wall_mode != 1) return fail(EHD_EINVAL, "wall_mode must be 0 or 1");
   if (o.n_modes < 0 || o.n_modes > EHD_MAX_PERT_MODES) return fail(EHD_EINVAL, "n_modes out of range");
+  if (o.step_kernel != 0 && o.step_kernel != 1) return fail(EHD_EINVAL, "step_kernel must be 0 or 1");
 
   ehd_run* r = new ehd_run();
   {
@@ -361,6 +390,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->Ny = Ny;
   r->P = (Nx + 31) / 32 * 32;
   r->Mh = Nx / 2 + 1;
+  r->Mp = (r->Mh + 3) / 4 * 4;
   while ((1 << r->log2Nx) < Nx) ++r->log2Nx;
   r->storage = o.storage;
   r->compute = o.compute;
@@ -405,6 +435,12 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     }
     r->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    destroy_quiet(r);
+    return fail(EHD_ECUDA, "stream/event creation failed");
+  }
   {
     const cudaError_t e = poisson_set_attributes();
     if (e != cudaSuccess) {
@@ -420,26 +456,37 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     r->g[k] = run_alloc(r, 9 * plane * sb);
   }
   r->dphi = run_alloc(r, plane * r->rsz);
-  r->phibar = static_cast<double*>(run_alloc(r, Ny * sizeof(double)));
+  r->rhoc = run_alloc(r, plane * r->rsz);
+  r->phibar = run_alloc(r, Ny * sizeof(double));
   r->Ebar = run_alloc(r, Ny * r->rsz);
-  r->spec = run_alloc(r, (size_t)Ny * r->Mh * 2 * r->rsz);
-  r->spec0 = static_cast<double*>(run_alloc(r, Ny * sizeof(double)));
-  r->rfac = run_alloc(r, (size_t)r->Mh * Ny * r->rsz);
-  r->rfac0 = static_cast<double*>(run_alloc(r, Ny * sizeof(double)));
-  r->tw = run_alloc(r, (size_t)(Nx / 2) * 2 * r->rsz);
+  r->spec = run_alloc(r, (size_t)Ny * r->Mp * 2 * r->rsz);
+  r->spec0 = run_alloc(r, Ny * sizeof(double));
+  r->rfac = run_alloc(r, (size_t)r->Mp * Ny * r->rsz);
+  r->rfac0 = run_alloc(r, Ny * sizeof(double));
+  r->tw = run_alloc(r, (size_t)Nx * 2 * r->rsz);
   if (shifted) r->rch = static_cast<float*>(run_alloc(r, Ny * sizeof(float)));
-  r->nxb = step_flux_blocks(Nx);
+  r->step_kernel = o.step_kernel;
+  r->nstrips = march_strips(Nx);
+  r->nxb = (r->step_kernel == 0) ? r->nstrips : step_flux_blocks(Nx);
   r->flux_part = static_cast<double*>(run_alloc(r, 2 * r->nxb * sizeof(double)));
   r->small = static_cast<double*>(run_alloc(r, 16 * sizeof(double) + 64));
   r->red_part = static_cast<double*>(run_alloc(r, (size_t)reduce_state_blocks() * 6 * sizeof(double)));
-  bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->phibar && r->Ebar && r->spec && r->spec0 &&
+  bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->phibar && r->Ebar && r->spec && r->spec0 &&
             r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part;
   if (!ok) {
     destroy_quiet(r);
     return fail(EHD_ENOMEM, "device allocation failed");
   }
   r->err = reinterpret_cast<int*>(r->small + 16);
-  // rows per CTA of K4: keep >= ~4 CTAs per SM
+  // march slabs: about 16 warps per SM in one wave, at least 4 rows each
+  {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
+    const long long target = 16LL * sms;
+    long long rows = ((long long)Ny * r->nstrips + target - 1) / target;
+    r->slab_rows = (int)std::max(4LL, std::min((long long)Ny, rows));
+  }
+  // rows per CTA of the node-parallel kernel: keep >= ~4 CTAs per SM
   {
     const long long xb = (Nx + 127) / 128;
     long long rows = xb * Ny / 608;
@@ -448,13 +495,14 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
 
   // ---- host tables: twiddles, Thomas pivots, shifts, initial profiles
   {
-    std::vector<double> twd((size_t)Nx);  // interleaved re, im for k < Nx/2
-    for (int k = 0; k < Nx / 2; ++k) {
-      const double ang = 2.0 * kPi * (double)k / (double)Nx;
-      twd[2 * k] = std::cos(ang);
-      twd[2 * k + 1] = -std::sin(ang);
+    std::vector<double> twd(2 * (size_t)Nx);  // interleaved re, im: exp(-2 pi i q / Nx), q < Nx
+    for (int q = 0; q < Nx; ++q) {
+      const double ang = 2.0 * kPi * (double)q / (double)Nx;
+      twd[2 * q] = std::cos(ang);
+      twd[2 * q + 1] = -std::sin(ang);
     }
-    std::vector<double> piv((size_t)r->Mh * Ny);
+    // reciprocal Thomas pivots, [Ny][Mp] (row-major, wavenumber fastest)
+    std::vector<double> piv((size_t)r->Mp * Ny, 1.0), piv0(Ny);
     for (int m = 0; m < r->Mh; ++m) {
       const double kx = 2.0 * kPi * (double)m / (double)Nx;
       const double diag = -(2.0 + kx * kx);
@@ -464,7 +512,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
         const double b = (j == 0 || j == Ny - 1) ? corner : diag;
         const double beta = (j == 0) ? b : b - prev;
         prev = 1.0 / beta;
-        piv[(size_t)m * Ny + j] = prev;
+        piv[(size_t)j * r->Mp + m] = prev;
+        if (m == 0) piv0[j] = prev;
       }
     }
     if (r->real_f64) {
@@ -475,7 +524,18 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
       st = upload(r, r->tw, twf.data(), twf.size() * 4);
       if (st == EHD_OK) st = upload(r, r->rfac, pivf.data(), pivf.size() * 4);
     }
-    if (st == EHD_OK) st = upload(r, r->rfac0, piv.data(), Ny * sizeof(double));
+    if (st == EHD_OK) {
+      if (r->real_f64) {
+        st = upload(r, r->rfac0, piv0.data(), Ny * sizeof(double));
+      } else {  // float-float (hi, lo) pairs for the FP32 path's mean mode
+        std::vector<float> ff(2 * (size_t)Ny);
+        for (int j = 0; j < Ny; ++j) {
+          ff[2 * j] = (float)piv0[j];
+          ff[2 * j + 1] = (float)(piv0[j] - (double)ff[2 * j]);
+        }
+        st = upload(r, r->rfac0, ff.data(), ff.size() * sizeof(float));
+      }
+    }
     if (st != EHD_OK) {
       destroy_quiet(r);
       return st;
@@ -526,7 +586,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
       if (e == cudaSuccess)
         e = launch_init(p, p + Ny, p + 2 * Ny, p + 3 * Ny, p + 4 * Ny, p + 5 * Ny, p + 5 * Ny + nx, Fh, r->mub,
                         r->f[0], r->g[0], r->storage, Nx, Ny, r->P, r->rch, r->sf, r->stream);
-      if (e == cudaSuccess) e = launch_poisson(poisson_args(r, 0), r->storage, r->real_f64, r->stream);
+      if (e == cudaSuccess) e = enqueue_poisson(r, 0, false);
       if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
       if (e != cudaSuccess) st = fail(EHD_ECUDA, "initialisation: %s", cudaGetErrorString(e));
     }
@@ -543,7 +603,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
 ehd_status ehd_poisson(ehd_run* r) {
   if (!r) return fail(EHD_EINVAL, "run is NULL");
   DeviceGuard dg(r->device);
-  EHD_CK(launch_poisson(poisson_args(r, r->cur), r->storage, r->real_f64, r->stream));
+  EHD_CK(enqueue_poisson(r, r->cur, false));
   return EHD_OK;
 }
 
@@ -581,15 +641,21 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
     if (e == cudaSuccess) e = cudaEventCreate(&x);
   for (long t = 0; t < n && e == cudaSuccess; ++t) {
     const StepArgs sa = step_args(r, r->cur);
+    const int nxt = 1 - r->cur;
     e = cudaEventRecord(ev[4 * t], r->stream);
-    if (e == cudaSuccess) e = launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
+    if (e == cudaSuccess)
+      e = (r->step_kernel == 0) ? launch_march(sa, r->storage, r->real_f64, r->stream)
+                                : launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 1], r->stream);
-    if (e == cudaSuccess) e = launch_flux_reduce(r->flux_part, r->nxb, r->small, r->stream);
+    if (e == cudaSuccess && r->step_kernel == 1)
+      e = launch_rhoc(r->g[nxt], (long long)r->Ny * r->P, r->storage, r->real_f64, r->Nx, r->Ny, r->P, r->rch,
+                      r->rhoc, r->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 2], r->stream);
-    if (e == cudaSuccess) e = launch_poisson(poisson_args(r, 1 - r->cur), r->storage, r->real_f64, r->stream);
+    if (e == cudaSuccess)
+      e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 3], r->stream);
     if (e == cudaSuccess) {
-      r->cur = 1 - r->cur;
+      r->cur = nxt;
       r->step += 1;
     }
   }
@@ -670,7 +736,7 @@ ehd_status ehd_load(ehd_run* r, const double* f_host, const double* g_host) {
       e = launch_load_plane(stage, static_cast<char*>(r->g[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
                             r->P, w[i], r->rch, 0.0, r->stream);
   }
-  if (e == cudaSuccess) e = launch_poisson(poisson_args(r, r->cur), r->storage, r->real_f64, r->stream);
+  if (e == cudaSuccess) e = enqueue_poisson(r, r->cur, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
   run_free(r, stage);
   if (e != cudaSuccess) return fail(EHD_ECUDA, "ehd_load: %s", cudaGetErrorString(e));

@@ -76,24 +76,30 @@ struct StepArgs {
   double wp, wm, gwp, gwm;   // omega+, omega-, omega_g+, omega_g-
   double mub, rho0, sf;      // ion mobility, injected density, f shift (1 or 0)
   int wall_mode;
+  // march form only
+  void* rhoc_out;            // R [Ny][P]: rho_c of the new state
+  int slab_rows;             // rows per warp slab
+  int nstrips;               // 32-column strips (30 owned columns each)
 };
 
 struct PoissonArgs {
   int Nx, Ny, P, Mh, log2Nx;
-  const void* gin;           // populations g (storage type), [9][Ny][P]
-  long long plane;
-  const float* rch;          // charge shift or nullptr
+  int Mp;                    // row pitch of the spectrum and pivot tables (Mh rounded up to 4)
+  const void* rhoc;          // charge density, R [Ny][P]
   double inv_eps;            // 1 / eps
-  void* spec;                // complex R [Ny][Mh]
-  double* spec0;             // [Ny]
-  const void* rfac;          // R [Mh][Ny]
-  const double* rfac0;       // [Ny]
-  const void* tw;            // complex R [Nx/2]
+  void* spec;                // half spectrum, complex R [Ny][Mp]
+  void* spec0;               // row sums (m = 0), [Ny]: double, or float (hi, lo) pairs when R = float
+  const void* rfac;          // reciprocal pivots, R [Ny][Mp] (m >= 1 used)
+  const void* rfac0;         // reciprocal pivots of m = 0, [Ny]: double, or float (hi, lo) pairs
+  const void* tw;            // complex R [Nx]: exp(-2 pi i q / Nx)
   void* dphi;                // R [Ny][P]
-  double* phibar;            // [Ny]
+  void* phibar;              // row-mean potential [Ny]: double, or float (hi, lo) pairs when R = float
   void* Ebar;                // R [Ny]
   double phi0;               // injector potential (collector is 0)
   int wall_mode;
+  const double* flux_part;   // [2][nflux] wall-flux partials of the last step, or nullptr
+  int nflux;
+  double* flux_acc;          // [2] FP64 totals of injected / collected charge
 };
 
 struct FieldArgs {
@@ -102,19 +108,39 @@ struct FieldArgs {
   const void* f;
   const void* g;
   const void* dphi;
-  const double* phibar;
+  const void* phibar;        // double, or float (hi, lo) pairs when R = float
   const void* Ebar;
   const float* rch;
   double sf, mub;
   int wall_mode;
 };
 
+// Row-mean potential as stored: a double, or a float-float (hi, lo) pair on
+// the FP32 path (kept off the slow scalar FP64 units during the step).
+template <class R>
+__device__ __forceinline__ double load_phibar(const void* p, int j) {
+  if constexpr (sizeof(R) == 8) {
+    return static_cast<const double*>(p)[j];
+  } else {
+    const float2 v = static_cast<const float2*>(p)[j];
+    return (double)v.x + (double)v.y;
+  }
+}
+
 // Launchers (defined in the .cu files); storage: 0 F64, 1 F32, 2 BF16, 3 F16;
 // real_f64: compute type (true = double).
 cudaError_t launch_step(const StepArgs& a, int storage, bool real_f64, int rows_per_cta, cudaStream_t s);
 int step_flux_blocks(int Nx);
-cudaError_t launch_flux_reduce(const double* part, int nxb, double* acc, cudaStream_t s);
-cudaError_t launch_poisson(const PoissonArgs& a, int storage, bool real_f64, cudaStream_t s);
+cudaError_t launch_march(const StepArgs& a, int storage, bool real_f64, cudaStream_t s);
+int march_strips(int Nx);
+// Poisson solve from the charge plane: forward row FFTs and the wavenumber
+// systems on s; the FP64 mean mode (and the wall-flux totals) on `side`
+// between the fork and join events when side != nullptr.
+cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
+                           cudaEvent_t join);
+// rho_c = sum_i g_i (+ the row shift) into the charge plane.
+cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f64, int Nx, int Ny, int P,
+                        const float* rch, void* rhoc, cudaStream_t s);
 cudaError_t poisson_set_attributes();
 cudaError_t launch_fields(const FieldArgs& a, int storage, bool real_f64, unsigned mask, double* out,
                           cudaStream_t s);

@@ -1,0 +1,395 @@
+// k_march.cu -- the fused collide-and-stream kernel in "march" form: one warp
+// walks up a slab of rows of a 32-column strip (30 owned columns plus one halo
+// column on each side), so that every population it stores has been pulled
+// from registers (x-neighbours by warp shuffles, y-neighbours from the rows
+// already collided) and the charge of the new state, rho_c(t+1) = sum_i g_i
+// (Eq. 6), is formed from exactly the values stored -- no second pass over g.
+//
+// Per row r of the walk: load the 9 f and 9 g of the lane's node (the next
+// row is prefetched), form E = -grad phi, the moments (Eqs. 5-7), collide f
+// with the electric force (TRT, Eqs. 8, 10, 12, 13, 15) and g with the drift
+// (TRT, Eqs. 9, 11, 14), then route the post-collision values:
+//   c_y = 0   -> row r     (complete once row r+1 has been collided)
+//   c_y = +1  -> row r + 1 (kept in registers)
+//   c_y = -1  -> row r - 1 (completes row r - 1, which is stored)
+// The walls of Table I enter as row rules: halfway bounce-back of f on both
+// walls, anti-bounce-back injection of rho0 (with the wall drift mu_b E) and
+// zero-gradient outflow of g.  Halo rows (one below and one above the slab)
+// and halo columns are collided but not stored.
+#include "ehd_dev.cuh"
+
+namespace ehd {
+
+namespace {
+
+template <class R>
+__device__ __forceinline__ void trt_f2(R& fi, R& fo, R w, R drho, R rho, R cu, R usq15, R cF, R uF3, R wp, R wm, R cp,
+                                       R cm) {
+  const R ep = w * (drho + rho * (R(4.5) * cu * cu - usq15));
+  const R em = w * rho * R(3) * cu;
+  const R Fp = w * (R(9) * cu * cF - uF3);
+  const R Fm = w * R(3) * cF;
+  const R sp = R(0.5) * (fi + fo), sm = R(0.5) * (fi - fo);
+  const R A = cp * Fp - wp * (sp - ep);
+  const R B = cm * Fm - wm * (sm - em);
+  fi = fi + A + B;
+  fo = fo + A - B;
+}
+
+template <class R>
+__device__ __forceinline__ void trt_g2(R& gi, R& go, R w, R drc, R rc, R cv, R vsq15, R wp, R wm) {
+  const R ep = w * (drc + rc * (R(4.5) * cv * cv - vsq15));
+  const R em = w * rc * R(3) * cv;
+  const R sp = R(0.5) * (gi + go), sm = R(0.5) * (gi - go);
+  const R A = -wp * (sp - ep);
+  const R B = -wm * (sm - em);
+  gi = gi + A + B;
+  go = go + A - B;
+}
+
+// cp.async of one element (4 or 8 bytes) global -> shared, per thread
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gsrc), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <class R>
+__device__ __forceinline__ R from_left(R v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <class R>
+__device__ __forceinline__ R from_right(R v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+}  // namespace
+
+// Rows ahead of the walk are staged per warp in a shared-memory ring of NST
+// rows by cp.async when the storage element is 4 or 8 bytes (2-byte storage
+// loads directly).  A stage holds 20 slots x 32 lanes: 18 populations, the
+// potential fluctuation of the next row in the lane's column, and one
+// lane-specific value (lane 0 / 31: the potential just outside the strip;
+// lane 1: the row's mean field; lanes 2-4: the charge shift of rows r, r+1,
+// r-1).
+template <class S>
+struct MarchStages {
+  static constexpr bool kAsync = sizeof(S) >= 4;
+  static constexpr int kN = sizeof(S) >= 8 ? 2 : 3;
+  static constexpr int kSlots = 20;
+  static constexpr size_t kBytesPerWarp = kAsync ? (size_t)kN * kSlots * 32 * sizeof(S) : 0;
+};
+
+template <class S, class R>
+__global__ void __launch_bounds__(128) k_march(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char march_smem[];
+  using St = MarchStages<S>;
+  constexpr int NST = St::kN;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
+  const int strip = gw % ns, slab = gw / ns;
+  const int y0 = slab * a.slab_rows;
+  if (y0 >= Ny) return;  // whole warp
+  const int y1 = min(y0 + a.slab_rows, Ny);
+  const int xs = strip * 30;
+  int xc = (xs - 1 + lane + Nx) % Nx;
+  const bool owned = lane >= 1 && lane <= 30 && xs + lane - 1 < Nx;
+  const int xW = (xc == 0) ? Nx - 1 : xc - 1;
+  const int xE = (xc == Nx - 1) ? 0 : xc + 1;
+  const long long pl = a.plane;
+  const S* __restrict__ fin = static_cast<const S*>(a.fin);
+  const S* __restrict__ gin = static_cast<const S*>(a.gin);
+  S* __restrict__ fo = static_cast<S*>(a.fout);
+  S* __restrict__ go = static_cast<S*>(a.gout);
+  R* __restrict__ rho_out = static_cast<R*>(a.rhoc_out);
+  const R* __restrict__ dphi = static_cast<const R*>(a.dphi);
+  const R* __restrict__ Ebar = static_cast<const R*>(a.Ebar);
+  const float* __restrict__ rch = a.rch;
+  const R wp = (R)a.wp, wm = (R)a.wm, gwp = (R)a.gwp, gwm = (R)a.gwm;
+  const R cp = R(1) - R(0.5) * wp, cm = R(1) - R(0.5) * wm;
+  const R mub = (R)a.mub, rho0 = (R)a.rho0, sf = (R)a.sf;
+  const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
+  const R W0 = (R)kW0, W1 = (R)kW1, W2 = (R)kW2;
+
+  const int rs = max(y0 - 1, 0), re = min(y1, Ny - 1);
+  // carried registers: H (c_y = 0) of row r-1, U (c_y = +1) of rows r-1 and r
+  R Hm[6] = {}, Um[6] = {}, Uc[6] = {};
+  // potential fluctuation in the lane's column: rows r-1, r
+  R pm, pc;
+  {
+    const R p0 = __ldg(dphi + (long long)rs * P + xc);
+    pm = (rs > 0) ? __ldg(dphi + (long long)(rs - 1) * P + xc) : gwall * p0;
+    pc = p0;
+  }
+  double qin = 0.0, qout = 0.0;
+  bool bad = false;
+  constexpr int SL = St::kSlots;
+  S* ring = reinterpret_cast<S*>(march_smem) + (size_t)(threadIdx.x >> 5) * NST * SL * 32 + lane;
+  auto issue = [&](int row_y, int stage) {
+    const long long c = (long long)row_y * P + xc;
+    S* dst = ring + (size_t)stage * SL * 32;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      cp_async_elem<sizeof(S)>(dst + i * 32, fin + i * pl + c);
+      cp_async_elem<sizeof(S)>(dst + (9 + i) * 32, gin + i * pl + c);
+    }
+    if (row_y + 1 < Ny) cp_async_elem<sizeof(R)>(dst + 18 * 32, dphi + c + P);
+    const void* extra = nullptr;
+    int eb = 0;  // bytes: 4 or sizeof(R)
+    if (lane == 0) {
+      extra = dphi + (long long)row_y * P + xW;
+      eb = sizeof(R);
+    } else if (lane == 31) {
+      extra = dphi + (long long)row_y * P + xE;
+      eb = sizeof(R);
+    } else if (lane == 1) {
+      extra = Ebar + row_y;
+      eb = sizeof(R);
+    } else if (rch && lane == 2) {
+      extra = rch + row_y;
+      eb = 4;
+    } else if (rch && lane == 3 && row_y + 1 < Ny) {
+      extra = rch + row_y + 1;
+      eb = 4;
+    } else if (rch && lane == 4 && row_y > 0) {
+      extra = rch + row_y - 1;
+      eb = 4;
+    }
+    if (eb == 8)
+      cp_async_elem<8>(dst + 19 * 32, extra);
+    else if (eb == 4)
+      cp_async_elem<4>(dst + 19 * 32, extra);
+  };
+  if constexpr (St::kAsync) {
+#pragma unroll
+    for (int k = 0; k < NST - 1; ++k) {
+      if (rs + k <= re) issue(rs + k, k);
+      cp_async_commit();
+    }
+  }
+  R F[9], G[9];
+  for (int r = rs; r <= re; ++r) {
+    const long long row = (long long)r * P;
+    R pn, pW, pE, Ebr, sy, s_up, s_dn;
+    if constexpr (St::kAsync) {
+      const int k = r - rs;
+      if (r + NST - 1 <= re) issue(r + NST - 1, (k + NST - 1) % NST);
+      cp_async_commit();
+      cp_async_wait<NST - 1>();  // this lane's copies of row r have landed
+      const S* src = ring + (size_t)(k % NST) * SL * 32;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        F[i] = (R)src[i * 32];
+        G[i] = (R)src[(9 + i) * 32];
+      }
+      __syncwarp();  // other lanes' extra slots are read below by shuffle sources
+      const R nx = *reinterpret_cast<const R*>(src + 18 * 32);
+      pn = (r + 1 < Ny) ? nx : gwall * pc;
+      const R ex_r = *reinterpret_cast<const R*>(src + 19 * 32);
+      const float ex_f = *reinterpret_cast<const float*>(src + 19 * 32);
+      pW = from_left(pc);
+      pE = from_right(pc);
+      if (lane == 0) pW = ex_r;
+      if (lane == 31) pE = ex_r;
+      Ebr = __shfl_sync(0xffffffffu, ex_r, 1);
+      sy = rch ? (R)__shfl_sync(0xffffffffu, ex_f, 2) : R(0);
+      s_up = (rch && r + 1 < Ny) ? (R)__shfl_sync(0xffffffffu, ex_f, 3) : sy;
+      s_dn = (rch && r > 0) ? (R)__shfl_sync(0xffffffffu, ex_f, 4) : sy;
+    } else {
+      const long long c = row + xc;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        F[i] = Store<S>::template ld<R>(fin + i * pl + c);
+        G[i] = Store<S>::template ld<R>(gin + i * pl + c);
+      }
+      pn = (r + 1 < Ny) ? __ldg(dphi + row + P + xc) : gwall * pc;
+      pW = __ldg(dphi + row + xW);
+      pE = __ldg(dphi + row + xE);
+      Ebr = __ldg(Ebar + r);
+      sy = rch ? (R)__ldg(rch + r) : R(0);
+      s_up = (rch && r + 1 < Ny) ? (R)__ldg(rch + r + 1) : sy;
+      s_dn = (rch && r > 0) ? (R)__ldg(rch + r - 1) : sy;
+    }
+    const R Ex = R(-0.5) * (pE - pW);
+    const R Ey = Ebr - R(0.5) * (pn - pm);
+    // moments, Eqs. 5-7
+    R f0 = F[0], f1 = F[1], f2 = F[2], f3 = F[3], f4 = F[4], f5 = F[5], f6 = F[6], f7 = F[7], f8 = F[8];
+    R g0 = G[0], g1 = G[1], g2 = G[2], g3 = G[3], g4 = G[4], g5 = G[5], g6 = G[6], g7 = G[7], g8 = G[8];
+    const R drho = ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
+    const R rho = sf + drho;
+    const R jx = (f1 - f3) + (f5 - f7) + (f8 - f6);
+    const R jy = (f2 - f4) + (f5 - f7) + (f6 - f8);
+    const R drc = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + (g6 + g7)) + g8;
+    const R rc = sy + drc;
+    if (owned && (!isfinite(drho) || !isfinite(drc))) bad = true;
+    const R Fx = rc * Ex, Fy = rc * Ey;
+    const R irho = R(1) / rho;
+    const R ux = (jx + R(0.5) * Fx) * irho;
+    const R uy = (jy + R(0.5) * Fy) * irho;
+    const R vx = ux + mub * Ex, vy = uy + mub * Ey;
+    const R usq15 = R(1.5) * (ux * ux + uy * uy);
+    const R uF3 = R(3) * (ux * Fx + uy * Fy);
+    f0 = f0 - wp * (f0 - W0 * (drho - rho * usq15)) - cp * W0 * uF3;
+    trt_f2<R>(f1, f3, W1, drho, rho, ux, usq15, Fx, uF3, wp, wm, cp, cm);
+    trt_f2<R>(f2, f4, W1, drho, rho, uy, usq15, Fy, uF3, wp, wm, cp, cm);
+    trt_f2<R>(f5, f7, W2, drho, rho, ux + uy, usq15, Fx + Fy, uF3, wp, wm, cp, cm);
+    trt_f2<R>(f6, f8, W2, drho, rho, uy - ux, usq15, Fy - Fx, uF3, wp, wm, cp, cm);
+    const R vsq15 = R(1.5) * (vx * vx + vy * vy);
+    g0 = g0 - gwp * (g0 - W0 * (drc - rc * vsq15));
+    trt_g2<R>(g1, g3, W1, drc, rc, vx, vsq15, gwp, gwm);
+    trt_g2<R>(g2, g4, W1, drc, rc, vy, vsq15, gwp, gwm);
+    trt_g2<R>(g5, g7, W2, drc, rc, vx + vy, vsq15, gwp, gwm);
+    trt_g2<R>(g6, g8, W2, drc, rc, vy - vx, vsq15, gwp, gwm);
+
+    // pulled values of this row's post-collision populations: x-shift by c_x
+    const R P1f = from_left(f1), P5f = from_left(f5), P8f = from_left(f8);
+    const R P3f = from_right(f3), P6f = from_right(f6), P7f = from_right(f7);
+    const R P1g = from_left(g1), P5g = from_left(g5), P8g = from_left(g8);
+    const R P3g = from_right(g3), P6g = from_right(g6), P7g = from_right(g7);
+
+    // c_y = +1: into row r + 1 (shift of the charge moves with the row)
+    R Un[6];
+    {
+      const R sh = sy - s_up;
+      Un[0] = f2;
+      Un[1] = P5f;
+      Un[2] = P6f;
+      Un[3] = g2 + W1 * sh;
+      Un[4] = P5g + W2 * sh;
+      Un[5] = P6g + W2 * sh;
+    }
+    if (r == 0) {
+      // injector wall: the upward populations of row 0 come from the node's
+      // own downward ones: bounce-back for f, anti-bounce-back for g
+      const R wx = mub * Ex, wy = mub * Ey;
+      const R w15 = R(1.5) * (wx * wx + wy * wy);
+      const R c2 = wy, c5 = wx + wy, c6 = wy - wx;
+      const R n2 = -(g4 + R(2) * W1 * sy) + R(2) * W1 * rho0 * (R(1) + R(4.5) * c2 * c2 - w15);
+      const R n5 = -(g7 + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c5 * c5 - w15);
+      const R n6 = -(g8 + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c6 * c6 - w15);
+      Uc[0] = f4;
+      Uc[1] = f7;
+      Uc[2] = f8;
+      Uc[3] = n2;
+      Uc[4] = n5;
+      Uc[5] = n6;
+      if (owned && y0 == 0)
+        qin += (((double)Store<S>::rt(n2) - (double)Store<S>::rt(g4)) +
+                ((double)Store<S>::rt(n5) - (double)Store<S>::rt(g7))) +
+               ((double)Store<S>::rt(n6) - (double)Store<S>::rt(g8));
+    }
+    // c_y = -1: into row r - 1, which is then complete
+    if (r - 1 >= y0) {
+      const R sh = sy - s_dn;
+      const long long c = row - P + xc;
+      if (owned) {
+        const R n4 = g4 + W1 * sh, n7 = P7g + W2 * sh, n8 = P8g + W2 * sh;
+        Store<S>::st(fo + c, Hm[0]);
+        Store<S>::st(fo + pl + c, Hm[1]);
+        Store<S>::st(fo + 2 * pl + c, Um[0]);
+        Store<S>::st(fo + 3 * pl + c, Hm[2]);
+        Store<S>::st(fo + 4 * pl + c, f4);
+        Store<S>::st(fo + 5 * pl + c, Um[1]);
+        Store<S>::st(fo + 6 * pl + c, Um[2]);
+        Store<S>::st(fo + 7 * pl + c, P7f);
+        Store<S>::st(fo + 8 * pl + c, P8f);
+        Store<S>::st(go + c, Hm[3]);
+        Store<S>::st(go + pl + c, Hm[4]);
+        Store<S>::st(go + 2 * pl + c, Um[3]);
+        Store<S>::st(go + 3 * pl + c, Hm[5]);
+        Store<S>::st(go + 4 * pl + c, n4);
+        Store<S>::st(go + 5 * pl + c, Um[4]);
+        Store<S>::st(go + 6 * pl + c, Um[5]);
+        Store<S>::st(go + 7 * pl + c, n7);
+        Store<S>::st(go + 8 * pl + c, n8);
+        const R sprev = s_dn;
+        const R q = ((Store<S>::rt(Hm[3]) + Store<S>::rt(Hm[4])) + (Store<S>::rt(Um[3]) + Store<S>::rt(Hm[5]))) +
+                    ((Store<S>::rt(n4) + Store<S>::rt(Um[4])) + (Store<S>::rt(Um[5]) + Store<S>::rt(n7))) +
+                    Store<S>::rt(n8);
+        rho_out[c] = sprev + q;
+      }
+    }
+    if (r == Ny - 1 && r >= y0 && r < y1) {
+      // collector wall: f bounces back into the node; g leaves and the
+      // downward populations re-enter from the node's own row (outflow)
+      const long long c = row + xc;
+      if (owned) {
+        Store<S>::st(fo + c, f0);
+        Store<S>::st(fo + pl + c, P1f);
+        Store<S>::st(fo + 2 * pl + c, Uc[0]);
+        Store<S>::st(fo + 3 * pl + c, P3f);
+        Store<S>::st(fo + 4 * pl + c, f2);
+        Store<S>::st(fo + 5 * pl + c, Uc[1]);
+        Store<S>::st(fo + 6 * pl + c, Uc[2]);
+        Store<S>::st(fo + 7 * pl + c, f5);
+        Store<S>::st(fo + 8 * pl + c, f6);
+        Store<S>::st(go + c, g0);
+        Store<S>::st(go + pl + c, P1g);
+        Store<S>::st(go + 2 * pl + c, Uc[3]);
+        Store<S>::st(go + 3 * pl + c, P3g);
+        Store<S>::st(go + 4 * pl + c, g4);
+        Store<S>::st(go + 5 * pl + c, Uc[4]);
+        Store<S>::st(go + 6 * pl + c, Uc[5]);
+        Store<S>::st(go + 7 * pl + c, P7g);
+        Store<S>::st(go + 8 * pl + c, P8g);
+        const R q = ((Store<S>::rt(g0) + Store<S>::rt(P1g)) + (Store<S>::rt(Uc[3]) + Store<S>::rt(P3g))) +
+                    ((Store<S>::rt(g4) + Store<S>::rt(Uc[4])) + (Store<S>::rt(Uc[5]) + Store<S>::rt(P7g))) +
+                    Store<S>::rt(P8g);
+        rho_out[c] = sy + q;
+        qout += ((double)Store<S>::rt(g2) + (double)Store<S>::rt(g5)) + (double)Store<S>::rt(g6);
+        qout -= ((double)Store<S>::rt(g4) + (double)Store<S>::rt(g7)) + (double)Store<S>::rt(g8);
+      }
+    }
+    // rotate the carried rows
+    Hm[0] = f0;
+    Hm[1] = P1f;
+    Hm[2] = P3f;
+    Hm[3] = g0;
+    Hm[4] = P1g;
+    Hm[5] = P3g;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      Um[k] = Uc[k];
+      Uc[k] = Un[k];
+    }
+    pm = pc;
+    pc = pn;
+  }
+  if constexpr (St::kAsync) cp_async_wait<0>();
+  if (bad) atomicOr(a.err, 1);
+  // wall fluxes: one partial per strip (slab 0 injects, the top slab collects)
+  if (y0 == 0) {
+    double v = qin;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.flux_part[strip] = v;
+  }
+  if (y1 == Ny) {
+    double v = qout;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.flux_part[ns + strip] = v;
+  }
+}
+
+namespace {
+template <class S, class R>
+cudaError_t march_t(const StepArgs& a, cudaStream_t s) {
+  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
+  k_march<S, R><<<(unsigned)((warps + 3) / 4), 128, 4 * MarchStages<S>::kBytesPerWarp, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+int march_strips(int Nx) { return (Nx + 29) / 30; }
+
+cudaError_t launch_march(const StepArgs& a, int storage, bool real_f64, cudaStream_t s) {
+  if (real_f64) return storage == 0 ? march_t<double, double>(a, s) : cudaErrorInvalidValue;
+  switch (storage) {
+    case 0: return march_t<double, float>(a, s);
+    case 1: return march_t<float, float>(a, s);
+    case 2: return march_t<__nv_bfloat16, float>(a, s);
+    case 3: return march_t<__half, float>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ehd

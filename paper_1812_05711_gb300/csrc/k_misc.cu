@@ -42,7 +42,7 @@ __device__ Macro macro_at(const FieldArgs& a, int x, int y) {
   Macro m;
   m.Ex = -0.5 * ((double)dphi[c - x + xr] - (double)dphi[c - x + xl]);
   m.Ey = (double)static_cast<const R*>(a.Ebar)[y] - 0.5 * (pN - pS);
-  m.phi = a.phibar[y] + pc;
+  m.phi = load_phibar<R>(a.phibar, y) + pc;
   m.rho = rho;
   m.rc = rc;
   m.ux = (jx + 0.5 * rc * m.Ex) / rho;

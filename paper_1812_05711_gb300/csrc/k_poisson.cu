@@ -1,18 +1,25 @@
 // k_poisson.cu -- fast Poisson solver of Sec. IV.3 (arXiv:1812.05711) on the
 // GB300: [Dx^2 + Dy^2] phi = s, s = -rho_c / eps (Eqs. 4, 18).  Spectral in x
-// (Eqs. 19-20), second-order finite differences in y with Dirichlet walls,
-// i.e. one constant-coefficient tridiagonal system per wavenumber (its
-// eigenvalues are the -4 sin^2 symbols of Eq. 24, so this equals the
-// odd-extension transform of Eqs. 21-25).
+// (Eqs. 19-20), second-order finite differences in y with Dirichlet walls:
+// one constant-coefficient tridiagonal system per wavenumber (its eigenvalues
+// are the -4 sin^2 symbols of Eq. 24, so this equals the odd-extension
+// transform of Eqs. 21-25).
 //
-//   K1 k_rows_fwd  one CTA per row: rho_c = sum_i g_i (Eq. 6), the row mean in
-//                  FP64 (the m = 0 mode), Stockham radix-2 FFT of the
-//                  fluctuation in shared memory, half spectrum out.
-//   K2 k_modes     one warp per wavenumber: Thomas recurrences with the
-//                  precomputed reciprocal pivots, written as a warp-parallel
-//                  scan of affine maps (32 lanes x Ny/32 rows each); the
-//                  m = 0 mode carries the wall potential and runs in FP64.
-//   K3 k_rows_inv  one CTA per row: inverse FFT -> phi minus its row mean.
+//   k_rhoc        rho_c = sum_i g_i (Eq. 6) from the populations, when the
+//                 step kernel did not already write it.
+//   k_rfft_rows   1024/L rows per CTA (L = Nx/2): the row's N real samples are
+//                 packed as L complex values, transformed by a radix-4
+//                 Stockham FFT in shared memory and untangled into the half
+//                 spectrum (Eq. 19).  The row mean (the m = 0 mode) is summed
+//                 in FP32 pairs with a compensated tree and removed first.
+//   k_modes_tile  8 wavenumbers x Ny rows per CTA held in shared memory; the
+//                 Thomas recurrences of each wavenumber (reciprocal pivots
+//                 precomputed) run as 32 chunk-parallel affine scans.
+//   k_mean_mode   128 threads: the m = 0 system in FP64 with the wall
+//                 potentials lifted into the right-hand side; also adds the
+//                 step's wall-flux partials to the run's FP64 totals.  It
+//                 runs on a second stream, beside k_modes_tile/k_rfft_inv.
+//   k_irfft_rows  inverse of k_rfft_rows -> phi minus its row mean.
 #include "ehd_dev.cuh"
 
 namespace ehd {
@@ -23,260 +30,649 @@ template <class R>
 __device__ __forceinline__ Cplx<R> cmul(Cplx<R> a, Cplx<R> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
-
-// Stockham autosort radix-2 FFT of length N (power of two) in shared memory,
-// ping-ponging between a and b.  tw[k] = exp(-2 pi i k / N), k < N/2.
-// Returns the buffer holding the result.  All threads of the block call it.
 template <class R>
-__device__ Cplx<R>* fft_shared(Cplx<R>* a, Cplx<R>* b, int N, const Cplx<R>* __restrict__ tw, bool inverse) {
-  const int half = N >> 1;
-  for (int Ns = 1; Ns < N; Ns <<= 1) {
-    const int tstride = N / (2 * Ns);
-    for (int j = threadIdx.x; j < half; j += blockDim.x) {
+__device__ __forceinline__ Cplx<R> cadd(Cplx<R> a, Cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+__device__ __forceinline__ Cplx<R> csub(Cplx<R> a, Cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+__device__ __forceinline__ Cplx<R> cconj(Cplx<R> a) { return {a.re, -a.im}; }
+
+// Radix-4 Stockham FFT of length L (power of two, L >= 2) for the rows of a
+// CTA, T = max(L/4, 1) threads per row; a/b point at this row's two buffers
+// (padded indexing).  tw[q] = exp(-2 pi i q / N) with N = 2L, in shared
+// memory; W_L^q = tw[2q].  Every thread of the CTA must call it (it
+// synchronises).  Returns the buffer with the result.
+template <class R>
+__device__ Cplx<R>* fft_rows(Cplx<R>* a, Cplx<R>* b, int L, int T, int tr, const Cplx<R>* tw, bool inverse);
+
+// shared-memory index with one complex of padding every 16 (bank spread)
+__device__ __forceinline__ int pidx(int c) { return c + (c >> 4); }
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_chunk(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gsrc), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// error-free sum of two floats (Knuth): s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <class R>
+__device__ Cplx<R>* fft_rows(Cplx<R>* a, Cplx<R>* b, int L, int T, int tr, const Cplx<R>* tw, bool inverse) {
+  int Ns = 1;
+  int log2L = 0;
+  while ((1 << log2L) < L) ++log2L;
+  if (log2L & 1) {  // one radix-2 stage
+    const int half = L >> 1;
+    for (int j = tr; j < half; j += T) {
       const int k = j & (Ns - 1);
-      Cplx<R> w = tw[k * tstride];
+      Cplx<R> w = tw[2 * k * (L / (2 * Ns))];
       if (inverse) w.im = -w.im;
-      const Cplx<R> u = a[j];
-      const Cplx<R> v = cmul(a[j + half], w);
+      const Cplx<R> u = a[pidx(j)], v = cmul(a[pidx(j + half)], w);
       const int idx = ((j - k) << 1) + k;
-      b[idx] = {u.re + v.re, u.im + v.im};
-      b[idx + Ns] = {u.re - v.re, u.im - v.im};
+      b[pidx(idx)] = cadd(u, v);
+      b[pidx(idx + Ns)] = csub(u, v);
     }
     __syncthreads();
     Cplx<R>* t = a;
     a = b;
     b = t;
+    Ns = 2;
+  }
+  const int q = L >> 2;
+  while (Ns < L) {
+    for (int j = tr; j < q; j += T) {
+      const int k = j & (Ns - 1);
+      const int st = 2 * (L / (4 * Ns)) * k;
+      Cplx<R> w1 = tw[st], w2 = tw[2 * st], w3 = tw[3 * st];
+      if (inverse) {
+        w1.im = -w1.im;
+        w2.im = -w2.im;
+        w3.im = -w3.im;
+      }
+      const Cplx<R> v0 = a[pidx(j)], v1 = cmul(a[pidx(j + q)], w1), v2 = cmul(a[pidx(j + 2 * q)], w2),
+                    v3 = cmul(a[pidx(j + 3 * q)], w3);
+      const Cplx<R> t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+      const Cplx<R> d = csub(v1, v3);
+      const Cplx<R> t3 = inverse ? Cplx<R>{-d.im, d.re} : Cplx<R>{d.im, -d.re};  // (+-i)(v1 - v3)
+      const int idx = (j - k) * 4 + k;
+      b[pidx(idx)] = cadd(t0, t2);
+      b[pidx(idx + Ns)] = cadd(t1, t3);
+      b[pidx(idx + 2 * Ns)] = csub(t0, t2);
+      b[pidx(idx + 3 * Ns)] = csub(t1, t3);
+    }
+    __syncthreads();
+    Cplx<R>* t = a;
+    a = b;
+    b = t;
+    Ns <<= 2;
   }
   return a;
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];  // fixed order
-    red[0] = t;
-  }
-  __syncthreads();
-  t = red[0];
-  __syncthreads();
-  return t;
-}
+// padded complex elements per row buffer
+__host__ __device__ __forceinline__ int row_len_padded(int L) { return L + (L >> 4) + 1; }
 
 }  // namespace
 
-// --------------------------------------------------------------------- K1 ---
+// ----------------------------------------------------------------- rho_c ---
 template <class S, class R>
-__global__ void __launch_bounds__(256) k_rows_fwd(PoissonArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[8];
-  Cplx<R>* A = reinterpret_cast<Cplx<R>*>(smem_raw);
-  Cplx<R>* B = A + a.Nx;
-  const int y = blockIdx.x;
-  const int N = a.Nx;
-  const S* __restrict__ g = static_cast<const S*>(a.gin);
-  const R sg = a.rch ? (R)a.rch[y] : R(0);
-  const R ieps = (R)a.inv_eps;
-  double sum = 0.0;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    const long long c = (long long)y * a.P + x;
-    R rc = R(0);
+__global__ void k_rhoc(const S* __restrict__ g, long long plane, int Nx, int Ny, int P, const float* __restrict__ rch,
+                       R* __restrict__ rhoc) {
+  const long long n = (long long)Nx * Ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % Nx), y = (int)(k / Nx);
+    const long long c = (long long)y * P + x;
+    R v = rch ? (R)rch[y] : R(0);
+    R s = R(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) rc += Store<S>::template ld<R>(g + i * a.plane + c);
-    const R s = -(rc + sg) * ieps;  // Eq. 4 source
-    A[x].re = s;
-    sum += (double)s;
+    for (int i = 0; i < 9; ++i) s += Store<S>::template ld<R>(g + i * plane + c);
+    rhoc[c] = v + s;
   }
-  const double total = block_sum(sum, red);  // DFT coefficient m = 0 (Eq. 19)
-  if (threadIdx.x == 0) a.spec0[y] = total;
-  const R mean = (R)(total / (double)N);
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    A[x].re -= mean;
-    A[x].im = R(0);
-  }
-  __syncthreads();
-  const Cplx<R>* res = fft_shared<R>(A, B, N, static_cast<const Cplx<R>*>(a.tw), false);
-  Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec) + (long long)y * a.Mh;
-  for (int m = threadIdx.x; m < a.Mh; m += blockDim.x) spec[m] = (m == 0) ? Cplx<R>{R(0), R(0)} : res[m];
 }
 
-// --------------------------------------------------------------------- K2 ---
-namespace {
-
-// Thomas for one system with unit off-diagonals, d'_j = r_j (d_j - d'_{j-1}),
-// x_j = d'_j - r_j x_{j+1}, each recurrence evaluated as a warp scan of the
-// affine maps of the lanes' contiguous chunks [j0, j1).
-template <class R, class V>
-struct Scan;
-
+// ------------------------------------------------------------ forward FFT ---
+// Shared memory: twiddle table (N complex), then per row two padded buffers.
 template <class R>
-struct Scan<R, R> {
-  __device__ static R shup(R v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
-  __device__ static R shdn(R v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
-  __device__ static R zero() { return R(0); }
-  __device__ static R axpy(R a, R x, R b) { return a * x + b; }   // a x + b
-  __device__ static R sub(R x, R y) { return x - y; }
-  __device__ static R scl(R a, R x) { return a * x; }
-};
-
-template <class R>
-struct Scan<R, Cplx<R>> {
-  using V = Cplx<R>;
-  __device__ static V shup(V v, int o) {
-    return {__shfl_up_sync(0xffffffffu, v.re, o), __shfl_up_sync(0xffffffffu, v.im, o)};
-  }
-  __device__ static V shdn(V v, int o) {
-    return {__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o)};
-  }
-  __device__ static V zero() { return {R(0), R(0)}; }
-  __device__ static V axpy(R a, V x, V b) { return {a * x.re + b.re, a * x.im + b.im}; }
-  __device__ static V sub(V x, V y) { return {x.re - y.re, x.im - y.im}; }
-  __device__ static V scl(R a, V x) { return {a * x.re, a * x.im}; }
-};
-
-template <class R, class V>
-__device__ void warp_thomas(V* d, const R* __restrict__ r, int Ny, int lane) {
-  using Op = Scan<R, V>;
-  const int C = (Ny + 31) >> 5;
-  const int j0 = min(lane * C, Ny), j1 = min(j0 + C, Ny);
-  // forward elimination: chunk map x -> al x + br
-  R al = R(1);
-  V br = Op::zero();
-  for (int j = j0; j < j1; ++j) {
-    const R rj = r[j];
-    al = -rj * al;
-    br = Op::scl(rj, Op::sub(d[j], br));
-  }
-  for (int o = 1; o < 32; o <<= 1) {
-    const R a2 = __shfl_up_sync(0xffffffffu, al, o);
-    const V b2 = Op::shup(br, o);
-    if (lane >= o) {
-      br = Op::axpy(al, b2, br);
-      al = al * a2;
-    }
-  }
-  V x = Op::shup(br, 1);
-  if (lane == 0) x = Op::zero();
-  for (int j = j0; j < j1; ++j) {
-    x = Op::scl(r[j], Op::sub(d[j], x));
-    d[j] = x;
-  }
-  __syncwarp();
-  // back substitution, chunks composed from the top lane down
-  al = R(1);
-  br = Op::zero();
-  for (int j = j1 - 1; j >= j0; --j) {
-    const R rj = r[j];
-    al = -rj * al;
-    br = Op::axpy(-rj, br, d[j]);
-  }
-  for (int o = 1; o < 32; o <<= 1) {
-    const R a2 = __shfl_down_sync(0xffffffffu, al, o);
-    const V b2 = Op::shdn(br, o);
-    if (lane + o < 32) {
-      br = Op::axpy(al, b2, br);
-      al = al * a2;
-    }
-  }
-  x = Op::shdn(br, 1);
-  if (lane == 31) x = Op::zero();
-  for (int j = j1 - 1; j >= j0; --j) {
-    x = Op::axpy(-r[j], x, d[j]);
-    d[j] = x;
-  }
-  __syncwarp();
-}
-
-}  // namespace
-
-template <class R>
-__global__ void __launch_bounds__(128) k_modes(PoissonArgs a, int warps_per_cta) {
+__global__ void __launch_bounds__(256) k_rfft_rows(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = blockIdx.x * warps_per_cta + warp;
-  if (warp >= warps_per_cta || m >= a.Mh) return;  // warp-uniform exit
-  const int Ny = a.Ny;
-  if (m == 0) {
-    // mean mode in FP64 with the wall potentials lifted into the right-hand
-    // side: mirror ghost phi_{-1} = 2 phi_w - phi_0 (or phi_w on node walls)
-    double* d = reinterpret_cast<double*>(smem_raw) + (size_t)warp * Ny * (sizeof(Cplx<R>) / sizeof(double));
-    const double wc = (a.wall_mode == 0) ? 2.0 : 1.0;
-    for (int j = lane; j < Ny; j += 32) {
-      double v = a.spec0[j];
-      if (j == 0) v -= wc * (double)a.Nx * a.phi0;
-      d[j] = v;
+  __shared__ float wred_hi[8], wred_lo[8];
+  __shared__ double wred_d[8];
+  const int N = a.Nx, L = N >> 1;
+  const int T = (L >= 4) ? (L >> 2) : 1;  // threads per row
+  const int rows = 256 / T;
+  const int lr = threadIdx.x / T, tr = threadIdx.x % T;
+  const int y = blockIdx.x * rows + lr;
+  const bool live = (y < a.Ny);
+  const int LP = row_len_padded(L);
+  Cplx<R>* stw = reinterpret_cast<Cplx<R>*>(smem_raw);
+  Cplx<R>* A = stw + N + (size_t)lr * LP;
+  Cplx<R>* B = stw + N + (size_t)rows * LP + (size_t)lr * LP;
+  const Cplx<R>* gtw = static_cast<const Cplx<R>*>(a.tw);
+  for (int q = threadIdx.x; q < N; q += 256) stw[q] = gtw[q];
+  const R* __restrict__ rc = static_cast<const R*>(a.rhoc) + (long long)(live ? y : 0) * a.P;
+  const R ieps = (R)a.inv_eps;
+  // s = -rho_c / eps packed as complex pairs; per-thread partial sum
+  R part = R(0);
+  for (int n = tr; n < L; n += T) {
+    R s0 = R(0), s1 = R(0);
+    if (live) {
+      if constexpr (sizeof(R) == 4) {
+        const float2 v = reinterpret_cast<const float2*>(rc)[n];
+        s0 = -v.x * ieps;
+        s1 = -v.y * ieps;
+      } else {
+        const double2 v = reinterpret_cast<const double2*>(rc)[n];
+        s0 = -v.x * ieps;
+        s1 = -v.y * ieps;
+      }
     }
-    __syncwarp();
-    warp_thomas<double, double>(d, a.rfac0, Ny, lane);
-    const double inN = 1.0 / (double)a.Nx;
-    R* Ebar = static_cast<R*>(a.Ebar);
-    for (int j = lane; j < Ny; j += 32) {
-      const double pc = d[j] * inN;
-      const double pd = (j > 0) ? d[j - 1] * inN : ((a.wall_mode == 0) ? 2.0 * a.phi0 - pc : a.phi0);
-      const double pu = (j < Ny - 1) ? d[j + 1] * inN : ((a.wall_mode == 0) ? -pc : 0.0);
-      a.phibar[j] = pc;
-      Ebar[j] = (R)(-0.5 * (pu - pd));
-    }
-    return;
+    A[pidx(n)] = {s0, s1};
+    part += s0 + s1;
   }
-  Cplx<R>* d = reinterpret_cast<Cplx<R>*>(smem_raw) + (size_t)warp * Ny;
-  Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec);
-  const R* r = static_cast<const R*>(a.rfac) + (long long)m * Ny;
-  for (int j = lane; j < Ny; j += 32) d[j] = spec[(long long)j * a.Mh + m];
-  __syncwarp();
-  warp_thomas<R, Cplx<R>>(d, r, Ny, lane);
-  for (int j = lane; j < Ny; j += 32) spec[(long long)j * a.Mh + m] = d[j];
-}
-
-// --------------------------------------------------------------------- K3 ---
-template <class R>
-__global__ void __launch_bounds__(256) k_rows_inv(PoissonArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cplx<R>* A = reinterpret_cast<Cplx<R>*>(smem_raw);
-  Cplx<R>* B = A + a.Nx;
-  const int y = blockIdx.x;
-  const int N = a.Nx, half = N >> 1;
-  const Cplx<R>* spec = static_cast<const Cplx<R>*>(a.spec) + (long long)y * a.Mh;
-  for (int m = threadIdx.x; m < N; m += blockDim.x) {
-    Cplx<R> v;
-    if (m == 0) {
-      v = {R(0), R(0)};  // the mean is carried by phibar
-    } else if (m <= half) {
-      v = spec[m];
+  // row sum (the m = 0 DFT coefficient) over the row's T threads: shuffles
+  // within segments of min(T, 32) lanes, then the row's warps
+  const int W = T < 32 ? T : 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float shi = 0.0f, slo = 0.0f;  // FP32 path: float-float
+  double sd = 0.0;               // FP64 path
+  if constexpr (sizeof(R) == 8) {
+    sd = (double)part;
+    for (int o = W >> 1; o > 0; o >>= 1) sd += __shfl_down_sync(0xffffffffu, sd, o, W);
+    if (T > 32) {
+      if (lane == 0) wred_d[warp] = sd;
+      __syncthreads();
+      if (tr == 0)
+        for (int w = 1; w < T / 32; ++w) sd += wred_d[warp + w];
+    }
+  } else {
+    shi = (float)part;
+    for (int o = W >> 1; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, shi, o, W), l2 = __shfl_down_sync(0xffffffffu, slo, o, W);
+      float s_, e_;
+      two_sum(shi, h2, s_, e_);
+      shi = s_;
+      slo = slo + l2 + e_;
+    }
+    if (T > 32) {
+      if (lane == 0) {
+        wred_hi[warp] = shi;
+        wred_lo[warp] = slo;
+      }
+      __syncthreads();
+      if (tr == 0)
+        for (int w = 1; w < T / 32; ++w) {
+          float s_, e_;
+          two_sum(shi, wred_hi[warp + w], s_, e_);
+          shi = s_;
+          slo = slo + wred_lo[warp + w] + e_;
+        }
+    }
+  }
+  __shared__ R rmean[256 / 2];  // rows per CTA <= 128
+  if (tr == 0) {
+    if constexpr (sizeof(R) == 8) {
+      if (live) static_cast<double*>(a.spec0)[y] = sd;
+      rmean[lr] = (R)(sd / (double)N);
     } else {
-      const Cplx<R> s = spec[N - m];  // Hermitian symmetry of a real row
-      v = {s.re, -s.im};
+      float h, l;  // renormalise
+      two_sum(shi, slo, h, l);
+      if (live) static_cast<float2*>(a.spec0)[y] = make_float2(h, l);
+      rmean[lr] = h / (float)N;
     }
-    A[m] = v;
   }
   __syncthreads();
-  const Cplx<R>* res = fft_shared<R>(A, B, N, static_cast<const Cplx<R>*>(a.tw), true);
-  R* dphi = static_cast<R*>(a.dphi) + (long long)y * a.P;
-  const R inN = R(1) / (R)N;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) dphi[x] = res[x].re * inN;
+  const R mean = rmean[lr];
+  for (int n = tr; n < L; n += T) {
+    A[pidx(n)].re -= mean;
+    A[pidx(n)].im -= mean;
+  }
+  __syncthreads();
+  const Cplx<R>* Z = fft_rows<R>(A, B, L, T, tr, stw, false);
+  // untangle: S[k] = (Z[k] + Z*[L-k]) / 2 - i W^k (Z[k] - Z*[L-k]) / 2
+  if (live) {
+    Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec) + (long long)y * a.Mp;
+    for (int k = tr; k <= L; k += T) {
+      if (k == 0) {
+        spec[0] = {R(0), R(0)};
+        continue;
+      }
+      const Cplx<R> zk = Z[pidx(k == L ? 0 : k)], zc = cconj(Z[pidx(L - k)]);
+      const Cplx<R> E = {R(0.5) * (zk.re + zc.re), R(0.5) * (zk.im + zc.im)};
+      const Cplx<R> Dm = {R(0.5) * (zk.re - zc.re), R(0.5) * (zk.im - zc.im)};
+      const Cplx<R> O = {Dm.im, -Dm.re};  // D / i
+      spec[k] = cadd(E, cmul(stw[k], O));
+    }
+  }
+}
+
+// ------------------------------------------------------------ inverse FFT ---
+template <class R>
+__global__ void __launch_bounds__(256) k_irfft_rows(PoissonArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.Nx, L = N >> 1;
+  const int T = (L >= 4) ? (L >> 2) : 1;
+  const int rows = 256 / T;
+  const int lr = threadIdx.x / T, tr = threadIdx.x % T;
+  const int y = blockIdx.x * rows + lr;
+  const bool live = (y < a.Ny);
+  const int LP = row_len_padded(L);
+  Cplx<R>* stw = reinterpret_cast<Cplx<R>*>(smem_raw);
+  Cplx<R>* A = stw + N + (size_t)lr * LP;
+  Cplx<R>* B = stw + N + (size_t)rows * LP + (size_t)lr * LP;
+  const Cplx<R>* gtw = static_cast<const Cplx<R>*>(a.tw);
+  for (int q = threadIdx.x; q < N; q += 256) stw[q] = gtw[q];
+  __syncthreads();
+  const Cplx<R>* spec = static_cast<const Cplx<R>*>(a.spec) + (long long)(live ? y : 0) * a.Mp;
+  // Z[k] = E[k] + i O[k], E = (S[k] + S*[L-k]) / 2, O = (S[k] - S*[L-k]) / (2 W^k);
+  // the mean S[0] is excluded (it lives in phibar)
+  for (int k = tr; k < L; k += T) {
+    Cplx<R> z = {R(0), R(0)};
+    if (live) {
+      const Cplx<R> sk = (k == 0) ? Cplx<R>{R(0), R(0)} : spec[k];
+      const Cplx<R> sc = cconj(spec[L - k]);
+      const Cplx<R> E = {R(0.5) * (sk.re + sc.re), R(0.5) * (sk.im + sc.im)};
+      const Cplx<R> D = {R(0.5) * (sk.re - sc.re), R(0.5) * (sk.im - sc.im)};
+      const Cplx<R> O = cmul(D, cconj(stw[k]));  // D / W^k
+      z = {E.re - O.im, E.im + O.re};            // E + i O
+    }
+    A[pidx(k)] = z;
+  }
+  __syncthreads();
+  const Cplx<R>* zr = fft_rows<R>(A, B, L, T, tr, stw, true);
+  if (live) {
+    R* dphi = static_cast<R*>(a.dphi) + (long long)y * a.P;
+    const R inL = R(1) / (R)L;
+    for (int n = tr; n < L; n += T) {
+      const Cplx<R> v = zr[pidx(n)];
+      if constexpr (sizeof(R) == 4)
+        reinterpret_cast<float2*>(dphi)[n] = make_float2(v.re * inL, v.im * inL);
+      else
+        reinterpret_cast<double2*>(dphi)[n] = make_double2(v.re * inL, v.im * inL);
+    }
+  }
+}
+
+// ---------------------------------------------------------- mode systems ---
+// Thomas with unit off-diagonals and reciprocal pivots r_j:
+//   forward  d'_j = r_j (d_j - d'_{j-1})      (affine in d'_{j-1})
+//   backward x_j  = d'_j - r_j x_{j+1}         (affine in x_{j+1})
+// A CTA holds MB wavenumbers x Ny rows in shared memory; thread (chunk, mode)
+// composes the affine maps of its chunk of rows, the chunk maps are combined
+// in order, then each chunk is evaluated from its carried-in value.
+template <class R, int MB>
+__global__ void __launch_bounds__(256) k_modes_tile(PoissonArgs a) {
+  constexpr int CH = 256 / MB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R s_al[CH][MB];
+  __shared__ Cplx<R> s_br[CH][MB];
+  __shared__ Cplx<R> s_carry[CH][MB];
+  const int Ny = a.Ny, Mh = a.Mh, Mp = a.Mp;
+  const int m0 = blockIdx.x * MB;  // the m = 0 column of tile 0 holds zeros and is never stored
+  Cplx<R>* d = reinterpret_cast<Cplx<R>*>(smem_raw);                          // [Ny][MB]
+  R* rt = reinterpret_cast<R*>(smem_raw + (size_t)Ny * MB * sizeof(Cplx<R>));  // [Ny][MB]
+  Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec);
+  const R* __restrict__ rf = static_cast<const R*>(a.rfac);  // [Ny][Mp]
+  {
+    // stage both tiles with cp.async chunks (rows are Mp-pitched, 16-B aligned)
+    constexpr int CB = (MB * (int)sizeof(Cplx<R>) < 16) ? MB * (int)sizeof(Cplx<R>) : 16;
+    constexpr int RB = (MB * (int)sizeof(R) < 16) ? MB * (int)sizeof(R) : 16;
+    constexpr int CPR = MB * (int)sizeof(Cplx<R>) / CB;  // chunks per row, spectrum
+    constexpr int RPR = MB * (int)sizeof(R) / RB;        // chunks per row, pivots
+    constexpr int CE = CB / (int)sizeof(Cplx<R>) > 0 ? CB / (int)sizeof(Cplx<R>) : 1;
+    constexpr int RE = RB / (int)sizeof(R);
+    for (int idx = threadIdx.x; idx < Ny * CPR; idx += 256) {
+      const int j = idx / CPR, c = idx % CPR;
+      const int m = m0 + c * CE;
+      if (m < Mp) cp_async_chunk<CB>(d + j * MB + c * CE, spec + (long long)j * Mp + m);
+    }
+    for (int idx = threadIdx.x; idx < Ny * RPR; idx += 256) {
+      const int j = idx / RPR, c = idx % RPR;
+      const int m = m0 + c * RE;
+      if (m < Mp) cp_async_chunk<RB>(rt + j * MB + c * RE, rf + (long long)j * Mp + m);
+    }
+    cp_async_all();
+  }
+  __syncthreads();
+  const int mo = threadIdx.x % MB, ch = threadIdx.x / MB;
+  const int C = (Ny + CH - 1) / CH;
+  const int j0 = min(ch * C, Ny), j1 = min(j0 + C, Ny);
+  // forward: compose chunk map
+  R al = R(1);
+  Cplx<R> br = {R(0), R(0)};
+  for (int j = j0; j < j1; ++j) {
+    const R r = rt[j * MB + mo];
+    const Cplx<R> dj = d[j * MB + mo];
+    al = -r * al;
+    br = {r * (dj.re - br.re), r * (dj.im - br.im)};
+  }
+  s_al[ch][mo] = al;
+  s_br[ch][mo] = br;
+  __syncthreads();
+  if (threadIdx.x < MB) {  // carries: value entering each chunk
+    Cplx<R> v = {R(0), R(0)};
+    for (int c = 0; c < CH; ++c) {
+      s_carry[c][threadIdx.x] = v;
+      const R ac = s_al[c][threadIdx.x];
+      const Cplx<R> bc = s_br[c][threadIdx.x];
+      v = {ac * v.re + bc.re, ac * v.im + bc.im};
+    }
+  }
+  __syncthreads();
+  // forward evaluation; compose the backward chunk map on the way
+  Cplx<R> x = s_carry[ch][mo];
+  R ab = R(1);
+  Cplx<R> bb = {R(0), R(0)};
+  for (int j = j0; j < j1; ++j) {
+    const R r = rt[j * MB + mo];
+    const Cplx<R> dj = d[j * MB + mo];
+    x = {r * (dj.re - x.re), r * (dj.im - x.im)};
+    d[j * MB + mo] = x;
+    bb = {bb.re + ab * x.re, bb.im + ab * x.im};
+    ab = -ab * r;
+  }
+  __syncthreads();
+  s_al[ch][mo] = ab;
+  s_br[ch][mo] = bb;
+  __syncthreads();
+  if (threadIdx.x < MB) {  // value just above each chunk, from the top down
+    Cplx<R> v = {R(0), R(0)};
+    for (int c = CH - 1; c >= 0; --c) {
+      s_carry[c][threadIdx.x] = v;
+      const R ac = s_al[c][threadIdx.x];
+      const Cplx<R> bc = s_br[c][threadIdx.x];
+      v = {ac * v.re + bc.re, ac * v.im + bc.im};
+    }
+  }
+  __syncthreads();
+  x = s_carry[ch][mo];
+  for (int j = j1 - 1; j >= j0; --j) {
+    const R r = rt[j * MB + mo];
+    const Cplx<R> dj = d[j * MB + mo];
+    x = {dj.re - r * x.re, dj.im - r * x.im};
+    d[j * MB + mo] = x;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < Ny * MB; idx += 256) {
+    const int j = idx / MB, mo2 = idx % MB;
+    const int m = m0 + mo2;
+    if (m >= 1 && m < Mh) spec[(long long)j * Mp + m] = d[idx];
+  }
+}
+
+// Float-float ("double-single") numbers for the FP32 path: value = hi + lo
+// with |lo| <= ulp(hi)/2, about 48 significant bits, on the FP32 pipes (scalar
+// FP64 is slow on this part).  Error-free transformations: Knuth's two-sum
+// and the FMA two-product.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double ff_to(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+  const float h = p + e;
+  return {h, e - (h - p)};
+}
+__device__ __forceinline__ ff ff_shfl_up(ff a, int o) {
+  return {__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ ff ff_shfl_down(ff a, int o) {
+  return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// Mean-mode arithmetic: native double, or float-float.
+template <class R>
+struct MeanNum;
+template <>
+struct MeanNum<double> {
+  using T = double;
+  __device__ static T from(double v) { return v; }
+  __device__ static T from_f(float v) { return (double)v; }
+  __device__ static double to(T v) { return v; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static T mul(T a, T b) { return a * b; }
+  __device__ static T neg(T a) { return -a; }
+  __device__ static T up(T a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
+  __device__ static T down(T a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+};
+template <>
+struct MeanNum<float> {
+  using T = ff;
+  __device__ static T from(double v) { return ff_from(v); }
+  __device__ static T from_f(float v) { return {v, 0.0f}; }
+  __device__ static double to(T v) { return ff_to(v); }
+  __device__ static T add(T a, T b) { return ff_add(a, b); }
+  __device__ static T mul(T a, T b) { return ff_mul(a, b); }
+  __device__ static T neg(T a) { return ff_neg(a); }
+  __device__ static T up(T a, int o) { return ff_shfl_up(a, o); }
+  __device__ static T down(T a, int o) { return ff_shfl_down(a, o); }
+};
+
+// m = 0 (128 threads, one row chunk each; chunk maps combined by a warp
+// shuffle scan and a scan over the 4 warps) + the step's wall fluxes.
+// Arithmetic: FP64 on the plain FP64 path, float-float on the FP32 path.
+template <class R>
+__global__ void __launch_bounds__(128) k_mean_mode(PoissonArgs a) {
+  using N = MeanNum<R>;
+  using T = typename N::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T wa[4], wb[4], wc_in[4];
+  T* d = reinterpret_cast<T*>(smem_raw);  // [Ny] right-hand side, then solution
+  T* r = d + a.Ny;                        // [Ny] reciprocal pivots
+  const int Ny = a.Ny, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (a.flux_part) {
+    // FP64 totals of the wall fluxes: a shuffle tree over the strips
+    double qi = 0.0, qo = 0.0;
+    for (int b = t; b < a.nflux; b += 128) {
+      qi += a.flux_part[b];
+      qo += a.flux_part[a.nflux + b];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      qi += __shfl_down_sync(0xffffffffu, qi, o);
+      qo += __shfl_down_sync(0xffffffffu, qo, o);
+    }
+    __shared__ double fq[2][4];
+    if (lane == 0) {
+      fq[0][warp] = qi;
+      fq[1][warp] = qo;
+    }
+    __syncthreads();
+    if (t == 0) {
+      a.flux_acc[0] += (fq[0][0] + fq[0][1]) + (fq[0][2] + fq[0][3]);
+      a.flux_acc[1] += (fq[1][0] + fq[1][1]) + (fq[1][2] + fq[1][3]);
+    }
+  }
+  const float lift = (a.wall_mode == 0 ? 2.0f : 1.0f) * (float)a.Nx * (float)a.phi0;  // exact
+  for (int j = t; j < Ny; j += 128) {
+    T v, p;
+    if constexpr (sizeof(R) == 8) {
+      v = static_cast<const double*>(a.spec0)[j];
+      p = static_cast<const double*>(a.rfac0)[j];
+    } else {
+      const float2 sv = static_cast<const float2*>(a.spec0)[j], pv = static_cast<const float2*>(a.rfac0)[j];
+      v = {sv.x, sv.y};
+      p = {pv.x, pv.y};
+    }
+    if (j == 0) v = N::add(v, N::from_f(-lift));
+    d[j] = v;
+    r[j] = p;
+  }
+  __syncthreads();
+  const T one = N::from_f(1.0f), zero = N::from_f(0.0f);
+  const int C = (Ny + 127) >> 7;
+  const int j0 = min(t * C, Ny), j1 = min(j0 + C, Ny);
+  // forward elimination d'_j = r_j (d_j - d'_{j-1}): chunk map x -> al x + br
+  T al = one, br = zero;
+  for (int j = j0; j < j1; ++j) {
+    al = N::mul(N::neg(r[j]), al);
+    br = N::mul(r[j], N::add(d[j], N::neg(br)));
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const T a2 = N::up(al, o), b2 = N::up(br, o);
+    if (lane >= o) {
+      br = N::add(N::mul(al, b2), br);
+      al = N::mul(al, a2);
+    }
+  }
+  if (lane == 31) {
+    wa[warp] = al;
+    wb[warp] = br;
+  }
+  __syncthreads();
+  if (t == 0) {
+    T v = zero;
+    for (int w = 0; w < 4; ++w) {
+      wc_in[w] = v;
+      v = N::add(N::mul(wa[w], v), wb[w]);
+    }
+  }
+  __syncthreads();
+  T ex_a = N::up(al, 1), ex_b = N::up(br, 1);
+  if (lane == 0) {
+    ex_a = one;
+    ex_b = zero;
+  }
+  T x = N::add(N::mul(ex_a, wc_in[warp]), ex_b);
+  // evaluate; compose the back-substitution map x_j = d'_j - r_j x_{j+1}
+  T ab = one, bb = zero;
+  for (int j = j0; j < j1; ++j) {
+    x = N::mul(r[j], N::add(d[j], N::neg(x)));
+    d[j] = x;
+    bb = N::add(bb, N::mul(ab, x));
+    ab = N::mul(N::neg(ab), r[j]);
+  }
+  for (int o = 1; o < 32; o <<= 1) {
+    const T a2 = N::down(ab, o), b2 = N::down(bb, o);
+    if (lane + o < 32) {
+      bb = N::add(N::mul(ab, b2), bb);
+      ab = N::mul(ab, a2);
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    wa[warp] = ab;
+    wb[warp] = bb;
+  }
+  __syncthreads();
+  if (t == 0) {
+    T v = zero;
+    for (int w = 3; w >= 0; --w) {
+      wc_in[w] = v;
+      v = N::add(N::mul(wa[w], v), wb[w]);
+    }
+  }
+  __syncthreads();
+  T fa = N::down(ab, 1), fb = N::down(bb, 1);
+  if (lane == 31) {
+    fa = one;
+    fb = zero;
+  }
+  x = N::add(N::mul(fa, wc_in[warp]), fb);
+  for (int j = j1 - 1; j >= j0; --j) {
+    x = N::add(d[j], N::neg(N::mul(r[j], x)));
+    d[j] = x;
+  }
+  __syncthreads();
+  // phibar = x / Nx (Nx a power of two: exact scaling), E_y = -(phibar_{j+1} - phibar_{j-1}) / 2
+  const T inN = N::from_f(1.0f / (float)a.Nx);
+  R* Ebar = static_cast<R*>(a.Ebar);
+  const T half = N::from_f(0.5f);
+  const T phi0 = N::from_f((float)a.phi0);
+  for (int j = t; j < Ny; j += 128) {
+    const T pc = N::mul(d[j], inN);
+    const T pd = (j > 0) ? N::mul(d[j - 1], inN)
+                         : ((a.wall_mode == 0) ? N::add(N::add(phi0, phi0), N::neg(pc)) : phi0);
+    const T pu = (j < Ny - 1) ? N::mul(d[j + 1], inN) : ((a.wall_mode == 0) ? N::neg(pc) : zero);
+    const T ey = N::mul(N::neg(half), N::add(pu, N::neg(pd)));
+    if constexpr (sizeof(R) == 8) {
+      static_cast<double*>(a.phibar)[j] = pc;
+      Ebar[j] = ey;
+    } else {
+      static_cast<float2*>(a.phibar)[j] = make_float2(pc.hi, pc.lo);
+      Ebar[j] = ey.hi + ey.lo;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- launch ---
 namespace {
 
-int modes_warps_per_cta(int Ny, size_t cplx_bytes) {
-  const size_t per_warp = (size_t)Ny * cplx_bytes;
-  int w = (int)((200u * 1024u) / per_warp);
-  return w < 1 ? 1 : (w > 4 ? 4 : w);
+constexpr size_t kSmemCap = 200 * 1024;
+
+// wavenumbers per CTA: the spectrum and pivot tiles of all rows must fit
+int tile_modes(int Ny, size_t cbytes, size_t rbytes) {
+  int mb = 8;
+  while (mb > 1 && (size_t)Ny * mb * (cbytes + rbytes) > kSmemCap) mb >>= 1;
+  return mb;
 }
 
-template <class S, class R>
-cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s) {
-  const size_t row_smem = 2 * (size_t)a.Nx * sizeof(Cplx<R>);
-  k_rows_fwd<S, R><<<a.Ny, 256, row_smem, s>>>(a);
-  const int wpc = modes_warps_per_cta(a.Ny, sizeof(Cplx<R>));
-  const size_t mode_smem = (size_t)wpc * a.Ny * sizeof(Cplx<R>);
-  k_modes<R><<<(a.Mh + wpc - 1) / wpc, 32 * wpc, mode_smem, s>>>(a, wpc);
-  k_rows_inv<R><<<a.Ny, 256, row_smem, s>>>(a);
+template <class R>
+cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
+  const int mb = tile_modes(a.Ny, sizeof(Cplx<R>), sizeof(R));
+  const size_t sm = (size_t)a.Ny * mb * (sizeof(Cplx<R>) + sizeof(R));
+  const int nm = a.Mh;  // tiles start at m = 0
+  switch (mb) {
+    case 8: k_modes_tile<R, 8><<<(nm + 7) / 8, 256, sm, s>>>(a); break;
+    case 4: k_modes_tile<R, 4><<<(nm + 3) / 4, 256, sm, s>>>(a); break;
+    case 2: k_modes_tile<R, 2><<<(nm + 1) / 2, 256, sm, s>>>(a); break;
+    default: k_modes_tile<R, 1><<<nm, 256, sm, s>>>(a); break;
+  }
   return cudaGetLastError();
+}
+
+template <class R>
+size_t row_smem(int Nx) {
+  const int L = Nx / 2, T = (L >= 4) ? L / 4 : 1, rows = 256 / T;
+  return ((size_t)Nx + 2 * (size_t)rows * row_len_padded(L)) * sizeof(Cplx<R>);
+}
+
+template <class R>
+int row_blocks(int Nx, int Ny) {
+  const int L = Nx / 2, T = (L >= 4) ? L / 4 : 1, rows = 256 / T;
+  return (Ny + rows - 1) / rows;
+}
+
+template <class R>
+cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  k_rfft_rows<R><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (side) {
+    if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+  }
+  k_mean_mode<R><<<1, 128, 2 * (size_t)a.Ny * sizeof(typename MeanNum<R>::T), side ? side : s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (side && (e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+  if ((e = launch_modes<R>(a, s)) != cudaSuccess) return e;
+  k_irfft_rows<R><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (side && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 template <class K>
@@ -292,38 +688,48 @@ cudaError_t allow_max_dynamic_smem(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
-template <class S, class R>
+template <class R>
 cudaError_t set_attrs_t() {
-  cudaError_t e = allow_max_dynamic_smem(k_rows_fwd<S, R>);
-  if (e != cudaSuccess) return e;
-  e = allow_max_dynamic_smem(k_modes<R>);
-  if (e != cudaSuccess) return e;
-  return allow_max_dynamic_smem(k_rows_inv<R>);
+  cudaError_t e;
+  if ((e = allow_max_dynamic_smem(k_rfft_rows<R>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_irfft_rows<R>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_mean_mode<R>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2>)) != cudaSuccess) return e;
+  return allow_max_dynamic_smem(k_modes_tile<R, 1>);
+}
+
+template <class S, class R>
+cudaError_t rhoc_t(const void* g, long long plane, int Nx, int Ny, int P, const float* rch, void* rhoc,
+                   cudaStream_t s) {
+  k_rhoc<S, R><<<1216, 256, 0, s>>>(static_cast<const S*>(g), plane, Nx, Ny, P, rch, static_cast<R*>(rhoc));
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t poisson_set_attributes() {
-  cudaError_t e;
-  if ((e = set_attrs_t<double, double>()) != cudaSuccess) return e;
-  if ((e = set_attrs_t<double, float>()) != cudaSuccess) return e;
-  if ((e = set_attrs_t<float, float>()) != cudaSuccess) return e;
-  if ((e = set_attrs_t<__nv_bfloat16, float>()) != cudaSuccess) return e;
-  return set_attrs_t<__half, float>();
+  cudaError_t e = set_attrs_t<double>();
+  if (e != cudaSuccess) return e;
+  return set_attrs_t<float>();
 }
 
-cudaError_t launch_poisson(const PoissonArgs& a, int storage, bool real_f64, cudaStream_t s) {
-  if (real_f64) {
-    if (storage != 0) return cudaErrorInvalidValue;
-    return poisson_t<double, double>(a, s);
-  }
+cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f64, int Nx, int Ny, int P,
+                        const float* rch, void* rhoc, cudaStream_t s) {
+  if (real_f64) return storage == 0 ? rhoc_t<double, double>(g, plane, Nx, Ny, P, rch, rhoc, s) : cudaErrorInvalidValue;
   switch (storage) {
-    case 0: return poisson_t<double, float>(a, s);
-    case 1: return poisson_t<float, float>(a, s);
-    case 2: return poisson_t<__nv_bfloat16, float>(a, s);
-    case 3: return poisson_t<__half, float>(a, s);
+    case 0: return rhoc_t<double, float>(g, plane, Nx, Ny, P, rch, rhoc, s);
+    case 1: return rhoc_t<float, float>(g, plane, Nx, Ny, P, rch, rhoc, s);
+    case 2: return rhoc_t<__nv_bfloat16, float>(g, plane, Nx, Ny, P, rch, rhoc, s);
+    case 3: return rhoc_t<__half, float>(g, plane, Nx, Ny, P, rch, rhoc, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
+                           cudaEvent_t join) {
+  return real_f64 ? poisson_t<double>(a, s, side, fork, join) : poisson_t<float>(a, s, side, fork, join);
 }
 
 }  // namespace ehd

@@ -9,8 +9,8 @@
 //   neighbours (periodic x; halfway bounce-back of f on both walls;
 //   anti-bounce-back injection of rho0 and zero-gradient outflow of g).
 //   CTAs on the wall rows also sum the injected and collected charge.
-// K5 k_flux_reduce: adds the per-CTA wall fluxes, in a fixed order, to the
-//   run's FP64 accumulators.
+// The per-CTA wall fluxes are added, in a fixed order, to the run's FP64
+// totals by the mean-mode kernel of the Poisson solve that follows.
 //
 // Shifted storage (FP32 compute): f~_i = f_i - w_i and g~_i = g_i - w_i s(y)
 // with s(y) the hydrostatic charge of the row; the TRT collision is applied to
@@ -209,25 +209,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a, int rows) {
   }
 }
 
-// --------------------------------------------------------------------- K5 ---
-__global__ void k_flux_reduce(const double* __restrict__ part, int nxb, double* acc) {
-  if (threadIdx.x == 0) {
-    double qi = 0.0, qo = 0.0;
-    for (int b = 0; b < nxb; ++b) {
-      qi += part[b];
-      qo += part[nxb + b];
-    }
-    acc[0] += qi;
-    acc[1] += qo;
-  }
-}
-
 int step_flux_blocks(int Nx) { return (Nx + kStepThreads - 1) / kStepThreads; }
-
-cudaError_t launch_flux_reduce(const double* part, int nxb, double* acc, cudaStream_t s) {
-  k_flux_reduce<<<1, 32, 0, s>>>(part, nxb, acc);
-  return cudaGetLastError();
-}
 
 namespace {
 template <class S, class R>

@@ -222,3 +222,23 @@ def test_full_size_fp32_two_steps_vs_oracle():
     o.step(s, 2)
     e = _errors(p, run.fields(), o.fields(s))
     assert max(e.values()) <= 2e-5, e
+
+
+@gpu
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_march_and_node_parallel_forms_agree(storage, tol):
+    """The march form (warp walks a slab, pulls through registers, writes the
+    new charge) and the node-parallel push form compute the same step."""
+    ehd = _ehd()
+    w = wl.small_channel(256, seed=16)
+    p = o.setup(*w.args(), u_ion=5e-3)
+    r1 = ehd.Run(*w.args(), storage=storage, u_ion=5e-3, amp=w.amp, phase=w.phase, step_kernel=0)
+    r2 = ehd.Run(*w.args(), storage=storage, u_ion=5e-3, amp=w.amp, phase=w.phase, step_kernel=1)
+    r1.step(37)
+    r2.step(37)
+    e = _errors(p, r1.fields(), r2.fields())
+    assert max(e.values()) <= tol, e
+    d1, d2 = r1.diagnostics(), r2.diagnostics()
+    ftol = 1e-11 if storage == "f64" else 1e-6
+    assert d1["q_in"] == pytest.approx(d2["q_in"], rel=ftol)
+    assert d1["q_out"] == pytest.approx(d2["q_out"], rel=ftol)
