@@ -93,6 +93,10 @@ def lib():
         L.ehd_destroy.restype = None
         L.ehd_last_error.restype = ctypes.c_char_p
         L.ehd_set_allocator.argtypes = [vp, vp, vp]
+        L.ehd_tune.argtypes = [vp, ip, ip]
+        L.ehd_tune.restype = ctypes.c_int
+        L.ehd_tune_get.argtypes = [vp, ip]
+        L.ehd_tune_get.restype = ctypes.c_int
         L.ehd_poisson_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ip, vp, vp, vp]
         L.ehd_poisson_noalloc.restype = ctypes.c_int
         for name in ("ehd_create", "ehd_poisson", "ehd_step", "ehd_step_profile", "ehd_fields", "ehd_diagnostics",
@@ -210,6 +214,17 @@ def ehd_poisson_noalloc(Nx, Ny, eps, phi0, wall_mode, rhoc_ptr: int, phi_ptr: in
     _check(lib().ehd_poisson_noalloc(int(Nx), int(Ny), float(eps), float(phi0), int(wall_mode),
                                      ctypes.c_void_p(rhoc_ptr), ctypes.c_void_p(phi_ptr),
                                      ctypes.c_void_p(stream) if stream else None))
+
+
+TUNE = {"slab_rows": 1, "ring_depth": 2, "step_kernel": 3}
+
+
+def ehd_tune(h, param, value: int):
+    _check(lib().ehd_tune(h, TUNE[param] if isinstance(param, str) else int(param), int(value)))
+
+
+def ehd_tune_get(h, param) -> int:
+    return int(lib().ehd_tune_get(h, TUNE[param] if isinstance(param, str) else int(param)))
 
 
 def ehd_sync(h):

@@ -91,6 +91,7 @@ struct ehd_run {
   int rows = 1;        // rows per CTA of the node-parallel step kernel
   int step_kernel = 0; // 0 march form, 1 node-parallel push form
   int slab_rows = 4;   // rows per warp slab of the march form
+  int ring_depth = 3;  // rows staged ahead in the march form
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -192,6 +193,7 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.rhoc_out = r->rhoc;
   a.slab_rows = r->slab_rows;
   a.nstrips = r->nstrips;
+  a.ring_depth = r->ring_depth;
   return a;
 }
 
@@ -442,7 +444,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_ECUDA, "stream/event creation failed");
   }
   {
-    const cudaError_t e = poisson_set_attributes();
+    cudaError_t e = poisson_set_attributes();
+    if (e == cudaSuccess) e = march_set_attributes();
     if (e != cudaSuccess) {
       destroy_quiet(r);
       return fail(EHD_ECUDA, "setting the shared-memory limit of the Poisson kernels: %s", cudaGetErrorString(e));
@@ -468,7 +471,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->step_kernel = o.step_kernel;
   r->nstrips = march_strips(Nx);
   r->nxb = (r->step_kernel == 0) ? r->nstrips : step_flux_blocks(Nx);
-  r->flux_part = static_cast<double*>(run_alloc(r, 2 * r->nxb * sizeof(double)));
+  r->flux_part = static_cast<double*>(
+      run_alloc(r, 2 * (size_t)std::max(r->nstrips, step_flux_blocks(Nx)) * sizeof(double)));
   r->small = static_cast<double*>(run_alloc(r, 16 * sizeof(double) + 64));
   r->red_part = static_cast<double*>(run_alloc(r, (size_t)reduce_state_blocks() * 6 * sizeof(double)));
   bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->phibar && r->Ebar && r->spec && r->spec0 &&
@@ -598,6 +602,44 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   }
   *out = r;
   return EHD_OK;
+}
+
+ehd_status ehd_tune(ehd_run* r, int param, int value) {
+  if (!r) return fail(EHD_EINVAL, "run is NULL");
+  switch (param) {
+    case EHD_TUNE_SLAB_ROWS:
+      if (value < 1 || value > r->Ny) return fail(EHD_EINVAL, "slab rows must be in [1, Ny]");
+      r->slab_rows = value;
+      break;
+    case EHD_TUNE_RING_DEPTH:
+      if (value != 2 && value != 3 && value != 4 && value != 6) return fail(EHD_EINVAL, "ring depth must be 2, 3, 4 or 6");
+      r->ring_depth = value;
+      break;
+    case EHD_TUNE_STEP_KERNEL:
+      if (value != 0 && value != 1) return fail(EHD_EINVAL, "step kernel must be 0 or 1");
+      r->step_kernel = value;
+      r->nxb = (value == 0) ? r->nstrips : step_flux_blocks(r->Nx);
+      break;
+    default:
+      return fail(EHD_EINVAL, "unknown tuning parameter %d", param);
+  }
+  DeviceGuard dg(r->device);
+  for (int k = 0; k < 2; ++k)
+    if (r->graph[k]) {
+      cudaGraphExecDestroy(r->graph[k]);
+      r->graph[k] = nullptr;
+    }
+  return EHD_OK;
+}
+
+int ehd_tune_get(ehd_run* r, int param) {
+  if (!r) return -1;
+  switch (param) {
+    case EHD_TUNE_SLAB_ROWS: return r->slab_rows;
+    case EHD_TUNE_RING_DEPTH: return r->ring_depth;
+    case EHD_TUNE_STEP_KERNEL: return r->step_kernel;
+  }
+  return -1;
 }
 
 ehd_status ehd_poisson(ehd_run* r) {

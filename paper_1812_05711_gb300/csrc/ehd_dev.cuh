@@ -80,6 +80,7 @@ struct StepArgs {
   void* rhoc_out;            // R [Ny][P]: rho_c of the new state
   int slab_rows;             // rows per warp slab
   int nstrips;               // 32-column strips (30 owned columns each)
+  int ring_depth;            // rows staged ahead by cp.async (2, 3, 4 or 6)
 };
 
 struct PoissonArgs {
@@ -133,6 +134,7 @@ cudaError_t launch_step(const StepArgs& a, int storage, bool real_f64, int rows_
 int step_flux_blocks(int Nx);
 cudaError_t launch_march(const StepArgs& a, int storage, bool real_f64, cudaStream_t s);
 int march_strips(int Nx);
+cudaError_t march_set_attributes();
 // Poisson solve from the charge plane: forward row FFTs and the wavenumber
 // systems on s; the FP64 mean mode (and the wall-flux totals) on `side`
 // between the fork and join events when side != nullptr.
@@ -142,6 +144,11 @@ cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, 
 cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f64, int Nx, int Ny, int P,
                         const float* rch, void* rhoc, cudaStream_t s);
 cudaError_t poisson_set_attributes();
+// warp-per-row real FFTs (FP32 path, Nx = 128 ... 2048)
+bool fftw_supported(int Nx);
+cudaError_t fftw_set_tables();
+cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s);
+cudaError_t launch_irfft_warp(const PoissonArgs& a, cudaStream_t s);
 cudaError_t launch_fields(const FieldArgs& a, int storage, bool real_f64, unsigned mask, double* out,
                           cudaStream_t s);
 cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, double* part, int nblk,

@@ -71,18 +71,18 @@ __device__ __forceinline__ R from_right(R v) { return __shfl_down_sync(0xfffffff
 // lane-specific value (lane 0 / 31: the potential just outside the strip;
 // lane 1: the row's mean field; lanes 2-4: the charge shift of rows r, r+1,
 // r-1).
-template <class S>
+template <class S, int NSTAGE>
 struct MarchStages {
   static constexpr bool kAsync = sizeof(S) >= 4;
-  static constexpr int kN = sizeof(S) >= 8 ? 2 : 3;
+  static constexpr int kN = NSTAGE;
   static constexpr int kSlots = 20;
   static constexpr size_t kBytesPerWarp = kAsync ? (size_t)kN * kSlots * 32 * sizeof(S) : 0;
 };
 
-template <class S, class R>
+template <class S, class R, int NSTAGE>
 __global__ void __launch_bounds__(128) k_march(StepArgs a) {
   extern __shared__ __align__(16) unsigned char march_smem[];
-  using St = MarchStages<S>;
+  using St = MarchStages<S, NSTAGE>;
   constexpr int NST = St::kN;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -371,15 +371,55 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
 }
 
 namespace {
+template <class S, class R, int NST>
+cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
+  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
+  k_march<S, R, NST><<<(unsigned)((warps + 3) / 4), 128, 4 * MarchStages<S, NST>::kBytesPerWarp, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class S, class R>
 cudaError_t march_t(const StepArgs& a, cudaStream_t s) {
-  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
-  k_march<S, R><<<(unsigned)((warps + 3) / 4), 128, 4 * MarchStages<S>::kBytesPerWarp, s>>>(a);
-  return cudaGetLastError();
+  switch (a.ring_depth) {
+    case 2: return march_n<S, R, 2>(a, s);
+    case 4: return march_n<S, R, 4>(a, s);
+    case 6: return march_n<S, R, 6>(a, s);
+    default: return march_n<S, R, 3>(a, s);
+  }
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+template <class S, class R>
+cudaError_t attrs_t() {
+  cudaError_t e;
+  if ((e = allow_smem(k_march<S, R, 2>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march<S, R, 3>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march<S, R, 4>)) != cudaSuccess) return e;
+  return allow_smem(k_march<S, R, 6>);
 }
 }  // namespace
 
 int march_strips(int Nx) { return (Nx + 29) / 30; }
+
+cudaError_t march_set_attributes() {
+  cudaError_t e;
+  if ((e = attrs_t<double, double>()) != cudaSuccess) return e;
+  if ((e = attrs_t<double, float>()) != cudaSuccess) return e;
+  if ((e = attrs_t<float, float>()) != cudaSuccess) return e;
+  if ((e = attrs_t<__nv_bfloat16, float>()) != cudaSuccess) return e;
+  return attrs_t<__half, float>();
+}
 
 cudaError_t launch_march(const StepArgs& a, int storage, bool real_f64, cudaStream_t s) {
   if (real_f64) return storage == 0 ? march_t<double, double>(a, s) : cudaErrorInvalidValue;

@@ -658,8 +658,14 @@ int row_blocks(int Nx, int Ny) {
 
 template <class R>
 cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-  k_rfft_rows<R><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  const bool warp_fft = (sizeof(R) == 4) && fftw_supported(a.Nx);
+  cudaError_t e;
+  if (warp_fft) {
+    e = launch_rfft_warp(a, s);
+  } else {
+    k_rfft_rows<R><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   if (side) {
     if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
@@ -669,8 +675,13 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (side && (e = cudaEventRecord(join, side)) != cudaSuccess) return e;
   if ((e = launch_modes<R>(a, s)) != cudaSuccess) return e;
-  k_irfft_rows<R><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (warp_fft) {
+    e = launch_irfft_warp(a, s);
+  } else {
+    k_irfft_rows<R><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
   if (side && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -710,7 +721,9 @@ cudaError_t rhoc_t(const void* g, long long plane, int Nx, int Ny, int P, const 
 }  // namespace
 
 cudaError_t poisson_set_attributes() {
-  cudaError_t e = set_attrs_t<double>();
+  cudaError_t e = fftw_set_tables();
+  if (e != cudaSuccess) return e;
+  e = set_attrs_t<double>();
   if (e != cudaSuccess) return e;
   return set_attrs_t<float>();
 }
