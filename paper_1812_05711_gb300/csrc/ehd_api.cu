@@ -91,7 +91,8 @@ struct ehd_run {
   int rows = 1;        // rows per CTA of the node-parallel step kernel
   int step_kernel = 0; // 0 march form, 1 node-parallel push form
   int slab_rows = 4;   // rows per warp slab of the march form
-  int ring_depth = 3;  // rows staged ahead in the march form
+  int ring_depth = 2;  // rows staged ahead in the march form
+  int cols_per_lane = 2;
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -194,6 +195,7 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.slab_rows = r->slab_rows;
   a.nstrips = r->nstrips;
   a.ring_depth = r->ring_depth;
+  a.cols_per_lane = r->cols_per_lane;
   return a;
 }
 
@@ -469,10 +471,11 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->tw = run_alloc(r, (size_t)Nx * 2 * r->rsz);
   if (shifted) r->rch = static_cast<float*>(run_alloc(r, Ny * sizeof(float)));
   r->step_kernel = o.step_kernel;
-  r->nstrips = march_strips(Nx);
+  r->cols_per_lane = 2;
+  r->nstrips = march_strips(Nx, r->cols_per_lane);
   r->nxb = (r->step_kernel == 0) ? r->nstrips : step_flux_blocks(Nx);
   r->flux_part = static_cast<double*>(
-      run_alloc(r, 2 * (size_t)std::max(r->nstrips, step_flux_blocks(Nx)) * sizeof(double)));
+      run_alloc(r, 2 * (size_t)std::max(march_strips(Nx, 1), step_flux_blocks(Nx)) * sizeof(double)));
   r->small = static_cast<double*>(run_alloc(r, 16 * sizeof(double) + 64));
   r->red_part = static_cast<double*>(run_alloc(r, (size_t)reduce_state_blocks() * 6 * sizeof(double)));
   bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->phibar && r->Ebar && r->spec && r->spec0 &&
@@ -482,12 +485,14 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_ENOMEM, "device allocation failed");
   }
   r->err = reinterpret_cast<int*>(r->small + 16);
-  // march slabs: about 16 warps per SM in one wave, at least 4 rows each
+  // march slabs: as many warps as the GPU holds at once (one wave), at
+  // least 4 rows each
   {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
-    const long long target = 16LL * sms;
-    long long rows = ((long long)Ny * r->nstrips + target - 1) / target;
+    const long long resident =
+        (long long)sms * march_warps_per_sm(r->storage, r->real_f64, r->cols_per_lane, r->ring_depth);
+    long long rows = ((long long)Ny * r->nstrips + resident - 1) / resident;
     r->slab_rows = (int)std::max(4LL, std::min((long long)Ny, rows));
   }
   // rows per CTA of the node-parallel kernel: keep >= ~4 CTAs per SM
@@ -613,7 +618,15 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       break;
     case EHD_TUNE_RING_DEPTH:
       if (value != 2 && value != 3 && value != 4 && value != 6) return fail(EHD_EINVAL, "ring depth must be 2, 3, 4 or 6");
+      if (value == 6 && r->cols_per_lane == 2) return fail(EHD_EINVAL, "ring depth 6 needs one column per lane");
       r->ring_depth = value;
+      break;
+    case EHD_TUNE_COLS_PER_LANE:
+      if (value != 1 && value != 2) return fail(EHD_EINVAL, "columns per lane must be 1 or 2");
+      if (value == 2 && r->ring_depth == 6) r->ring_depth = 3;
+      r->cols_per_lane = value;
+      r->nstrips = march_strips(r->Nx, value);
+      if (r->step_kernel == 0) r->nxb = r->nstrips;
       break;
     case EHD_TUNE_STEP_KERNEL:
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "step kernel must be 0 or 1");
@@ -638,6 +651,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_SLAB_ROWS: return r->slab_rows;
     case EHD_TUNE_RING_DEPTH: return r->ring_depth;
     case EHD_TUNE_STEP_KERNEL: return r->step_kernel;
+    case EHD_TUNE_COLS_PER_LANE: return r->cols_per_lane;
   }
   return -1;
 }

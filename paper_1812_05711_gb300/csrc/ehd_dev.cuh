@@ -81,6 +81,7 @@ struct StepArgs {
   int slab_rows;             // rows per warp slab
   int nstrips;               // 32-column strips (30 owned columns each)
   int ring_depth;            // rows staged ahead by cp.async (2, 3, 4 or 6)
+  int cols_per_lane;         // 1: 32-column strips (30 owned); 2: 64-column strips (60 owned)
 };
 
 struct PoissonArgs {
@@ -133,7 +134,8 @@ __device__ __forceinline__ double load_phibar(const void* p, int j) {
 cudaError_t launch_step(const StepArgs& a, int storage, bool real_f64, int rows_per_cta, cudaStream_t s);
 int step_flux_blocks(int Nx);
 cudaError_t launch_march(const StepArgs& a, int storage, bool real_f64, cudaStream_t s);
-int march_strips(int Nx);
+int march_strips(int Nx, int cols_per_lane);
+int march_warps_per_sm(int storage, bool real_f64, int cols_per_lane, int ring_depth);
 cudaError_t march_set_attributes();
 // Poisson solve from the charge plane: forward row FFTs and the wavenumber
 // systems on s; the FP64 mean mode (and the wall-flux totals) on `side`

@@ -16,6 +16,8 @@
 // walls, anti-bounce-back injection of rho0 (with the wall drift mu_b E) and
 // zero-gradient outflow of g.  Halo rows (one below and one above the slab)
 // and halo columns are collided but not stored.
+#include <type_traits>
+
 #include "ehd_dev.cuh"
 
 namespace ehd {
@@ -370,6 +372,370 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Two columns per lane: a warp covers 64 columns (60 owned) and every lane
+// loads, collides and stores an adjacent pair of nodes (8-byte pairs in FP32
+// storage).  The x-shift of the post-collision pair needs one shuffle per
+// direction; the halo lanes' outer columns are never used, so their potential
+// neighbours need no extra load.
+template <class S>
+struct Pair;
+template <>
+struct Pair<float> {
+  template <class R>
+  __device__ static void st(float* p, R a, R b) { *reinterpret_cast<float2*>(p) = make_float2((float)a, (float)b); }
+  template <class R>
+  __device__ static void ld(const float* p, R& a, R& b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = (R)v.x;
+    b = (R)v.y;
+  }
+};
+template <>
+struct Pair<double> {
+  template <class R>
+  __device__ static void st(double* p, R a, R b) { *reinterpret_cast<double2*>(p) = make_double2((double)a, (double)b); }
+  template <class R>
+  __device__ static void ld(const double* p, R& a, R& b) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = (R)v.x;
+    b = (R)v.y;
+  }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+  template <class R>
+  __device__ static void st(__nv_bfloat16* p, R a, R b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn((float)a, (float)b);
+  }
+  template <class R>
+  __device__ static void ld(const __nv_bfloat16* p, R& a, R& b) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    a = (R)v.x;
+    b = (R)v.y;
+  }
+};
+template <>
+struct Pair<__half> {
+  template <class R>
+  __device__ static void st(__half* p, R a, R b) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn((float)a, (float)b); }
+  template <class R>
+  __device__ static void ld(const __half* p, R& a, R& b) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+    a = (R)v.x;
+    b = (R)v.y;
+  }
+};
+
+template <class S, class R, int NSTAGE>
+struct March2Stages {
+  static constexpr int kSlotBytes = 2 * (sizeof(S) > sizeof(R) ? sizeof(S) : sizeof(R));
+  static constexpr int kSlots = 20;
+  static constexpr size_t kBytesPerWarp = (size_t)NSTAGE * kSlots * 32 * kSlotBytes;
+};
+
+template <class S, class R>
+__device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R sy, R sf, R mub, R wp, R wm,
+                                             R cp, R cm, R gwp, R gwm, bool& bad) {
+  const R W0 = (R)kW0, W1 = (R)kW1, W2 = (R)kW2;
+  const R drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const R rho = sf + drho;
+  const R jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+  const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  const R drc = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  const R rc = sy + drc;
+  bad = !isfinite(drho) || !isfinite(drc);
+  const R Fx = rc * Ex, Fy = rc * Ey;
+  const R irho = R(1) / rho;
+  const R ux = (jx + R(0.5) * Fx) * irho;
+  const R uy = (jy + R(0.5) * Fy) * irho;
+  const R vx = ux + mub * Ex, vy = uy + mub * Ey;
+  const R usq15 = R(1.5) * (ux * ux + uy * uy);
+  const R uF3 = R(3) * (ux * Fx + uy * Fy);
+  f[0] = f[0] - wp * (f[0] - W0 * (drho - rho * usq15)) - cp * W0 * uF3;
+  trt_f2<R>(f[1], f[3], W1, drho, rho, ux, usq15, Fx, uF3, wp, wm, cp, cm);
+  trt_f2<R>(f[2], f[4], W1, drho, rho, uy, usq15, Fy, uF3, wp, wm, cp, cm);
+  trt_f2<R>(f[5], f[7], W2, drho, rho, ux + uy, usq15, Fx + Fy, uF3, wp, wm, cp, cm);
+  trt_f2<R>(f[6], f[8], W2, drho, rho, uy - ux, usq15, Fy - Fx, uF3, wp, wm, cp, cm);
+  const R vsq15 = R(1.5) * (vx * vx + vy * vy);
+  g[0] = g[0] - gwp * (g[0] - W0 * (drc - rc * vsq15));
+  trt_g2<R>(g[1], g[3], W1, drc, rc, vx, vsq15, gwp, gwm);
+  trt_g2<R>(g[2], g[4], W1, drc, rc, vy, vsq15, gwp, gwm);
+  trt_g2<R>(g[5], g[7], W2, drc, rc, vx + vy, vsq15, gwp, gwm);
+  trt_g2<R>(g[6], g[8], W2, drc, rc, vy - vx, vsq15, gwp, gwm);
+}
+
+template <class S, class R, int NSTAGE>
+__global__ void __launch_bounds__(128) k_march2(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char march_smem[];
+  using St = March2Stages<S, R, NSTAGE>;
+  constexpr int NST = NSTAGE, SL = St::kSlots, SB = St::kSlotBytes;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
+  const int strip = gw % ns, slab = gw / ns;
+  const int y0 = slab * a.slab_rows;
+  if (y0 >= Ny) return;  // whole warp
+  const int y1 = min(y0 + a.slab_rows, Ny);
+  const int xs = strip * 60;
+  const int xc = (xs - 2 + 2 * lane + 2 * Nx) % Nx;  // even: the pair (xc, xc + 1)
+  const bool owned = lane >= 1 && lane <= 30 && xs + 2 * (lane - 1) < Nx;
+  const long long pl = a.plane;
+  const S* __restrict__ fin = static_cast<const S*>(a.fin);
+  const S* __restrict__ gin = static_cast<const S*>(a.gin);
+  S* __restrict__ fo = static_cast<S*>(a.fout);
+  S* __restrict__ go = static_cast<S*>(a.gout);
+  R* __restrict__ rho_out = static_cast<R*>(a.rhoc_out);
+  const R* __restrict__ dphi = static_cast<const R*>(a.dphi);
+  const R* __restrict__ Ebar = static_cast<const R*>(a.Ebar);
+  const float* __restrict__ rch = a.rch;
+  const R wp = (R)a.wp, wm = (R)a.wm, gwp = (R)a.gwp, gwm = (R)a.gwm;
+  const R cp = R(1) - R(0.5) * wp, cm = R(1) - R(0.5) * wm;
+  const R mub = (R)a.mub, rho0 = (R)a.rho0, sf = (R)a.sf;
+  const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
+  const R W1 = (R)kW1, W2 = (R)kW2;
+  const int rs = max(y0 - 1, 0), re = min(y1, Ny - 1);
+
+  // carried rows, [k][j]: H (c_y = 0) of row r-1, U (c_y = +1) of rows r-1, r
+  R Hm[6][2] = {}, Um[6][2] = {}, Uc[6][2] = {};
+  R pm[2], pc[2];
+  {
+    const long long c = (long long)rs * P + xc;
+    pc[0] = dphi[c];
+    pc[1] = dphi[c + 1];
+    if (rs > 0) {
+      pm[0] = dphi[c - P];
+      pm[1] = dphi[c - P + 1];
+    } else {
+      pm[0] = gwall * pc[0];
+      pm[1] = gwall * pc[1];
+    }
+  }
+  double qin = 0.0, qout = 0.0;
+  bool bad = false;
+  unsigned char* ring = march_smem + (size_t)(threadIdx.x >> 5) * NST * SL * 32 * SB + (size_t)lane * SB;
+  auto slot = [&](int stage, int s) { return ring + ((size_t)stage * SL + s) * 32 * SB; };
+  auto issue = [&](int row_y, int stage) {
+    const long long c = (long long)row_y * P + xc;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      cp_async_elem<2 * sizeof(S)>(slot(stage, i), fin + i * pl + c);
+      cp_async_elem<2 * sizeof(S)>(slot(stage, 9 + i), gin + i * pl + c);
+    }
+    if (row_y + 1 < Ny) cp_async_elem<2 * sizeof(R)>(slot(stage, 18), dphi + c + P);
+    if (lane == 1) {
+      cp_async_elem<sizeof(R)>(slot(stage, 19), Ebar + row_y);
+    } else if (rch && lane == 2) {
+      cp_async_elem<4>(slot(stage, 19), rch + row_y);
+    } else if (rch && lane == 3 && row_y + 1 < Ny) {
+      cp_async_elem<4>(slot(stage, 19), rch + row_y + 1);
+    } else if (rch && lane == 4 && row_y > 0) {
+      cp_async_elem<4>(slot(stage, 19), rch + row_y - 1);
+    }
+  };
+#pragma unroll
+  for (int k = 0; k < NST - 1; ++k) {
+    if (rs + k <= re) issue(rs + k, k);
+    cp_async_commit();
+  }
+  for (int r = rs; r <= re; ++r) {
+    const long long row = (long long)r * P;
+    const int kk = r - rs;
+    if (r + NST - 1 <= re) issue(r + NST - 1, (kk + NST - 1) % NST);
+    cp_async_commit();
+    cp_async_wait<NST - 1>();
+    const int st = kk % NST;
+    R F[9][2], G[9][2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      Pair<S>::ld(reinterpret_cast<const S*>(slot(st, i)), F[i][0], F[i][1]);
+      Pair<S>::ld(reinterpret_cast<const S*>(slot(st, 9 + i)), G[i][0], G[i][1]);
+    }
+    R pn[2];
+    {
+      const R* nx = reinterpret_cast<const R*>(slot(st, 18));
+      pn[0] = (r + 1 < Ny) ? nx[0] : gwall * pc[0];
+      pn[1] = (r + 1 < Ny) ? nx[1] : gwall * pc[1];
+    }
+    const R ex_r = *reinterpret_cast<const R*>(slot(st, 19));
+    const float ex_f = *reinterpret_cast<const float*>(slot(st, 19));
+    const R Ebr = __shfl_sync(0xffffffffu, ex_r, 1);
+    const R sy = rch ? (R)__shfl_sync(0xffffffffu, ex_f, 2) : R(0);
+    const R s_up = (rch && r + 1 < Ny) ? (R)__shfl_sync(0xffffffffu, ex_f, 3) : sy;
+    const R s_dn = (rch && r > 0) ? (R)__shfl_sync(0xffffffffu, ex_f, 4) : sy;
+    // E = -grad phi at both nodes of the pair
+    const R pWl = from_left(pc[1]);   // phi(xc - 1)
+    const R pEr = from_right(pc[0]);  // phi(xc + 2)
+    const R Ex0 = R(-0.5) * (pc[1] - pWl), Ex1 = R(-0.5) * (pEr - pc[0]);
+    const R Ey0 = Ebr - R(0.5) * (pn[0] - pm[0]), Ey1 = Ebr - R(0.5) * (pn[1] - pm[1]);
+    R f0[9], g0[9], f1[9], g1[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      f0[i] = F[i][0];
+      g0[i] = G[i][0];
+      f1[i] = F[i][1];
+      g1[i] = G[i][1];
+    }
+    bool b0, b1;
+    collide_node<S, R>(f0, g0, Ex0, Ey0, sy, sf, mub, wp, wm, cp, cm, gwp, gwm, b0);
+    collide_node<S, R>(f1, g1, Ex1, Ey1, sy, sf, mub, wp, wm, cp, cm, gwp, gwm, b1);
+    if (owned && (b0 || b1)) bad = true;
+    // pulled values at (xc, xc + 1): x-shift by c_x
+    // c_x = +1 (1, 5, 8): [0] from the left lane's second node, [1] own first
+    // c_x = -1 (3, 6, 7): [0] own second node, [1] from the right lane's first
+    const R P1f0 = from_left(f1[1]), P5f0 = from_left(f1[5]), P8f0 = from_left(f1[8]);
+    const R P3f1 = from_right(f0[3]), P6f1 = from_right(f0[6]), P7f1 = from_right(f0[7]);
+    const R P1g0 = from_left(g1[1]), P5g0 = from_left(g1[5]), P8g0 = from_left(g1[8]);
+    const R P3g1 = from_right(g0[3]), P6g1 = from_right(g0[6]), P7g1 = from_right(g0[7]);
+    const R Pf1[2] = {P1f0, f0[1]}, Pf5[2] = {P5f0, f0[5]}, Pf8[2] = {P8f0, f0[8]};
+    const R Pf3[2] = {f1[3], P3f1}, Pf6[2] = {f1[6], P6f1}, Pf7[2] = {f1[7], P7f1};
+    const R Pg1[2] = {P1g0, g0[1]}, Pg5[2] = {P5g0, g0[5]}, Pg8[2] = {P8g0, g0[8]};
+    const R Pg3[2] = {g1[3], P3g1}, Pg6[2] = {g1[6], P6g1}, Pg7[2] = {g1[7], P7g1};
+    const R f0c[2] = {f0[0], f1[0]}, g0c[2] = {g0[0], g1[0]};
+    const R f2c[2] = {f0[2], f1[2]}, g2c[2] = {g0[2], g1[2]};
+    const R f4c[2] = {f0[4], f1[4]}, g4c[2] = {g0[4], g1[4]};
+    // own (unshifted) values used by the wall rules
+    const R f5c[2] = {f0[5], f1[5]}, f6c[2] = {f0[6], f1[6]}, f7c[2] = {f0[7], f1[7]}, f8c[2] = {f0[8], f1[8]};
+    const R g5c[2] = {g0[5], g1[5]}, g6c[2] = {g0[6], g1[6]}, g7c[2] = {g0[7], g1[7]}, g8c[2] = {g0[8], g1[8]};
+    R Un[6][2];
+    {
+      const R sh = sy - s_up;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        Un[0][j] = f2c[j];
+        Un[1][j] = Pf5[j];
+        Un[2][j] = Pf6[j];
+        Un[3][j] = g2c[j] + W1 * sh;
+        Un[4][j] = Pg5[j] + W2 * sh;
+        Un[5][j] = Pg6[j] + W2 * sh;
+      }
+    }
+    if (r == 0) {
+      // injector: bounce-back of f, anti-bounce-back of g (own node values)
+      const R Exs[2] = {Ex0, Ex1}, Eys[2] = {Ey0, Ey1};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const R wx = mub * Exs[j], wy = mub * Eys[j];
+        const R w15 = R(1.5) * (wx * wx + wy * wy);
+        const R c2 = wy, c5 = wx + wy, c6 = wy - wx;
+        const R n2 = -(g4c[j] + R(2) * W1 * sy) + R(2) * W1 * rho0 * (R(1) + R(4.5) * c2 * c2 - w15);
+        const R n5 = -(g7c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c5 * c5 - w15);
+        const R n6 = -(g8c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c6 * c6 - w15);
+        Uc[0][j] = f4c[j];
+        Uc[1][j] = f7c[j];
+        Uc[2][j] = f8c[j];
+        Uc[3][j] = n2;
+        Uc[4][j] = n5;
+        Uc[5][j] = n6;
+        if (owned && y0 == 0)
+          qin += (((double)Store<S>::rt(n2) - (double)Store<S>::rt(g4c[j])) +
+                  ((double)Store<S>::rt(n5) - (double)Store<S>::rt(g7c[j]))) +
+                 ((double)Store<S>::rt(n6) - (double)Store<S>::rt(g8c[j]));
+      }
+    }
+    if (r - 1 >= y0 && owned) {
+      // c_y = -1 completes row r - 1
+      const R sh = sy - s_dn;
+      const long long c = row - P + xc;
+      R n4[2], n7[2], n8[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        n4[j] = g4c[j] + W1 * sh;
+        n7[j] = Pg7[j] + W2 * sh;
+        n8[j] = Pg8[j] + W2 * sh;
+      }
+      Pair<S>::st(fo + c, Hm[0][0], Hm[0][1]);
+      Pair<S>::st(fo + pl + c, Hm[1][0], Hm[1][1]);
+      Pair<S>::st(fo + 2 * pl + c, Um[0][0], Um[0][1]);
+      Pair<S>::st(fo + 3 * pl + c, Hm[2][0], Hm[2][1]);
+      Pair<S>::st(fo + 4 * pl + c, f4c[0], f4c[1]);
+      Pair<S>::st(fo + 5 * pl + c, Um[1][0], Um[1][1]);
+      Pair<S>::st(fo + 6 * pl + c, Um[2][0], Um[2][1]);
+      Pair<S>::st(fo + 7 * pl + c, Pf7[0], Pf7[1]);
+      Pair<S>::st(fo + 8 * pl + c, Pf8[0], Pf8[1]);
+      Pair<S>::st(go + c, Hm[3][0], Hm[3][1]);
+      Pair<S>::st(go + pl + c, Hm[4][0], Hm[4][1]);
+      Pair<S>::st(go + 2 * pl + c, Um[3][0], Um[3][1]);
+      Pair<S>::st(go + 3 * pl + c, Hm[5][0], Hm[5][1]);
+      Pair<S>::st(go + 4 * pl + c, n4[0], n4[1]);
+      Pair<S>::st(go + 5 * pl + c, Um[4][0], Um[4][1]);
+      Pair<S>::st(go + 6 * pl + c, Um[5][0], Um[5][1]);
+      Pair<S>::st(go + 7 * pl + c, n7[0], n7[1]);
+      Pair<S>::st(go + 8 * pl + c, n8[0], n8[1]);
+      R q[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        q[j] = s_dn + (((Store<S>::rt(Hm[3][j]) + Store<S>::rt(Hm[4][j])) +
+                        (Store<S>::rt(Um[3][j]) + Store<S>::rt(Hm[5][j]))) +
+                       ((Store<S>::rt(n4[j]) + Store<S>::rt(Um[4][j])) +
+                        (Store<S>::rt(Um[5][j]) + Store<S>::rt(n7[j]))) +
+                       Store<S>::rt(n8[j]));
+      Pair<R>::st(rho_out + c, q[0], q[1]);
+    }
+    if (r == Ny - 1 && r >= y0 && r < y1 && owned) {
+      // collector: f bounces back; g leaves and re-enters from its own row
+      const long long c = row + xc;
+      Pair<S>::st(fo + c, f0c[0], f0c[1]);
+      Pair<S>::st(fo + pl + c, Pf1[0], Pf1[1]);
+      Pair<S>::st(fo + 2 * pl + c, Uc[0][0], Uc[0][1]);
+      Pair<S>::st(fo + 3 * pl + c, Pf3[0], Pf3[1]);
+      Pair<S>::st(fo + 4 * pl + c, f2c[0], f2c[1]);
+      Pair<S>::st(fo + 5 * pl + c, Uc[1][0], Uc[1][1]);
+      Pair<S>::st(fo + 6 * pl + c, Uc[2][0], Uc[2][1]);
+      Pair<S>::st(fo + 7 * pl + c, f5c[0], f5c[1]);
+      Pair<S>::st(fo + 8 * pl + c, f6c[0], f6c[1]);
+      Pair<S>::st(go + c, g0c[0], g0c[1]);
+      Pair<S>::st(go + pl + c, Pg1[0], Pg1[1]);
+      Pair<S>::st(go + 2 * pl + c, Uc[3][0], Uc[3][1]);
+      Pair<S>::st(go + 3 * pl + c, Pg3[0], Pg3[1]);
+      Pair<S>::st(go + 4 * pl + c, g4c[0], g4c[1]);
+      Pair<S>::st(go + 5 * pl + c, Uc[4][0], Uc[4][1]);
+      Pair<S>::st(go + 6 * pl + c, Uc[5][0], Uc[5][1]);
+      Pair<S>::st(go + 7 * pl + c, Pg7[0], Pg7[1]);
+      Pair<S>::st(go + 8 * pl + c, Pg8[0], Pg8[1]);
+      R q[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        q[j] = sy + (((Store<S>::rt(g0c[j]) + Store<S>::rt(Pg1[j])) + (Store<S>::rt(Uc[3][j]) + Store<S>::rt(Pg3[j]))) +
+                     ((Store<S>::rt(g4c[j]) + Store<S>::rt(Uc[4][j])) + (Store<S>::rt(Uc[5][j]) + Store<S>::rt(Pg7[j]))) +
+                     Store<S>::rt(Pg8[j]));
+        qout += ((double)Store<S>::rt(g2c[j]) + (double)Store<S>::rt(g5c[j])) + (double)Store<S>::rt(g6c[j]);
+        qout -= ((double)Store<S>::rt(g4c[j]) + (double)Store<S>::rt(g7c[j])) + (double)Store<S>::rt(g8c[j]);
+      }
+      Pair<R>::st(rho_out + c, q[0], q[1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      Hm[0][j] = f0c[j];
+      Hm[1][j] = Pf1[j];
+      Hm[2][j] = Pf3[j];
+      Hm[3][j] = g0c[j];
+      Hm[4][j] = Pg1[j];
+      Hm[5][j] = Pg3[j];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        Um[q][j] = Uc[q][j];
+        Uc[q][j] = Un[q][j];
+      }
+      pm[j] = pc[j];
+      pc[j] = pn[j];
+    }
+  }
+  cp_async_wait<0>();
+  if (bad) atomicOr(a.err, 1);
+  if (y0 == 0) {
+    double v = qin;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.flux_part[strip] = v;
+  }
+  if (y1 == Ny) {
+    double v = qout;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.flux_part[ns + strip] = v;
+  }
+}
+
 namespace {
 template <class S, class R, int NST>
 cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
@@ -378,8 +744,22 @@ cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class S, class R, int NST>
+cudaError_t march2_n(const StepArgs& a, cudaStream_t s) {
+  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
+  k_march2<S, R, NST><<<(unsigned)((warps + 3) / 4), 128, 4 * March2Stages<S, R, NST>::kBytesPerWarp, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class S, class R>
 cudaError_t march_t(const StepArgs& a, cudaStream_t s) {
+  if (a.cols_per_lane == 2) {
+    switch (a.ring_depth) {
+      case 2: return march2_n<S, R, 2>(a, s);
+      case 4: return march2_n<S, R, 4>(a, s);
+      default: return march2_n<S, R, 3>(a, s);
+    }
+  }
   switch (a.ring_depth) {
     case 2: return march_n<S, R, 2>(a, s);
     case 4: return march_n<S, R, 4>(a, s);
@@ -403,6 +783,9 @@ cudaError_t allow_smem(K kernel) {
 template <class S, class R>
 cudaError_t attrs_t() {
   cudaError_t e;
+  if ((e = allow_smem(k_march2<S, R, 2>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march2<S, R, 3>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march2<S, R, 4>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march<S, R, 2>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march<S, R, 3>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march<S, R, 4>)) != cudaSuccess) return e;
@@ -410,7 +793,34 @@ cudaError_t attrs_t() {
 }
 }  // namespace
 
-int march_strips(int Nx) { return (Nx + 29) / 30; }
+// Warps of the march kernel one SM holds at once (occupancy API).
+int march_warps_per_sm(int storage, bool real_f64, int cols_per_lane, int ring_depth) {
+  int blocks = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  auto occ = [&](auto kernel, size_t smem) { e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 128, smem); };
+  auto pick = [&](auto* sp, auto* rp) {
+    using S = std::remove_pointer_t<decltype(sp)>;
+    using R = std::remove_pointer_t<decltype(rp)>;
+    if (cols_per_lane == 2) {
+      if (ring_depth == 2) occ(k_march2<S, R, 2>, 4 * March2Stages<S, R, 2>::kBytesPerWarp);
+      else if (ring_depth == 4) occ(k_march2<S, R, 4>, 4 * March2Stages<S, R, 4>::kBytesPerWarp);
+      else occ(k_march2<S, R, 3>, 4 * March2Stages<S, R, 3>::kBytesPerWarp);
+    } else {
+      if (ring_depth == 2) occ(k_march<S, R, 2>, 4 * MarchStages<S, 2>::kBytesPerWarp);
+      else if (ring_depth == 4) occ(k_march<S, R, 4>, 4 * MarchStages<S, 4>::kBytesPerWarp);
+      else if (ring_depth == 6) occ(k_march<S, R, 6>, 4 * MarchStages<S, 6>::kBytesPerWarp);
+      else occ(k_march<S, R, 3>, 4 * MarchStages<S, 3>::kBytesPerWarp);
+    }
+  };
+  if (real_f64) pick((double*)nullptr, (double*)nullptr);
+  else if (storage == 0) pick((double*)nullptr, (float*)nullptr);
+  else if (storage == 1) pick((float*)nullptr, (float*)nullptr);
+  else if (storage == 2) pick((__nv_bfloat16*)nullptr, (float*)nullptr);
+  else pick((__half*)nullptr, (float*)nullptr);
+  return (e == cudaSuccess && blocks > 0) ? 4 * blocks : 16;
+}
+
+int march_strips(int Nx, int cols_per_lane) { return cols_per_lane == 2 ? (Nx + 59) / 60 : (Nx + 29) / 30; }
 
 cudaError_t march_set_attributes() {
   cudaError_t e;
