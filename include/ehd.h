@@ -31,7 +31,8 @@
 extern "C" {
 #endif
 
-typedef struct ehd_run ehd_run; /* opaque, owned by the library */
+typedef struct ehd_run ehd_run;     /* opaque, owned by the library */
+typedef struct ehd_batch ehd_batch; /* opaque, owned by the library */
 
 typedef enum {
   EHD_OK = 0,
@@ -219,6 +220,53 @@ ehd_status ehd_poisson_noalloc(int Nx, int Ny, double eps, double phi0,
 
 /* Free the run and its device memory (synchronises first).  NULL is a no-op. */
 void ehd_destroy(ehd_run* run);
+
+/* ------------------------------------------------------------------ batches
+ * A batch advances many runs of uneven sizes together (the paper runs one
+ * channel at a time; batching is this library's addition for parameter
+ * sweeps).  Every phase of the coupled step -- collide-and-stream, forward row
+ * FFT, FP32 wavenumber systems, float-float mean mode, inverse row FFT -- is
+ * one persistent kernel over work lists that cover all member runs; a tick of
+ * k steps is captured once per k as a CUDA graph.  Members must be
+ * FP32-storage, FP32-compute runs in the march form with 64 <= Nx <= max_nx,
+ * Ny <= max_ny.  Each member's result is the one it gets alone (the kernels
+ * are the single-run ones, applied per run). */
+
+/* Create a batch for up to max_runs runs (max_nx a power of two in
+ * [64, 2048], max_ny in [2, 4096]); stream = cudaStream_t or NULL for an own
+ * stream.  EHD_EINVAL / EHD_ENOMEM / EHD_ECUDA. */
+ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream,
+                            ehd_batch** out);
+
+/* Add a run with a budget of `steps` further steps.  Synchronises the run's
+ * own stream.  EHD_EBUSY if the batch is full; EHD_EINVAL for a run of the
+ * wrong kind or size, or one that is already in a batch.  While a member, the
+ * run is advanced only by ehd_batch_tick (ehd_step returns EHD_EBUSY); its
+ * fields, diagnostics and checkpoints stay readable. */
+ehd_status ehd_batch_add(ehd_batch* batch, ehd_run* run, long steps);
+
+/* Remove a run (synchronises the batch stream).  EHD_EINVAL if not a member. */
+ehd_status ehd_batch_remove(ehd_batch* batch, ehd_run* run);
+
+/* Advance every member by min(steps, its remaining budget); steps is even
+ * and >= 2.  Asynchronous on the batch stream. */
+ehd_status ehd_batch_tick(ehd_batch* batch, int steps);
+
+/* Steps a member still has in its budget (-1 if not a member). */
+long ehd_batch_remaining(ehd_batch* batch, ehd_run* run);
+
+/* Number of member runs (-1 for NULL). */
+int ehd_batch_size(ehd_batch* batch);
+
+/* Wait for the batch stream; EHD_EDIVERGED if a member holds a non-finite
+ * density or charge. */
+ehd_status ehd_batch_sync(ehd_batch* batch);
+
+/* The cudaStream_t the batch enqueues on. */
+void* ehd_batch_stream(ehd_batch* batch);
+
+/* Free the batch (synchronises); its members become ordinary runs. */
+void ehd_batch_destroy(ehd_batch* batch);
 
 /* Message of the last failure on this host thread ("" if none). */
 const char* ehd_last_error(void);

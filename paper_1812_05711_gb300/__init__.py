@@ -97,6 +97,21 @@ def lib():
         L.ehd_tune.restype = ctypes.c_int
         L.ehd_tune_get.argtypes = [vp, ip]
         L.ehd_tune_get.restype = ctypes.c_int
+        L.ehd_batch_create.argtypes = [ip, ip, ip, vp, ctypes.POINTER(vp)]
+        L.ehd_batch_add.argtypes = [vp, vp, ctypes.c_long]
+        L.ehd_batch_remove.argtypes = [vp, vp]
+        L.ehd_batch_tick.argtypes = [vp, ip]
+        L.ehd_batch_sync.argtypes = [vp]
+        for name in ("ehd_batch_create", "ehd_batch_add", "ehd_batch_remove", "ehd_batch_tick", "ehd_batch_sync"):
+            getattr(L, name).restype = ctypes.c_int
+        L.ehd_batch_remaining.argtypes = [vp, vp]
+        L.ehd_batch_remaining.restype = ctypes.c_long
+        L.ehd_batch_size.argtypes = [vp]
+        L.ehd_batch_size.restype = ctypes.c_int
+        L.ehd_batch_stream.argtypes = [vp]
+        L.ehd_batch_stream.restype = vp
+        L.ehd_batch_destroy.argtypes = [vp]
+        L.ehd_batch_destroy.restype = None
         L.ehd_poisson_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ip, vp, vp, vp]
         L.ehd_poisson_noalloc.restype = ctypes.c_int
         for name in ("ehd_create", "ehd_poisson", "ehd_step", "ehd_step_profile", "ehd_fields", "ehd_diagnostics",
@@ -342,3 +357,87 @@ class Run:
         g = np.empty((9, self.Ny, self.Nx))
         ehd_save(self.handle, f, g)
         return f, g
+
+
+# ------------------------------------------------------------------ batches
+def ehd_batch_create(max_runs, max_nx, max_ny, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ehd_batch_create(int(max_runs), int(max_nx), int(max_ny), stream, ctypes.byref(h)))
+    return h.value
+
+
+def ehd_batch_add(b, run_handle, steps):
+    _check(lib().ehd_batch_add(b, run_handle, int(steps)))
+
+
+def ehd_batch_remove(b, run_handle):
+    _check(lib().ehd_batch_remove(b, run_handle))
+
+
+def ehd_batch_tick(b, steps):
+    _check(lib().ehd_batch_tick(b, int(steps)))
+
+
+def ehd_batch_remaining(b, run_handle) -> int:
+    return int(lib().ehd_batch_remaining(b, run_handle))
+
+
+def ehd_batch_size(b) -> int:
+    return int(lib().ehd_batch_size(b))
+
+
+def ehd_batch_sync(b):
+    _check(lib().ehd_batch_sync(b))
+
+
+def ehd_batch_stream(b) -> int:
+    return lib().ehd_batch_stream(b) or 0
+
+
+def ehd_batch_destroy(b):
+    lib().ehd_batch_destroy(b)
+
+
+class Batch:
+    """Runs of uneven sizes advanced together (FP32 storage and compute)."""
+
+    def __init__(self, max_runs, max_nx=2048, max_ny=1680, stream=None, torch_stream=True):
+        self._stream_obj = None
+        if stream is None and torch_stream:
+            import torch
+            self._stream_obj = torch.cuda.Stream()
+            stream = self._stream_obj.cuda_stream
+        self.handle = ehd_batch_create(max_runs, max_nx, max_ny, stream)
+        self.members = {}
+
+    def add(self, run: "Run", steps: int):
+        ehd_batch_add(self.handle, run.handle, steps)
+        self.members[run.handle] = run
+
+    def remove(self, run: "Run"):
+        ehd_batch_remove(self.handle, run.handle)
+        self.members.pop(run.handle, None)
+
+    def tick(self, steps: int):
+        ehd_batch_tick(self.handle, steps)
+
+    def remaining(self, run: "Run") -> int:
+        return ehd_batch_remaining(self.handle, run.handle)
+
+    def __len__(self):
+        return ehd_batch_size(self.handle)
+
+    def sync(self):
+        ehd_batch_sync(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ehd_batch_destroy(self.handle)
+            self.handle = None
+            self.members = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -96,6 +97,32 @@ struct ehd_run {
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  ehd_batch* batch = nullptr;  // batch the run belongs to, if any
+};
+
+struct ehd_batch {
+  int device = 0, max_runs = 0, max_nx = 0, max_ny = 0, sms = 152;
+  cudaStream_t stream = nullptr, side = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_upload = nullptr;
+  std::vector<ehd_run*> members;
+  std::vector<long> remaining;
+  int slab_rows = 4;
+  // device tables and their pinned host staging copies
+  BatchRunDesc* d_runs = nullptr;
+  int4* d_march = nullptr;
+  int2* d_rows = nullptr;
+  int2* d_tiles = nullptr;
+  int* d_counts = nullptr;
+  BatchRunDesc* h_runs = nullptr;
+  int4* h_march = nullptr;
+  int2* h_rows = nullptr;
+  int2* h_tiles = nullptr;
+  int* h_counts = nullptr;
+  size_t cap_march = 0, cap_rows = 0, cap_tiles = 0;
+  bool dirty = true;
+  int grid_march = 0, grid_rows = 0, grid_tiles = 0, grid_mean = 0, modes_smem = 0;
+  std::map<int, cudaGraphExec_t> graphs;  // by tick length
 };
 
 namespace {
@@ -288,6 +315,7 @@ ehd_status build_graph(ehd_run* r, int cur) {
 }
 
 ehd_status check_err(ehd_run* r) {
+  if (r->batch) EHD_CK(cudaStreamSynchronize(r->batch->stream));
   int h = 0;
   EHD_CK(cudaMemcpyAsync(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
   EHD_CK(cudaStreamSynchronize(r->stream));
@@ -665,6 +693,7 @@ ehd_status ehd_poisson(ehd_run* r) {
 
 ehd_status ehd_step(ehd_run* r, long n) {
   if (!r) return fail(EHD_EINVAL, "run is NULL");
+  if (r->batch) return fail(EHD_EBUSY, "run is a member of a batch: advance it with ehd_batch_tick");
   if (n < 0) return fail(EHD_EINVAL, "negative step count");
   DeviceGuard dg(r->device);
   while (n >= kGraphSteps) {
@@ -736,6 +765,7 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
 
 ehd_status ehd_fields(ehd_run* r, unsigned mask, double* host_out) {
   if (!r) return fail(EHD_EINVAL, "run is NULL");
+  if (r->batch) EHD_CK(cudaStreamSynchronize(r->batch->stream));
   if (mask == 0 || (mask & ~EHD_FIELD_ALL)) return fail(EHD_EINVAL, "invalid field mask 0x%x", mask);
   if (!host_out) return fail(EHD_EINVAL, "host_out is NULL");
   DeviceGuard dg(r->device);
@@ -754,6 +784,7 @@ ehd_status ehd_fields(ehd_run* r, unsigned mask, double* host_out) {
 
 ehd_status ehd_diagnostics(ehd_run* r, double* out) {
   if (!r || !out) return fail(EHD_EINVAL, "NULL argument");
+  if (r->batch) EHD_CK(cudaStreamSynchronize(r->batch->stream));
   DeviceGuard dg(r->device);
   EHD_CK(launch_reduce_state(field_args(r), r->storage, r->real_f64, r->red_part, reduce_state_blocks(),
                              r->small + 2, r->err, r->stream));
@@ -801,6 +832,7 @@ ehd_status ehd_load(ehd_run* r, const double* f_host, const double* g_host) {
 
 ehd_status ehd_save(ehd_run* r, double* f_host, double* g_host) {
   if (!r) return fail(EHD_EINVAL, "run is NULL");
+  if (r->batch) EHD_CK(cudaStreamSynchronize(r->batch->stream));
   DeviceGuard dg(r->device);
   const size_t n = (size_t)r->Nx * r->Ny, plane = (size_t)r->Ny * r->P;
   const size_t sb = storage_bytes(r->storage);
@@ -843,6 +875,298 @@ ehd_status ehd_sync(ehd_run* r) {
 
 void* ehd_stream(ehd_run* r) { return r ? static_cast<void*>(r->stream) : nullptr; }
 
-void ehd_destroy(ehd_run* r) { destroy_quiet(r); }
+void ehd_destroy(ehd_run* r) {
+  if (r && r->batch) ehd_batch_remove(r->batch, r);
+  destroy_quiet(r);
+}
+
+}  // extern "C"
+
+// ===================================================================== batches
+namespace {
+
+template <class T>
+T* pinned(size_t n) {
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, n * sizeof(T) + 1, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+  return static_cast<T*>(p);
+}
+
+template <class T>
+T* devmem(size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, n * sizeof(T) + 256) != cudaSuccess) return nullptr;
+  return static_cast<T*>(p);
+}
+
+void batch_free(ehd_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (ehd_run* r : b->members) r->batch = nullptr;
+  cudaFree(b->d_runs);
+  cudaFree(b->d_march);
+  cudaFree(b->d_rows);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_counts);
+  cudaFreeHost(b->h_runs);
+  cudaFreeHost(b->h_march);
+  cudaFreeHost(b->h_rows);
+  cudaFreeHost(b->h_tiles);
+  cudaFreeHost(b->h_counts);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->ev_upload) cudaEventDestroy(b->ev_upload);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+BatchTables batch_tables(const ehd_batch* b) {
+  BatchTables t{};
+  t.runs = b->d_runs;
+  t.march_items = b->d_march;
+  t.row_items = b->d_rows;
+  t.tile_items = b->d_tiles;
+  t.counts = b->d_counts;
+  t.modes_smem = b->modes_smem;
+  return t;
+}
+
+// Work lists of the current membership; slab height chosen so the march
+// items of all members fill about one wave of resident warps.
+void batch_build_items(ehd_batch* b, int resident_warps) {
+  long long strip_rows = 0;
+  for (ehd_run* r : b->members) strip_rows += (long long)march_strips(r->Nx, 2) * r->Ny;
+  long long rows = (strip_rows + resident_warps - 1) / std::max(1, resident_warps);
+  b->slab_rows = (int)std::max(4LL, rows);
+  size_t nm = 0, nr = 0, nt = 0;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    ehd_run* r = b->members[i];
+    const int ns = march_strips(r->Nx, 2), nsl = (r->Ny + b->slab_rows - 1) / b->slab_rows;
+    for (int sl = 0; sl < nsl; ++sl)
+      for (int s = 0; s < ns; ++s) b->h_march[nm++] = make_int4((int)i, s, sl, 0);
+    for (int y = 0; y < r->Ny; ++y) b->h_rows[nr++] = make_int2((int)i, y);
+    for (int m0 = 0; m0 < r->Mh; m0 += kBatchTileModes) b->h_tiles[nt++] = make_int2((int)i, m0);
+  }
+  b->h_counts[0] = (int)b->members.size();
+  b->h_counts[1] = (int)nm;
+  b->h_counts[2] = (int)nr;
+  b->h_counts[3] = (int)nt;
+}
+
+ehd_status batch_capture(ehd_batch* b, int K, cudaGraphExec_t* out) {
+  const BatchTables t = batch_tables(b);
+  cudaGraph_t g = nullptr;
+  EHD_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < K && e == cudaSuccess; ++s) {
+    e = launch_batch_march(t, s, b->grid_march, b->stream);
+    if (e == cudaSuccess) e = launch_batch_rfft(t, s, b->grid_rows, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_batch_mean(t, s, b->grid_mean, b->side);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
+    if (e == cudaSuccess) e = launch_batch_modes(t, s, b->grid_tiles, b->stream);
+    if (e == cudaSuccess) e = launch_batch_irfft(t, s, b->grid_rows, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(EHD_ECUDA, "batch graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(EHD_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+  return EHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream, ehd_batch** out) {
+  if (!out) return fail(EHD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_runs < 1 || max_runs > 4096) return fail(EHD_EINVAL, "max_runs must be in [1, 4096]");
+  if (max_nx < 64 || max_nx > 2048 || (max_nx & (max_nx - 1)))
+    return fail(EHD_EINVAL, "max_nx must be a power of two in [64, 2048]");
+  if (max_ny < 2 || max_ny > 4096) return fail(EHD_EINVAL, "max_ny must be in [2, 4096]");
+  ehd_batch* b = new ehd_batch();
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    delete b;
+    return fail(EHD_ECUDA, "no CUDA device");
+  }
+  b->max_runs = max_runs;
+  b->max_nx = max_nx;
+  b->max_ny = max_ny;
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (stream) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+    b->own_stream = true;
+  }
+  if (!b->stream || cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming) != cudaSuccess) {
+    batch_free(b);
+    return fail(EHD_ECUDA, "stream/event creation failed");
+  }
+  {
+    cudaError_t e = poisson_set_attributes();
+    if (e == cudaSuccess) e = march_set_attributes();
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return fail(EHD_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    }
+  }
+  const size_t per_march = (size_t)march_strips(max_nx, 2) * (size_t)((max_ny + 3) / 4);
+  b->cap_march = (size_t)max_runs * per_march;
+  b->cap_rows = (size_t)max_runs * max_ny;
+  b->cap_tiles = (size_t)max_runs * ((max_nx / 2 + 1 + kBatchTileModes - 1) / kBatchTileModes);
+  b->d_runs = devmem<BatchRunDesc>(max_runs);
+  b->d_march = devmem<int4>(b->cap_march);
+  b->d_rows = devmem<int2>(b->cap_rows);
+  b->d_tiles = devmem<int2>(b->cap_tiles);
+  b->d_counts = devmem<int>(4);
+  b->h_runs = pinned<BatchRunDesc>(max_runs);
+  b->h_march = pinned<int4>(b->cap_march);
+  b->h_rows = pinned<int2>(b->cap_rows);
+  b->h_tiles = pinned<int2>(b->cap_tiles);
+  b->h_counts = pinned<int>(4);
+  if (!b->d_runs || !b->d_march || !b->d_rows || !b->d_tiles || !b->d_counts || !b->h_runs || !b->h_march ||
+      !b->h_rows || !b->h_tiles || !b->h_counts) {
+    batch_free(b);
+    return fail(EHD_ENOMEM, "batch table allocation failed");
+  }
+  const int wps = march_warps_per_sm(1, false, 2, 2);
+  b->grid_march = b->sms * std::max(1, wps / 4);
+  b->grid_rows = b->sms * 4;
+  b->grid_tiles = b->sms;
+  b->grid_mean = std::min(max_runs, b->sms);
+  // wavenumber tile (spectrum + pivots) of the tallest admissible run; the
+  // mean-mode solve needs less
+  b->modes_smem = max_ny * kBatchTileModes * (int)(sizeof(float2) + sizeof(float));
+  *out = b;
+  return EHD_OK;
+}
+
+ehd_status ehd_batch_add(ehd_batch* b, ehd_run* r, long steps) {
+  if (!b || !r) return fail(EHD_EINVAL, "NULL argument");
+  if (steps < 0) return fail(EHD_EINVAL, "negative step budget");
+  if (r->batch) return fail(EHD_EINVAL, "run is already in a batch");
+  if (r->storage != EHD_STORE_F32 || r->real_f64 || r->step_kernel != 0)
+    return fail(EHD_EINVAL, "batches take FP32-storage, FP32-compute runs in the march form");
+  if (r->Nx < 64 || r->Nx > b->max_nx || r->Ny > b->max_ny) return fail(EHD_EINVAL, "run size exceeds the batch limits");
+  if (r->device != b->device) return fail(EHD_EINVAL, "run and batch are on different devices");
+  if ((int)b->members.size() >= b->max_runs) return fail(EHD_EBUSY, "batch is full");
+  DeviceGuard dg(b->device);
+  EHD_CK(cudaStreamSynchronize(r->stream));
+  r->batch = b;
+  b->members.push_back(r);
+  b->remaining.push_back(steps);
+  b->dirty = true;
+  return EHD_OK;
+}
+
+ehd_status ehd_batch_remove(ehd_batch* b, ehd_run* r) {
+  if (!b || !r) return fail(EHD_EINVAL, "NULL argument");
+  auto it = std::find(b->members.begin(), b->members.end(), r);
+  if (it == b->members.end()) return fail(EHD_EINVAL, "run is not a member of this batch");
+  DeviceGuard dg(b->device);
+  EHD_CK(cudaStreamSynchronize(b->stream));
+  const size_t i = (size_t)(it - b->members.begin());
+  b->members.erase(it);
+  b->remaining.erase(b->remaining.begin() + i);
+  r->batch = nullptr;
+  b->dirty = true;
+  return EHD_OK;
+}
+
+ehd_status ehd_batch_tick(ehd_batch* b, int steps) {
+  if (!b) return fail(EHD_EINVAL, "batch is NULL");
+  if (steps < 2 || (steps & 1)) return fail(EHD_EINVAL, "a tick is an even number of steps >= 2");
+  DeviceGuard dg(b->device);
+  // the staging buffers of the previous tick must have been consumed
+  EHD_CK(cudaEventSynchronize(b->ev_upload));
+  if (b->dirty) {
+    const int wps = march_warps_per_sm(1, false, 2, 2);
+    batch_build_items(b, b->sms * wps);
+  }
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    ehd_run* r = b->members[i];
+    BatchRunDesc& d = b->h_runs[i];
+    for (int p = 0; p < 2; ++p) {
+      d.sa[p] = step_args(r, p);
+      d.sa[p].cols_per_lane = 2;
+      d.sa[p].ring_depth = 2;
+      d.sa[p].nstrips = march_strips(r->Nx, 2);
+      d.sa[p].slab_rows = b->slab_rows;
+    }
+    d.pa = poisson_args(r, true);
+    d.pa.nflux = d.sa[0].nstrips;
+    d.cur0 = r->cur;
+    d.remaining = (int)std::min<long>(steps, b->remaining[i]);
+    d.E = r->Nx / 64;
+  }
+  const size_t nrun = b->members.size();
+  if (nrun > 0) EHD_CK(cudaMemcpyAsync(b->d_runs, b->h_runs, nrun * sizeof(BatchRunDesc), cudaMemcpyHostToDevice, b->stream));
+  if (b->dirty) {
+    EHD_CK(cudaMemcpyAsync(b->d_counts, b->h_counts, 4 * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    if (b->h_counts[1] > 0)
+      EHD_CK(cudaMemcpyAsync(b->d_march, b->h_march, b->h_counts[1] * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+    if (b->h_counts[2] > 0)
+      EHD_CK(cudaMemcpyAsync(b->d_rows, b->h_rows, b->h_counts[2] * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    if (b->h_counts[3] > 0)
+      EHD_CK(cudaMemcpyAsync(b->d_tiles, b->h_tiles, b->h_counts[3] * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    b->dirty = false;
+  }
+  EHD_CK(cudaEventRecord(b->ev_upload, b->stream));
+  if (nrun == 0) return EHD_OK;
+  auto it = b->graphs.find(steps);
+  if (it == b->graphs.end()) {
+    cudaGraphExec_t ge = nullptr;
+    ehd_status st = batch_capture(b, steps, &ge);
+    if (st != EHD_OK) return st;
+    it = b->graphs.emplace(steps, ge).first;
+  }
+  EHD_CK(cudaGraphLaunch(it->second, b->stream));
+  for (size_t i = 0; i < nrun; ++i) {
+    ehd_run* r = b->members[i];
+    const long k = std::min<long>(steps, b->remaining[i]);
+    b->remaining[i] -= k;
+    r->step += k;
+    r->cur ^= (int)(k & 1);
+  }
+  return EHD_OK;
+}
+
+long ehd_batch_remaining(ehd_batch* b, ehd_run* r) {
+  if (!b || !r) return -1;
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (b->members[i] == r) return b->remaining[i];
+  return -1;
+}
+
+int ehd_batch_size(ehd_batch* b) { return b ? (int)b->members.size() : -1; }
+
+ehd_status ehd_batch_sync(ehd_batch* b) {
+  if (!b) return fail(EHD_EINVAL, "batch is NULL");
+  DeviceGuard dg(b->device);
+  EHD_CK(cudaStreamSynchronize(b->stream));
+  for (ehd_run* r : b->members) {
+    int h = 0;
+    EHD_CK(cudaMemcpy(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(EHD_EDIVERGED, "a member run holds a non-finite density or charge");
+  }
+  return EHD_OK;
+}
+
+void* ehd_batch_stream(ehd_batch* b) { return b ? static_cast<void*>(b->stream) : nullptr; }
+
+void ehd_batch_destroy(ehd_batch* b) { batch_free(b); }
 
 }  // extern "C"

@@ -129,6 +129,35 @@ __device__ __forceinline__ double load_phibar(const void* p, int j) {
   }
 }
 
+// ------------------------------------------------------------- batches ---
+// A batch advances many runs (FP32 storage and compute, march form) together:
+// each phase of the step is one persistent kernel over a work list that
+// covers every member run; the lists live in device memory, so membership
+// changes need no new launch configuration.
+struct BatchRunDesc {
+  StepArgs sa[2];    // [p]: step from buffer p to 1 - p
+  PoissonArgs pa;    // Poisson solve of the run (with its wall fluxes)
+  int cur0;          // buffer holding the state at the start of the tick
+  int remaining;     // steps the run still takes in this tick
+  int E;             // Nx / 64: warp-FFT shape
+  int pad;
+};
+struct BatchTables {
+  const BatchRunDesc* runs;
+  const int4* march_items;  // (run, strip, slab, 0)
+  const int2* row_items;    // (run, row)
+  const int2* tile_items;   // (run, first wavenumber)
+  const int* counts;        // device: [0] runs, [1] march items, [2] rows, [3] tiles
+  int modes_smem;           // tile bytes for the largest admissible Ny (fixed per batch)
+};
+// one launch of each phase for step t (0-based) of a tick
+cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, cudaStream_t s);
+cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStream_t s);
+cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStream_t s);
+cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s);
+cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s);
+constexpr int kBatchTileModes = 8;
+
 // Launchers (defined in the .cu files); storage: 0 F64, 1 F32, 2 BF16, 3 F16;
 // real_f64: compute type (true = double).
 cudaError_t launch_step(const StepArgs& a, int storage, bool real_f64, int rows_per_cta, cudaStream_t s);
@@ -146,7 +175,7 @@ cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, 
 cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f64, int Nx, int Ny, int P,
                         const float* rch, void* rhoc, cudaStream_t s);
 cudaError_t poisson_set_attributes();
-// warp-per-row real FFTs (FP32 path, Nx = 128 ... 2048)
+// warp-per-row real FFTs (FP32 path, Nx = 64 ... 2048)
 bool fftw_supported(int Nx);
 cudaError_t fftw_set_tables();
 cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s);

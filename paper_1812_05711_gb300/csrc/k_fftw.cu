@@ -1,5 +1,5 @@
 // k_fftw.cu -- warp-per-row real FFTs of the Poisson solve (FP32 path) for
-// rows of N = 64 E real samples, E in {2, 4, 8, 16, 32} (Nx = 128 ... 2048).
+// rows of N = 64 E real samples, E in {1, 2, 4, 8, 16, 32} (Nx = 64 ... 2048).
 //
 // A row of N reals is packed as L = N/2 = 32 E complex values z[n]
 // (Eq. 19 via the half-length transform) and transformed by the four-step
@@ -114,12 +114,10 @@ __device__ __forceinline__ void four_step(float (&re)[E], float (&im)[E], float 
 
 }  // namespace
 
+// Forward transform of row y by one warp; sm: the warp's E x 33 buffer.
 template <int E>
-__global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
-  __shared__ float2 smem[4][E * 33];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = blockIdx.x * 4 + warp;
-  if (y >= a.Ny) return;  // whole warp
+__device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, float2* sm) {
+  const int lane = threadIdx.x & 31;
   constexpr int L = 32 * E, N = 2 * L;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
   const float2* rc2 = reinterpret_cast<const float2*>(static_cast<const float*>(a.rhoc) + (long long)y * a.P);
@@ -158,7 +156,7 @@ __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
     }
   }
   float xr[32], xi[32];
-  four_step<E>(re, im, xr, xi, tw, smem[warp], lane);
+  four_step<E>(re, im, xr, xi, tw, sm, lane);
   // untangle into the half spectrum: S[k] = E_k + W_N^k O_k,
   // E_k = (Z[k] + Z*[L-k]) / 2, O_k = (Z[k] - Z*[L-k]) / (2i); lane k2 holds
   // k = k2 + E k1, whose partner L - k sits in lane (E - k2) mod E at 31 - k1
@@ -187,12 +185,10 @@ __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
   if (lane == 0) spec[L] = make_float2(xr[0] - xi[0], 0.0f);  // Nyquist: Re Z0 - Im Z0
 }
 
+// Inverse transform of row y by one warp -> phi minus its row mean.
 template <int E>
-__global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
-  __shared__ float2 smem[4][E * 33];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = blockIdx.x * 4 + warp;
-  if (y >= a.Ny) return;
+__device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, float2* sm) {
+  const int lane = threadIdx.x & 31;
   constexpr int L = 32 * E;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
   const float2* spec = static_cast<const float2*>(a.spec) + (long long)y * a.Mp;
@@ -214,13 +210,64 @@ __global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
     im[n2] = -(Ev.y + O.x);                                        // -Im: conjugate
   }
   float xr[32], xi[32];
-  four_step<E>(re, im, xr, xi, tw, smem[warp], lane);
+  four_step<E>(re, im, xr, xi, tw, sm, lane);
   if (lane < E) {
     float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(a.dphi) + (long long)y * a.P);
     const float inL = 1.0f / (float)L;
 #pragma unroll
     for (int k1 = 0; k1 < 32; ++k1) dphi2[lane + E * k1] = make_float2(xr[k1] * inL, -xi[k1] * inL);
   }
+}
+
+template <int E>
+__global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
+  __shared__ float2 smem[4][E * 33];
+  const int warp = threadIdx.x >> 5;
+  const int y = blockIdx.x * 4 + warp;
+  if (y < a.Ny) rfft_warp_body<E>(a, y, smem[warp]);
+}
+
+template <int E>
+__global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
+  __shared__ float2 smem[4][E * 33];
+  const int warp = threadIdx.x >> 5;
+  const int y = blockIdx.x * 4 + warp;
+  if (y < a.Ny) irfft_warp_body<E>(a, y, smem[warp]);
+}
+
+// Batch: warps of a fixed grid take row items (run, y); the row length picks
+// the transform shape.
+template <bool INV>
+__global__ void __launch_bounds__(128) k_batch_fft(BatchTables t, int step) {
+  __shared__ float2 smem[4][32 * 33];
+  const int warp = threadIdx.x >> 5;
+  const int nw = gridDim.x * 4;
+  const int n = t.counts[2];
+  for (int it = blockIdx.x * 4 + warp; it < n; it += nw) {
+    const int2 w = t.row_items[it];
+    const BatchRunDesc& rd = t.runs[w.x];
+    if (step >= rd.remaining) continue;
+    const PoissonArgs a = rd.pa;
+    float2* sm = smem[warp];
+    switch (rd.E) {
+      case 1: INV ? irfft_warp_body<1>(a, w.y, sm) : rfft_warp_body<1>(a, w.y, sm); break;
+      case 2: INV ? irfft_warp_body<2>(a, w.y, sm) : rfft_warp_body<2>(a, w.y, sm); break;
+      case 4: INV ? irfft_warp_body<4>(a, w.y, sm) : rfft_warp_body<4>(a, w.y, sm); break;
+      case 8: INV ? irfft_warp_body<8>(a, w.y, sm) : rfft_warp_body<8>(a, w.y, sm); break;
+      case 16: INV ? irfft_warp_body<16>(a, w.y, sm) : rfft_warp_body<16>(a, w.y, sm); break;
+      default: INV ? irfft_warp_body<32>(a, w.y, sm) : rfft_warp_body<32>(a, w.y, sm); break;
+    }
+  }
+}
+
+cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  k_batch_fft<false><<<grid, 128, 0, s>>>(t, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  k_batch_fft<true><<<grid, 128, 0, s>>>(t, step);
+  return cudaGetLastError();
 }
 
 cudaError_t fftw_set_tables() {
@@ -233,11 +280,12 @@ cudaError_t fftw_set_tables() {
   return cudaMemcpyToSymbol(c_w64, w64, sizeof w64);
 }
 
-bool fftw_supported(int Nx) { return Nx >= 128 && Nx <= 2048; }
+bool fftw_supported(int Nx) { return Nx >= 64 && Nx <= 2048; }
 
 cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
+    case 64: k_rfft_warp<1><<<g, 128, 0, s>>>(a); break;
     case 128: k_rfft_warp<2><<<g, 128, 0, s>>>(a); break;
     case 256: k_rfft_warp<4><<<g, 128, 0, s>>>(a); break;
     case 512: k_rfft_warp<8><<<g, 128, 0, s>>>(a); break;
@@ -251,6 +299,7 @@ cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
 cudaError_t launch_irfft_warp(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
+    case 64: k_irfft_warp<1><<<g, 128, 0, s>>>(a); break;
     case 128: k_irfft_warp<2><<<g, 128, 0, s>>>(a); break;
     case 256: k_irfft_warp<4><<<g, 128, 0, s>>>(a); break;
     case 512: k_irfft_warp<8><<<g, 128, 0, s>>>(a); break;

@@ -466,15 +466,14 @@ __device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R
   trt_g2<R>(g[6], g[8], W2, drc, rc, vy - vx, vsq15, gwp, gwm);
 }
 
+// One warp's walk over slab `slab` of strip `strip`; warp_ring is the warp's
+// NSTAGE-row staging area.  Shared by the single-run and the batch kernels.
 template <class S, class R, int NSTAGE>
-__global__ void __launch_bounds__(128) k_march2(StepArgs a) {
-  extern __shared__ __align__(16) unsigned char march_smem[];
+__device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int slab, unsigned char* warp_ring) {
   using St = March2Stages<S, R, NSTAGE>;
   constexpr int NST = NSTAGE, SL = St::kSlots, SB = St::kSlotBytes;
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
-  const int strip = gw % ns, slab = gw / ns;
   const int y0 = slab * a.slab_rows;
   if (y0 >= Ny) return;  // whole warp
   const int y1 = min(y0 + a.slab_rows, Ny);
@@ -514,7 +513,7 @@ __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
   }
   double qin = 0.0, qout = 0.0;
   bool bad = false;
-  unsigned char* ring = march_smem + (size_t)(threadIdx.x >> 5) * NST * SL * 32 * SB + (size_t)lane * SB;
+  unsigned char* ring = warp_ring + (size_t)lane * SB;
   auto slot = [&](int stage, int s) { return ring + ((size_t)stage * SL + s) * 32 * SB; };
   auto issue = [&](int row_y, int stage) {
     const long long c = (long long)row_y * P + xc;
@@ -736,6 +735,36 @@ __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
   }
 }
 
+template <class S, class R, int NSTAGE>
+__global__ void __launch_bounds__(128) k_march2(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char march_smem[];
+  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
+  march2_body<S, R, NSTAGE>(a, gw % a.nstrips, gw / a.nstrips,
+                            march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<S, R, NSTAGE>::kBytesPerWarp);
+}
+
+// Batch: every warp of a fixed grid takes march items (run, strip, slab) in
+// turn; runs whose budget in the tick is used up are skipped.
+__global__ void __launch_bounds__(128) k_batch_march(BatchTables t, int step) {
+  extern __shared__ __align__(16) unsigned char march_smem[];
+  constexpr int NST = 2;
+  unsigned char* ring = march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<float, float, NST>::kBytesPerWarp;
+  const int nw = gridDim.x * 4;
+  const int n = t.counts[1];
+  for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < n; it += nw) {
+    const int4 w = t.march_items[it];
+    const BatchRunDesc& rd = t.runs[w.x];
+    if (step >= rd.remaining) continue;  // whole warp
+    const StepArgs a = rd.sa[rd.cur0 ^ (step & 1)];
+    march2_body<float, float, NST>(a, w.y, w.z, ring);
+  }
+}
+
+cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  k_batch_march<<<grid, 128, 4 * March2Stages<float, float, 2>::kBytesPerWarp, s>>>(t, step);
+  return cudaGetLastError();
+}
+
 namespace {
 template <class S, class R, int NST>
 cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
@@ -783,6 +812,7 @@ cudaError_t allow_smem(K kernel) {
 template <class S, class R>
 cudaError_t attrs_t() {
   cudaError_t e;
+  if ((e = allow_smem(k_batch_march)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 2>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 3>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 4>)) != cudaSuccess) return e;

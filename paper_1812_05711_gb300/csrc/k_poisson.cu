@@ -312,14 +312,23 @@ __global__ void __launch_bounds__(256) k_irfft_rows(PoissonArgs a) {
 // composes the affine maps of its chunk of rows, the chunk maps are combined
 // in order, then each chunk is evaluated from its carried-in value.
 template <class R, int MB>
-__global__ void __launch_bounds__(256) k_modes_tile(PoissonArgs a) {
+struct TileScratch {
+  R al[256 / MB][MB];
+  Cplx<R> br[256 / MB][MB];
+  Cplx<R> carry[256 / MB][MB];
+};
+
+// One CTA solves wavenumbers m0 .. m0 + MB - 1 of run a (smem_raw: tile
+// storage, ts: chunk-map scratch).  The m = 0 column of tile 0 holds zeros
+// and is never stored.
+template <class R, int MB>
+__device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, unsigned char* smem_raw,
+                                                TileScratch<R, MB>& ts) {
   constexpr int CH = 256 / MB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ R s_al[CH][MB];
-  __shared__ Cplx<R> s_br[CH][MB];
-  __shared__ Cplx<R> s_carry[CH][MB];
+  auto& s_al = ts.al;
+  auto& s_br = ts.br;
+  auto& s_carry = ts.carry;
   const int Ny = a.Ny, Mh = a.Mh, Mp = a.Mp;
-  const int m0 = blockIdx.x * MB;  // the m = 0 column of tile 0 holds zeros and is never stored
   Cplx<R>* d = reinterpret_cast<Cplx<R>*>(smem_raw);                          // [Ny][MB]
   R* rt = reinterpret_cast<R*>(smem_raw + (size_t)Ny * MB * sizeof(Cplx<R>));  // [Ny][MB]
   Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec);
@@ -411,6 +420,13 @@ __global__ void __launch_bounds__(256) k_modes_tile(PoissonArgs a) {
   }
 }
 
+template <class R, int MB>
+__global__ void __launch_bounds__(256) k_modes_tile(PoissonArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TileScratch<R, MB> ts;
+  modes_tile_body<R, MB>(a, blockIdx.x * MB, smem_raw, ts);
+}
+
 // Float-float ("double-single") numbers for the FP32 path: value = hi + lo
 // with |lo| <= ulp(hi)/2, about 48 significant bits, on the FP32 pipes (scalar
 // FP64 is slow on this part).  Error-free transformations: Knuth's two-sum
@@ -476,11 +492,18 @@ struct MeanNum<float> {
 // shuffle scan and a scan over the 4 warps) + the step's wall fluxes.
 // Arithmetic: FP64 on the plain FP64 path, float-float on the FP32 path.
 template <class R>
-__global__ void __launch_bounds__(128) k_mean_mode(PoissonArgs a) {
+struct MeanScratch {
+  typename MeanNum<R>::T wa[4], wb[4], wc_in[4];
+  double fq[2][4];
+};
+
+template <class R>
+__device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned char* smem_raw, MeanScratch<R>& ms) {
   using N = MeanNum<R>;
   using T = typename N::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T wa[4], wb[4], wc_in[4];
+  auto& wa = ms.wa;
+  auto& wb = ms.wb;
+  auto& wc_in = ms.wc_in;
   T* d = reinterpret_cast<T*>(smem_raw);  // [Ny] right-hand side, then solution
   T* r = d + a.Ny;                        // [Ny] reciprocal pivots
   const int Ny = a.Ny, t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -495,7 +518,7 @@ __global__ void __launch_bounds__(128) k_mean_mode(PoissonArgs a) {
       qi += __shfl_down_sync(0xffffffffu, qi, o);
       qo += __shfl_down_sync(0xffffffffu, qo, o);
     }
-    __shared__ double fq[2][4];
+    auto& fq = ms.fq;
     if (lane == 0) {
       fq[0][warp] = qi;
       fq[1][warp] = qo;
@@ -618,6 +641,41 @@ __global__ void __launch_bounds__(128) k_mean_mode(PoissonArgs a) {
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(128) k_mean_mode(PoissonArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MeanScratch<R> ms;
+  mean_mode_body<R>(a, smem_raw, ms);
+}
+
+// Batch kernels: CTAs take (run, tile) items / one CTA per run.
+__global__ void __launch_bounds__(256) k_batch_modes(BatchTables t, int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TileScratch<float, kBatchTileModes> ts;
+  const int n = t.counts[3];
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = t.tile_items[it];
+    const BatchRunDesc& rd = t.runs[w.x];
+    if (step >= rd.remaining) continue;  // whole CTA
+    const PoissonArgs a = rd.pa;
+    modes_tile_body<float, kBatchTileModes>(a, w.y, smem_raw, ts);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(128) k_batch_mean(BatchTables t, int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MeanScratch<float> ms;
+  const int n = t.counts[0];
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const BatchRunDesc& rd = t.runs[r];
+    if (step >= rd.remaining) continue;
+    const PoissonArgs a = rd.pa;
+    mean_mode_body<float>(a, smem_raw, ms);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- launch ---
 namespace {
 
@@ -720,9 +778,21 @@ cudaError_t rhoc_t(const void* g, long long plane, int Nx, int Ny, int P, const 
 
 }  // namespace
 
+cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  k_batch_modes<<<grid, 256, t.modes_smem, s>>>(t, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  k_batch_mean<<<grid, 128, t.modes_smem, s>>>(t, step);
+  return cudaGetLastError();
+}
+
 cudaError_t poisson_set_attributes() {
   cudaError_t e = fftw_set_tables();
   if (e != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_modes)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_mean)) != cudaSuccess) return e;
   e = set_attrs_t<double>();
   if (e != cudaSuccess) return e;
   return set_attrs_t<float>();

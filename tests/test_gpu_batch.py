@@ -1,0 +1,90 @@
+"""Batches: runs of uneven sizes advanced together by the batch phase
+kernels give, run by run, exactly the state the run reaches alone (the same
+per-run arithmetic), whatever else is in the batch and however budgets end
+inside a tick."""
+import numpy as np
+import pytest
+
+import workloads as wl
+
+gpu = pytest.mark.gpu
+
+
+def _ehd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1812_05711_gb300 as ehd
+    return ehd
+
+
+def _mk(ehd, w):
+    return ehd.Run(*w.args(), storage="f32", u_ion=5e-3, amp=w.amp, phase=w.phase)
+
+
+@gpu
+def test_batch_members_match_alone_bitwise():
+    ehd = _ehd()
+    specs = [(64, 150.0, 5.0, 23), (128, 175.0, 10.0, 40), (256, 200.0, 20.0, 17), (512, 240.0, 10.0, 30),
+             (128, 260.0, 5.0, 40)]
+    ws = []
+    for k, (nx, T, C, steps) in enumerate(specs):
+        a, ph = wl.roll(300 + k, 1e-3)
+        ws.append((wl.Workload(f"b{k}", nx, wl.ny_for(nx), T, C=C, amp=a, phase=ph), steps))
+    batch = ehd.Batch(8, max_nx=512, max_ny=wl.ny_for(512))
+    members = []
+    for w, steps in ws:
+        r = _mk(ehd, w)
+        batch.add(r, steps)
+        members.append(r)
+    ticks = 0
+    while any(batch.remaining(r) > 0 for r in members):
+        batch.tick(4)
+        ticks += 1
+    batch.sync()
+    assert ticks == 10
+    for (w, steps), r in zip(ws, members):
+        alone = _mk(ehd, w)
+        alone.step(steps)
+        assert r.params()["Nx"] == w.Nx
+        fa, ga = alone.save()
+        fb, gb = r.save()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), w.name
+        A, B = alone.fields(), r.fields()
+        for k in A:
+            assert np.array_equal(A[k], B[k]), (w.name, k)
+        da, db = alone.diagnostics(), r.diagnostics()
+        assert da["q_in"] == db["q_in"] and da["q_out"] == db["q_out"]
+        assert db["step"] == steps
+    batch.close()
+
+
+@gpu
+def test_batch_membership_changes_between_ticks():
+    ehd = _ehd()
+    a0, p0 = wl.roll(401, 1e-3)
+    a1, p1 = wl.roll(402, 1e-3)
+    w0 = wl.Workload("m0", 128, 104, 190.0, amp=a0, phase=p0)
+    w1 = wl.Workload("m1", 256, 208, 210.0, amp=a1, phase=p1)
+    batch = ehd.Batch(2, max_nx=256, max_ny=208)
+    r0, r1 = _mk(ehd, w0), _mk(ehd, w1)
+    batch.add(r0, 12)
+    batch.tick(6)
+    batch.add(r1, 8)            # joins mid-way
+    with pytest.raises(ehd.EhdError) as ei:
+        batch.add(_mk(ehd, w0), 4)  # full
+    assert ei.value.status == -6
+    batch.tick(6)
+    batch.remove(r0)            # r0 done (12 steps)
+    batch.tick(2)
+    batch.sync()
+    assert batch.remaining(r1) == 0 and len(batch) == 1
+    with pytest.raises(ehd.EhdError):
+        r1.step(1)              # members are advanced by the batch only
+    for w, r, n in ((w0, r0, 12), (w1, r1, 8)):
+        alone = _mk(ehd, w)
+        alone.step(n)
+        assert np.array_equal(alone.fields()["phi"], r.fields()["phi"]), w.name
+        assert np.array_equal(alone.save()[1], r.save()[1]), w.name
+    batch.close()
+    r1.step(2)                  # an ordinary run again
