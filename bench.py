@@ -278,6 +278,227 @@ def run_ours(args):
     return 0
 
 
+def _cells(w):
+    return w.Nx * w.Ny
+
+
+def run_batch(args):
+    """64 runs of uneven sizes advanced together (FP32), launch shapes from the
+    autotuner; metric: aggregate GLUPS over all runs."""
+    import torch
+
+    import paper_1812_05711_gb300 as ehd
+    from paper_1812_05711_gb300 import autotune
+
+    torch.cuda.set_device(0)
+    ws = wl.batch_workloads(seed=4, n=64)
+    K = args.steps
+    max_nx, max_ny = 512, wl.ny_for(512)
+    # tune on a throwaway copy of the batch (tuning consumes step budget)
+    tb = ehd.Batch(len(ws), max_nx, max_ny)
+    truns = [ehd.Run(*w.args(), storage="f32", amp=w.amp, phase=w.phase) for w in ws]
+    for r in truns:
+        tb.add(r, 10 ** 9)
+    rec = autotune.tune(tb, steps=8, ticks=3, use_cache=False)
+    params = rec["params"]
+    tb.close()
+    for r in truns:
+        r.close()
+    batch = ehd.Batch(len(ws), max_nx, max_ny)
+    batch.tune(**params)
+    runs = [ehd.Run(*w.args(), storage="f32", amp=w.amp, phase=w.phase) for w in ws]
+    inits = [r.save() for r in runs]
+    for r in runs:
+        batch.add(r, K + args.warmup * args.tick)
+    stream = torch.cuda.ExternalStream(ehd.ehd_batch_stream(batch.handle))
+    for _ in range(args.warmup):
+        batch.tick(args.tick)
+    batch.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ticks = (K + args.tick - 1) // args.tick
+    e0.record(stream)
+    for _ in range(ticks):
+        batch.tick(args.tick)
+    e1.record(stream)
+    batch.sync()
+    ms = e0.elapsed_time(e1)
+    cells = sum(_cells(w) for w in ws)
+    value = cells * K / (ms * 1e-3) / 1e9
+    # end to end: host initial states in, K steps, four fields of every run out
+    for r in runs:
+        batch.remove(r)
+    pins = []
+    for f0, g0 in inits:
+        pf = torch.empty(f0.shape, dtype=torch.float64, pin_memory=True).numpy()
+        pg = torch.empty(g0.shape, dtype=torch.float64, pin_memory=True).numpy()
+        pf[...] = f0
+        pg[...] = g0
+        pins.append((pf, pg))
+    outs = [torch.empty((4, w.Ny, w.Nx), dtype=torch.float64, pin_memory=True).numpy() for w in ws]
+    mask = ehd.FIELD_BITS["rho"] | ehd.FIELD_BITS["ux"] | ehd.FIELD_BITS["uy"] | ehd.FIELD_BITS["rho_c"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, (pf, pg) in zip(runs, pins):
+        ehd.ehd_load(r.handle, pf, pg)
+        batch.add(r, K)
+    for _ in range(ticks):
+        batch.tick(args.tick)
+    batch.sync()
+    for r, o in zip(runs, outs):
+        ehd.ehd_fields(r.handle, mask, o)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(pf.nbytes + pg.nbytes for pf, pg in pins) / K
+    d2h = sum(o.nbytes for o in outs) / K
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, n, el = _oracle_glups(ws[0], budget_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} oracle steps of member 0 ({ws[0].Nx}x{ws[0].Ny}) in {el:.1f} s"}
+    sizes = {}
+    for w in ws:
+        sizes[f"{w.Nx}x{w.Ny}"] = sizes.get(f"{w.Nx}x{w.Ny}", 0) + 1
+    line = {"metric": "batched coupled-step GLUPS", "value": value, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / ticks / args.tick, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch-64-uneven", "runs": len(ws), "sizes": sizes, "tick": args.tick,
+                       "tuning": params, "tuner_us_per_step": rec["us_per_step"]},
+            "roofline": None,
+            "e2e": {"value": cells * K / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 5 * ticks * args.tick, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
+def run_serve(args):
+    """Poisson-arrival stream of stability-sweep requests through the
+    continuous-batching server; the plain FP64 one-at-a-time path serves a
+    bounded prefix of the same stream for comparison."""
+    import torch
+
+    from paper_1812_05711_gb300 import serve
+
+    torch.cuda.set_device(0)
+    stream = wl.serving_stream(seed=5, n=args.requests, rate=20.0)
+    reqs = [serve.Request(k, w.Nx, w.Ny, w.T, w.C, w.M, w.Fe, w.Lambda, w.steps, w.amp, w.phase, arrival=t)
+            for k, (t, w) in enumerate(stream)]
+    budget = int(args.hbm_gb * 1e9)
+    srv = serve.Server(budget, max_runs=256, tick_steps=args.tick, max_nx=1024, max_ny=wl.ny_for(1024))
+    res = srv.serve(reqs, realtime=True)
+    srv.close()
+    cells = {r.rid: r.Nx * r.Ny for r in reqs}
+    summ = serve.summarize(res, cells_of=lambda r: cells[r.rid])
+    # comparison: plain FP64, one run at a time, on the first requests of the
+    # same stream (bounded by time); the server again on the same prefix
+    prefix = reqs[:args.fp64_requests]
+    base = serve.summarize(serve.serve_plain_fp64(prefix, realtime=True), cells_of=lambda r: cells[r.rid])
+    srv2 = serve.Server(budget, max_runs=256, tick_steps=args.tick, max_nx=1024, max_ny=wl.ny_for(1024))
+    pref = serve.summarize(srv2.serve([serve.Request(**{**q.__dict__}) for q in prefix], realtime=True),
+                           cells_of=lambda r: cells[r.rid])
+    srv2.close()
+    line = {"metric": "served runs/s", "value": summ["runs_per_s"], "unit": "runs/s", "n_gpus": 1,
+            "steps": int(sum(q.steps for q in reqs)), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve-poisson-{args.requests}req-20per_s", "tick": args.tick,
+                       "hbm_budget_gb": args.hbm_gb},
+            "latency": {"p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_s": summ["mean_s"]},
+            "served_glups": summ.get("glups"), "makespan_s": summ["makespan_s"],
+            "prefix_compare": {"requests": len(prefix), "batched_fp32": pref, "plain_fp64_one_at_a_time": base},
+            "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fp64(args):
+    """Plain FP64 single run (128x104, T = 200, 10,000 steps) on the GPU and
+    the FP64 oracle on the host, same steps."""
+    import torch
+
+    import paper_1812_05711_gb300 as ehd
+
+    torch.cuda.set_device(0)
+    w = wl.plain_fp64_channel()
+    K = args.steps
+    run = ehd.Run(*w.args(), storage="f64", amp=w.amp, phase=w.phase)
+    run.step(args.warmup)
+    run.sync()
+    stream = torch.cuda.ExternalStream(ehd.ehd_stream(run.handle))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run.step(K)
+    e1.record(stream)
+    run.sync()
+    ms = e0.elapsed_time(e1)
+    value = _cells(w) * K / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, n, el = _oracle_glups(w, budget_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"{n} oracle steps in {el:.1f} s"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "Nx": w.Nx, "Ny": w.Ny, "storage": "f64", "compute": "f64"},
+            "roofline": None, "e2e": None, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision(args):
+    """1024x840, T = 170: every storage (FP64 / FP32 / BF16 / FP16, FP32
+    compute) against the plain FP64 GPU path after K steps, and against the
+    FP64 oracle after a short prefix; GLUPS of each."""
+    import torch
+
+    import oracle as o
+    import paper_1812_05711_gb300 as ehd
+
+    torch.cuda.set_device(0)
+    w = wl.precision_channel()
+    K = args.steps
+    p = o.setup(*w.args())
+    scale = {"rho": 1.0, "ux": p.u_ion, "uy": p.u_ion, "rho_c": p.rho0, "phi": 1.0, "Ex": 1.0 / p.H, "Ey": 1.0 / p.H}
+
+    def err(a, b):
+        return {k: float(np.abs(a[k] - b[k]).max() / scale[k]) for k in a}
+
+    short = args.oracle_steps
+    s = o.init_state(p, w.amp, w.phase)
+    o.step(s, short)
+    ora = o.fields(s)
+    ref = ehd.Run(*w.args(), storage="f64", amp=w.amp, phase=w.phase)
+    ref.step(short)
+    ref_short = ref.fields()
+    ref.step(K - short)
+    ref_long = ref.fields()
+    ref.close()
+    table = {"f64_plain_vs_oracle_at_%d" % short: max(err(ref_short, ora).values())}
+    rows = {}
+    for st in ("f64", "f32", "bf16", "f16"):
+        r = ehd.Run(*w.args(), storage=st, compute="f32", amp=w.amp, phase=w.phase)
+        r.step(short)
+        e_short = err(r.fields(), ora)
+        stream = torch.cuda.ExternalStream(ehd.ehd_stream(r.handle))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.step(K - short)
+        e1.record(stream)
+        r.sync()
+        ms = e0.elapsed_time(e1)
+        e_long = err(r.fields(), ref_long)
+        rows[st] = {"glups": _cells(w) * (K - short) / (ms * 1e-3) / 1e9,
+                    f"max_scaled_err_vs_oracle_at_{short}": max(e_short.values()),
+                    f"scaled_err_vs_gpu_fp64_at_{K}": e_long}
+        r.close()
+    line = {"metric": METRIC, "value": rows["f32"]["glups"], "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": short, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "Nx": w.Nx, "Ny": w.Ny, "compute": "f32"},
+            "precision": rows, "reference": table, "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,11 +508,27 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="channel", choices=["channel", "batch", "serve", "fp64", "precision"],
+                    help="channel: 2048x1680 headline (default); batch: 64 uneven runs; serve: request stream; "
+                         "fp64: 128x104 plain FP64; precision: 1024x840 storage variants")
+    ap.add_argument("--tick", type=int, default=100, help="steps per batch tick (batch / serve)")
+    ap.add_argument("--requests", type=int, default=200, help="requests in the serving stream")
+    ap.add_argument("--fp64-requests", type=int, default=4, help="prefix served by the plain FP64 path")
+    ap.add_argument("--hbm-gb", type=float, default=200.0, help="HBM budget of the server")
+    ap.add_argument("--oracle-steps", type=int, default=50, help="precision: steps compared with the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "fp64":
+        return run_fp64(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 

@@ -265,6 +265,20 @@ ehd_status ehd_batch_sync(ehd_batch* batch);
 /* The cudaStream_t the batch enqueues on. */
 void* ehd_batch_stream(ehd_batch* batch);
 
+/* Launch-shape tuning of a batch (results unchanged): EHD_BATCH_SLAB_ROWS
+ * (rows per march warp item; 0 = chosen from the membership so the march
+ * items fill about one wave), EHD_BATCH_MARCH_CTAS / EHD_BATCH_ROW_CTAS /
+ * EHD_BATCH_TILE_CTAS (fixed grid of the persistent march, row-FFT and
+ * wavenumber kernels).  Drops the captured graphs.  EHD_EINVAL otherwise. */
+#define EHD_BATCH_SLAB_ROWS 1
+#define EHD_BATCH_MARCH_CTAS 2
+#define EHD_BATCH_ROW_CTAS 3
+#define EHD_BATCH_TILE_CTAS 4
+ehd_status ehd_batch_tune(ehd_batch* batch, int param, int value);
+
+/* Current value of a batch tuning parameter (-1 if unknown). */
+int ehd_batch_tune_get(ehd_batch* batch, int param);
+
 /* Free the batch (synchronises); its members become ordinary runs. */
 void ehd_batch_destroy(ehd_batch* batch);
 

@@ -110,6 +110,10 @@ def lib():
         L.ehd_batch_size.restype = ctypes.c_int
         L.ehd_batch_stream.argtypes = [vp]
         L.ehd_batch_stream.restype = vp
+        L.ehd_batch_tune.argtypes = [vp, ip, ip]
+        L.ehd_batch_tune.restype = ctypes.c_int
+        L.ehd_batch_tune_get.argtypes = [vp, ip]
+        L.ehd_batch_tune_get.restype = ctypes.c_int
         L.ehd_batch_destroy.argtypes = [vp]
         L.ehd_batch_destroy.restype = None
         L.ehd_poisson_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ip, vp, vp, vp]
@@ -394,6 +398,17 @@ def ehd_batch_stream(b) -> int:
     return lib().ehd_batch_stream(b) or 0
 
 
+BATCH_TUNE = {"slab_rows": 1, "march_ctas": 2, "row_ctas": 3, "tile_ctas": 4}
+
+
+def ehd_batch_tune(b, param, value):
+    _check(lib().ehd_batch_tune(b, BATCH_TUNE[param] if isinstance(param, str) else int(param), int(value)))
+
+
+def ehd_batch_tune_get(b, param) -> int:
+    return int(lib().ehd_batch_tune_get(b, BATCH_TUNE[param] if isinstance(param, str) else int(param)))
+
+
 def ehd_batch_destroy(b):
     lib().ehd_batch_destroy(b)
 
@@ -429,6 +444,13 @@ class Batch:
 
     def sync(self):
         ehd_batch_sync(self.handle)
+
+    def tune(self, **params):
+        for k, v in params.items():
+            ehd_batch_tune(self.handle, k, v)
+
+    def tuning(self) -> dict:
+        return {k: ehd_batch_tune_get(self.handle, k) for k in BATCH_TUNE}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -122,6 +122,7 @@ struct ehd_batch {
   size_t cap_march = 0, cap_rows = 0, cap_tiles = 0;
   bool dirty = true;
   int grid_march = 0, grid_rows = 0, grid_tiles = 0, grid_mean = 0, modes_smem = 0;
+  int slab_rows_fixed = 0;  // 0: choose from the membership
   std::map<int, cudaGraphExec_t> graphs;  // by tick length
 };
 
@@ -940,7 +941,7 @@ void batch_build_items(ehd_batch* b, int resident_warps) {
   long long strip_rows = 0;
   for (ehd_run* r : b->members) strip_rows += (long long)march_strips(r->Nx, 2) * r->Ny;
   long long rows = (strip_rows + resident_warps - 1) / std::max(1, resident_warps);
-  b->slab_rows = (int)std::max(4LL, rows);
+  b->slab_rows = b->slab_rows_fixed > 0 ? b->slab_rows_fixed : (int)std::max(4LL, rows);
   size_t nm = 0, nr = 0, nt = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {
     ehd_run* r = b->members[i];
@@ -1166,6 +1167,43 @@ ehd_status ehd_batch_sync(ehd_batch* b) {
 }
 
 void* ehd_batch_stream(ehd_batch* b) { return b ? static_cast<void*>(b->stream) : nullptr; }
+
+ehd_status ehd_batch_tune(ehd_batch* b, int param, int value) {
+  if (!b) return fail(EHD_EINVAL, "batch is NULL");
+  switch (param) {
+    case EHD_BATCH_SLAB_ROWS:
+      if (value < 0 || value > b->max_ny) return fail(EHD_EINVAL, "slab rows must be in [0, max_ny]");
+      b->slab_rows_fixed = value;
+      b->dirty = true;
+      break;
+    case EHD_BATCH_MARCH_CTAS:
+    case EHD_BATCH_ROW_CTAS:
+    case EHD_BATCH_TILE_CTAS:
+      if (value < 1 || value > 65535) return fail(EHD_EINVAL, "CTA count must be in [1, 65535]");
+      if (param == EHD_BATCH_MARCH_CTAS) b->grid_march = value;
+      if (param == EHD_BATCH_ROW_CTAS) b->grid_rows = value;
+      if (param == EHD_BATCH_TILE_CTAS) b->grid_tiles = value;
+      break;
+    default:
+      return fail(EHD_EINVAL, "unknown batch tuning parameter %d", param);
+  }
+  DeviceGuard dg(b->device);
+  EHD_CK(cudaStreamSynchronize(b->stream));
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  return EHD_OK;
+}
+
+int ehd_batch_tune_get(ehd_batch* b, int param) {
+  if (!b) return -1;
+  switch (param) {
+    case EHD_BATCH_SLAB_ROWS: return b->slab_rows_fixed > 0 ? b->slab_rows_fixed : b->slab_rows;
+    case EHD_BATCH_MARCH_CTAS: return b->grid_march;
+    case EHD_BATCH_ROW_CTAS: return b->grid_rows;
+    case EHD_BATCH_TILE_CTAS: return b->grid_tiles;
+  }
+  return -1;
+}
 
 void ehd_batch_destroy(ehd_batch* b) { batch_free(b); }
 
