@@ -41,7 +41,7 @@ UNIT = "GLUPS"
 # kernels per coupled step: collide-stream (march form, writes the charge),
 # forward row FFT, FP64 mean mode, wavenumber systems, inverse row FFT
 LAUNCHES_PER_STEP = 5
-K4_BYTES_PER_NODE = {"f32": 36 * 4 + 4, "f64": 36 * 8 + 8, "bf16": 36 * 2 + 4, "f16": 36 * 2 + 4}
+K4_BYTES_PER_NODE = {"f32": 36 * 4 + 8, "f64": 36 * 8 + 16, "bf16": 36 * 2 + 8, "f16": 36 * 2 + 8}
 
 
 def _peaks():

@@ -141,13 +141,16 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * warp of the march form walks, 1..Ny), EHD_TUNE_RING_DEPTH (rows staged
  * ahead by cp.async: 2, 3, 4 or 6; with 2 columns per lane only 2, 3, 4),
  * EHD_TUNE_STEP_KERNEL (0 march form, 1 node-parallel form),
- * EHD_TUNE_COLS_PER_LANE (march form: 1 or 2 adjacent nodes per lane).
+ * EHD_TUNE_COLS_PER_LANE (march form: 1 or 2 adjacent nodes per lane),
+ * EHD_TUNE_TILE_MODES (wavenumbers per CTA of the mode solve: 1, 2, 4, 8;
+ * 0 = the largest whose tile fits in shared memory).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
 #define EHD_TUNE_RING_DEPTH 2
 #define EHD_TUNE_STEP_KERNEL 3
 #define EHD_TUNE_COLS_PER_LANE 4
+#define EHD_TUNE_TILE_MODES 5
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

@@ -94,6 +94,7 @@ struct ehd_run {
   int slab_rows = 4;   // rows per warp slab of the march form
   int ring_depth = 2;  // rows staged ahead in the march form
   int cols_per_lane = 2;
+  int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -250,6 +251,7 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.flux_part = with_flux ? r->flux_part : nullptr;
   a.nflux = r->nxb;
   a.flux_acc = r->small;
+  a.tile_modes = r->tile_modes;
   return a;
 }
 
@@ -650,6 +652,11 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       if (value == 6 && r->cols_per_lane == 2) return fail(EHD_EINVAL, "ring depth 6 needs one column per lane");
       r->ring_depth = value;
       break;
+    case EHD_TUNE_TILE_MODES:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+        return fail(EHD_EINVAL, "tile modes must be 0, 1, 2, 4 or 8");
+      r->tile_modes = value;
+      break;
     case EHD_TUNE_COLS_PER_LANE:
       if (value != 1 && value != 2) return fail(EHD_EINVAL, "columns per lane must be 1 or 2");
       if (value == 2 && r->ring_depth == 6) r->ring_depth = 3;
@@ -681,6 +688,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_RING_DEPTH: return r->ring_depth;
     case EHD_TUNE_STEP_KERNEL: return r->step_kernel;
     case EHD_TUNE_COLS_PER_LANE: return r->cols_per_lane;
+    case EHD_TUNE_TILE_MODES: return r->tile_modes;
   }
   return -1;
 }

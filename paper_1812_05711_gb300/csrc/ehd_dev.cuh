@@ -102,6 +102,7 @@ struct PoissonArgs {
   const double* flux_part;   // [2][nflux] wall-flux partials of the last step, or nullptr
   int nflux;
   double* flux_acc;          // [2] FP64 totals of injected / collected charge
+  int tile_modes;            // wavenumbers per CTA of the mode solve (8, 4, 2, 1; 0 = largest that fits)
 };
 
 struct FieldArgs {

@@ -690,7 +690,8 @@ int tile_modes(int Ny, size_t cbytes, size_t rbytes) {
 
 template <class R>
 cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
-  const int mb = tile_modes(a.Ny, sizeof(Cplx<R>), sizeof(R));
+  int mb = tile_modes(a.Ny, sizeof(Cplx<R>), sizeof(R));
+  if (a.tile_modes > 0 && a.tile_modes < mb) mb = a.tile_modes;
   const size_t sm = (size_t)a.Ny * mb * (sizeof(Cplx<R>) + sizeof(R));
   const int nm = a.Mh;  // tiles start at m = 0
   switch (mb) {
