@@ -36,12 +36,29 @@ import workloads as wl  # noqa: E402
 
 METRIC = "coupled-step GLUPS"
 UNIT = "GLUPS"
-# algorithmic bytes per node of the fused collide-stream kernel (FP32
-# storage): 9 f + 9 g loaded, 9 f + 9 g stored, one potential value loaded
 # kernels per coupled step: collide-stream (march form, writes the charge),
-# forward row FFT, FP64 mean mode, wavenumber systems, inverse row FFT
+# forward row FFT, mean mode (side stream), wavenumber systems, inverse row FFT
 LAUNCHES_PER_STEP = 5
+# algorithmic bytes per node of the fused collide-stream kernel: 9 f + 9 g
+# loaded, 9 f + 9 g stored, one potential value loaded, one charge density
+# stored (both in the compute precision: FP64 for f64 storage, else FP32)
 K4_BYTES_PER_NODE = {"f32": 36 * 4 + 8, "f64": 36 * 8 + 16, "bf16": 36 * 2 + 8, "f16": 36 * 2 + 8}
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the fused step kernel, from an ncu capture of the 2048 x 1680 FP32 channel;
+# keyed by a hash of the kernel's sources so that it reads null once the
+# kernel has changed since the capture.
+NCU_TRAFFIC = {("f32", "a366f3513a8b7f5c"): 279.155968e6 + 212.970240e6}
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("k_march.cu", "ehd_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_1812_05711_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -262,7 +279,8 @@ def run_ours(args):
                    "Fe": w.Fe, "Lambda": w.Lambda, "storage": storage, "compute": "f32" if storage != "f64" else "f64",
                    "per_rank": "one independent run", "l2": "state 495 MB > 129 MB L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_march (fused collide-stream)",
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((storage, _kernel_hash())) if w.name == "channel-2048x1680" else None,
+                     "traffic_unit": "bytes per launch, ncu dram read + write", "kernel": "k_march2 (fused collide-stream)",
                      "bytes_per_node": K4_BYTES_PER_NODE[storage], "kernel_ms": k4_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs", "poisson_ms": prof["poisson_ms"] / args.steps,
                      "charge_ms": prof["charge_ms"] / args.steps,
