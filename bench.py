@@ -136,6 +136,12 @@ def _dist():
     return dist, rank, ws, local
 
 
+def _weak_value(ws: int, cells: int, steps: int, ms_max: float) -> float:
+    """Whole-job GLUPS: every rank advances its own channel of `cells` nodes
+    (weak scaling), timed by the slowest rank."""
+    return ws * cells * steps / (ms_max * 1e-3) / 1e9
+
+
 def _max_over_ranks(dist, x: float) -> float:
     if dist is None:
         return x
@@ -163,9 +169,10 @@ def _oracle_glups(w: wl.Workload, budget_s: float, max_steps: int | None = None)
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
-    dist, rank, ws, _ = _dist()
-    if rank != 0:
+    """Reference arm: the FP64 CPU oracle, timed on the host cores.  Under
+    torchrun only rank 0 works; the other ranks exit at once (no process
+    group is formed: the arm has no collective)."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
     import oracle as o
     full = wl.large_channel()
@@ -228,7 +235,7 @@ def run_ours(args):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     ms_max = _max_over_ranks(dist, ms)
-    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e9
+    value = _weak_value(ws, cells, args.steps, ms_max)
     run.sync()
 
     # ---- per-kernel timing (events around each kernel on the run's stream)
@@ -254,7 +261,7 @@ def run_ours(args):
     ehd.ehd_fields(h, mask, out)
     e2e_s = time.perf_counter() - t0
     e2e_s = _max_over_ranks(dist, e2e_s)
-    e2e = ws * cells * args.steps / e2e_s / 1e9
+    e2e = _weak_value(ws, cells, args.steps, e2e_s * 1e3)
     h2d = (pin_f.nbytes + pin_g.nbytes) / args.steps
     d2h = out.nbytes / args.steps
     diag = run.diagnostics()
@@ -539,6 +546,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "channel" and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit(f"--workload {args.workload} runs on one GPU; use the channel workload under torchrun")
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":

@@ -375,3 +375,35 @@ def test_initial_state_moments():
     # Eq. 7 with the discrete field: the stored momentum was built with the
     # analytic force, so u differs from Eq. 29 only by (F_disc - F_h)/(2 rho)
     assert np.abs(F["ux"] - ux).max() < 1e-3 * p.u_ion * 1e-2 + 1e-12
+
+
+# ------------------------------------------------- linear threshold ---
+def _growth_rate(max_uy, steps_per_sample=1):
+    """Exponential rate of max|u_y| per step: least-squares slope of its log
+    over the second half of the record (the first half lets the initial
+    roll relax onto the least stable mode)."""
+    a = np.asarray(max_uy, dtype=np.float64)
+    t = np.arange(1, a.size + 1) * steps_per_sample
+    h = a.size // 2
+    return float(np.polyfit(t[h:], np.log(a[h:]), 1)[0])
+
+
+def test_threshold_sign_of_growth_eq29_roll():
+    """Electro-convective threshold: with C = 10, M = 10, Fe = 4000 and an
+    Eq. 29 roll in a box of aspect 1.23 (the paper's Lx/H), a perturbation
+    decays below the critical T (163.4 in the paper) and grows above it:
+    sigma(T = 150) < 0 < sigma(T = 180).  Coarse 32 x 26 grid (the sign is
+    robust; this grid's own threshold lies near T = 153)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def rate(T):
+        p = o.setup(32, 26, T, 10, 10, 4000, 0.25, u_ion=2e-3)
+        s = o.init_state(p, [1e-3], [0.0])
+        d = o.step(s, 40000, diag=True)
+        return _growth_rate(d[:, 5])
+
+    with ThreadPoolExecutor(2) as ex:
+        s150, s180 = ex.map(rate, (150.0, 180.0))
+    assert s150 < 0 < s180, (s150, s180)
+    # the unstable side grows by well over the decaying side's rate
+    assert s180 > 4 * abs(s150)
