@@ -130,10 +130,12 @@ ehd_status ehd_step(ehd_run* run, long n);
  * no counterpart (measurement only).  host ms_out[EHD_NPROFILE]: summed
  * milliseconds of [0] the fused collide-stream kernel, [1] the charge-moment
  * kernel (0 when the step kernel writes the charge itself), [2] the Poisson
- * solve (forward FFT, tridiagonal modes, inverse FFT; the FP64 mean mode runs
+ * solve (forward FFT, tridiagonal modes, inverse FFT; the mean mode runs
  * beside them on a second stream and is joined before the event), [3] whole
- * steps, [4] = n.  Synchronises. */
-#define EHD_NPROFILE 5
+ * steps, [4] = n, and inside [2]: [5] the forward row FFT, [6] the solves of
+ * the wavenumbers m >= 1, [7] the inverse row FFT, [8] the mean mode m = 0
+ * (on its own stream, concurrent with [6]).  Synchronises. */
+#define EHD_NPROFILE 9
 ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 
 /* Launch-shape tuning of a run (the paper has no counterpart; results do
@@ -143,7 +145,13 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * EHD_TUNE_STEP_KERNEL (0 march form, 1 node-parallel form),
  * EHD_TUNE_COLS_PER_LANE (march form: 1 or 2 adjacent nodes per lane),
  * EHD_TUNE_TILE_MODES (wavenumbers per CTA of the mode solve: 1, 2, 4, 8;
- * 0 = the largest whose tile fits in shared memory).
+ * 0 = the largest whose tile fits in shared memory), EHD_TUNE_PDL (1: the
+ * Poisson kernels are launched with programmatic dependent launch, so each
+ * is resident and waiting when its predecessor ends, which shortens steps of
+ * small grids; 0, the default: plain stream order, since early-resident CTAs
+ * unbalance the one-wave grids of large runs), EHD_TUNE_FFT_CTA (FP32 rows
+ * of 2048: 1, the default, one CTA of 64 threads per row; 0, one warp per
+ * row).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -151,6 +159,8 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_STEP_KERNEL 3
 #define EHD_TUNE_COLS_PER_LANE 4
 #define EHD_TUNE_TILE_MODES 5
+#define EHD_TUNE_PDL 6
+#define EHD_TUNE_FFT_CTA 7
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

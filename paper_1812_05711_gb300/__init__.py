@@ -195,10 +195,11 @@ def ehd_step(h, n: int):
 
 
 def ehd_step_profile(h, n: int) -> dict:
-    out = np.zeros(5)
+    out = np.zeros(9)
     _check(lib().ehd_step_profile(h, int(n), _dp(out)))
     return {"collide_stream_ms": out[0], "charge_ms": out[1], "poisson_ms": out[2], "step_ms": out[3],
-            "steps": int(out[4])}
+            "steps": int(out[4]), "fft_fwd_ms": out[5], "modes_ms": out[6], "fft_inv_ms": out[7],
+            "mean_mode_ms": out[8]}
 
 
 def ehd_fields(h, mask: int, out: np.ndarray):
@@ -235,7 +236,7 @@ def ehd_poisson_noalloc(Nx, Ny, eps, phi0, wall_mode, rhoc_ptr: int, phi_ptr: in
                                      ctypes.c_void_p(stream) if stream else None))
 
 
-TUNE = {"slab_rows": 1, "ring_depth": 2, "step_kernel": 3, "cols_per_lane": 4, "tile_modes": 5}
+TUNE = {"slab_rows": 1, "ring_depth": 2, "step_kernel": 3, "cols_per_lane": 4, "tile_modes": 5, "pdl": 6, "fft_cta": 7}
 
 
 def ehd_tune(h, param, value: int):

@@ -95,6 +95,8 @@ struct ehd_run {
   int ring_depth = 2;  // rows staged ahead in the march form
   int cols_per_lane = 2;
   int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
+  int pdl = 0;         // programmatic dependent launch between the Poisson kernels (off: see ehd_tune)
+  int fft_cta = 1;     // rows of 2048: CTA-per-row transforms
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -225,6 +227,7 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.nstrips = r->nstrips;
   a.ring_depth = r->ring_depth;
   a.cols_per_lane = r->cols_per_lane;
+  a.pdl = r->pdl;
   return a;
 }
 
@@ -252,6 +255,8 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.nflux = r->nxb;
   a.flux_acc = r->small;
   a.tile_modes = r->tile_modes;
+  a.pdl = r->pdl;
+  a.fft_cta = r->fft_cta;
   return a;
 }
 
@@ -657,6 +662,14 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
         return fail(EHD_EINVAL, "tile modes must be 0, 1, 2, 4 or 8");
       r->tile_modes = value;
       break;
+    case EHD_TUNE_PDL:
+      if (value != 0 && value != 1) return fail(EHD_EINVAL, "programmatic dependent launch must be 0 or 1");
+      r->pdl = value;
+      break;
+    case EHD_TUNE_FFT_CTA:
+      if (value != 0 && value != 1) return fail(EHD_EINVAL, "CTA-per-row transforms must be 0 or 1");
+      r->fft_cta = value;
+      break;
     case EHD_TUNE_COLS_PER_LANE:
       if (value != 1 && value != 2) return fail(EHD_EINVAL, "columns per lane must be 1 or 2");
       if (value == 2 && r->ring_depth == 6) r->ring_depth = 3;
@@ -689,6 +702,8 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_STEP_KERNEL: return r->step_kernel;
     case EHD_TUNE_COLS_PER_LANE: return r->cols_per_lane;
     case EHD_TUNE_TILE_MODES: return r->tile_modes;
+    case EHD_TUNE_PDL: return r->pdl;
+    case EHD_TUNE_FFT_CTA: return r->fft_cta;
   }
   return -1;
 }
@@ -728,42 +743,45 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
   DeviceGuard dg(r->device);
   for (int k = 0; k < EHD_NPROFILE; ++k) ms_out[k] = 0.0;
   if (n == 0) return EHD_OK;
-  // events: per step, before K4, after K4, after K5, after the Poisson solve
-  std::vector<cudaEvent_t> ev((size_t)4 * n, nullptr);
+  // events per step: [0] before the step kernel, [1] after it, [2] after the
+  // charge kernel, [3] after the Poisson solve, [4..8] the Poisson marks
+  constexpr int NE = 9;
+  std::vector<cudaEvent_t> ev((size_t)NE * n, nullptr);
   cudaError_t e = cudaSuccess;
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
   for (long t = 0; t < n && e == cudaSuccess; ++t) {
+    cudaEvent_t* E = &ev[(size_t)NE * t];
     const StepArgs sa = step_args(r, r->cur);
     const int nxt = 1 - r->cur;
-    e = cudaEventRecord(ev[4 * t], r->stream);
+    e = cudaEventRecord(E[0], r->stream);
     if (e == cudaSuccess)
       e = (r->step_kernel == 0) ? launch_march(sa, r->storage, r->real_f64, r->stream)
                                 : launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 1], r->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[1], r->stream);
     if (e == cudaSuccess && r->step_kernel == 1)
       e = launch_rhoc(r->g[nxt], (long long)r->Ny * r->P, r->storage, r->real_f64, r->Nx, r->Ny, r->P, r->rch,
                       r->rhoc, r->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 2], r->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[2], r->stream);
     if (e == cudaSuccess)
-      e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * t + 3], r->stream);
+      e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join, E + 4);
+    if (e == cudaSuccess) e = cudaEventRecord(E[3], r->stream);
     if (e == cudaSuccess) {
       r->cur = nxt;
       r->step += 1;
     }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+  // (slot, from, to): summed intervals
+  static const int span[8][3] = {{0, 0, 1}, {1, 1, 2}, {2, 2, 3}, {3, 0, 3},
+                                 {5, 2, 4}, {6, 4, 5}, {7, 5, 6}, {8, 7, 8}};
   for (long t = 0; t < n && e == cudaSuccess; ++t) {
-    float a = 0, b = 0, c = 0, d = 0;
-    e = cudaEventElapsedTime(&a, ev[4 * t], ev[4 * t + 1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[4 * t + 1], ev[4 * t + 2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&c, ev[4 * t + 2], ev[4 * t + 3]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&d, ev[4 * t], ev[4 * t + 3]);
-    ms_out[0] += a;
-    ms_out[1] += b;
-    ms_out[2] += c;
-    ms_out[3] += d;
+    const cudaEvent_t* E = &ev[(size_t)NE * t];
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+      float ms = 0;
+      e = cudaEventElapsedTime(&ms, E[span[k][1]], E[span[k][2]]);
+      ms_out[span[k][0]] += ms;
+    }
   }
   for (auto& x : ev)
     if (x) cudaEventDestroy(x);

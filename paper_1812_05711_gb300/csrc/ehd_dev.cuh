@@ -61,6 +61,31 @@ template <> struct Store<__half> {
 template <class R> struct Cplx { R re, im; };
 
 // ----------------------------------------------------------- kernel args ---
+// Programmatic dependent launch.  A kernel launched with pdl = true may
+// start while the previous kernel of its stream is still running; it must
+// call grid_dep_wait() before touching anything that kernel writes or reads,
+// and calls grid_dep_launch() after that wait, so that when a kernel starts,
+// every kernel two or more launches back has completed.  Both instructions
+// are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <class... P, class... A>
+cudaError_t launch_ex(bool pdl, void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      A&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t c = {};
+  c.gridDim = grid;
+  c.blockDim = block;
+  c.dynamicSmemBytes = smem;
+  c.stream = s;
+  c.attrs = at;
+  c.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&c, kernel, static_cast<A&&>(args)...);
+}
+
 struct StepArgs {
   int Nx, Ny, P;
   long long plane;           // elements per population plane (Ny * P)
@@ -82,6 +107,7 @@ struct StepArgs {
   int nstrips;               // 32-column strips (30 owned columns each)
   int ring_depth;            // rows staged ahead by cp.async (2, 3, 4 or 6)
   int cols_per_lane;         // 1: 32-column strips (30 owned); 2: 64-column strips (60 owned)
+  int pdl;                   // launch with programmatic dependent launch (see launch_ex)
 };
 
 struct PoissonArgs {
@@ -103,6 +129,8 @@ struct PoissonArgs {
   int nflux;
   double* flux_acc;          // [2] FP64 totals of injected / collected charge
   int tile_modes;            // wavenumbers per CTA of the mode solve (8, 4, 2, 1; 0 = largest that fits)
+  int pdl;                   // launch the main-stream kernels with programmatic dependent launch
+  int fft_cta;               // rows of 2048: one CTA of 64 threads per row (else one warp per row)
 };
 
 struct FieldArgs {
@@ -171,7 +199,7 @@ cudaError_t march_set_attributes();
 // systems on s; the FP64 mean mode (and the wall-flux totals) on `side`
 // between the fork and join events when side != nullptr.
 cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
-                           cudaEvent_t join);
+                           cudaEvent_t join, const cudaEvent_t* marks = nullptr);
 // rho_c = sum_i g_i (+ the row shift) into the charge plane.
 cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f64, int Nx, int Ny, int P,
                         const float* rch, void* rhoc, cudaStream_t s);

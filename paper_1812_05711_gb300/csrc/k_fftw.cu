@@ -219,9 +219,261 @@ __device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, flo
   }
 }
 
+// In-register 16-point forward DFT, natural order in and out, as 4 x 4:
+// X[k2 + 4 k1] = sum_n1 W_16^(n1 k2) W_4^(n1 k1) sum_n2 v[n1 + 4 n2] W_4^(n2 k2).
+// The twiddles are literal constants, so trivial products fold away.
+__device__ __forceinline__ void dft4(float& r0, float& i0, float& r1, float& i1, float& r2, float& i2, float& r3,
+                                     float& i3) {
+  const float sr = r0 + r2, si = i0 + i2, dr = r0 - r2, di = i0 - i2;
+  const float tr = r1 + r3, ti = i1 + i3, ur = r1 - r3, ui = i1 - i3;
+  r0 = sr + tr;
+  i0 = si + ti;
+  r2 = sr - tr;
+  i2 = si - ti;
+  r1 = dr + ui;  // (d) - i (u)
+  i1 = di - ur;
+  r3 = dr - ui;  // (d) + i (u)
+  i3 = di + ur;
+}
+
+template <int M>  // multiply by W_16^M = exp(-2 pi i M / 16), M in {0..9}
+__device__ __forceinline__ void mul_w16(float& re, float& im) {
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
+  float r = re, i = im;
+  if constexpr (M == 0) return;
+  if constexpr (M == 1) { re = r * c1 + i * s1; im = i * c1 - r * s1; }
+  if constexpr (M == 2) { re = (r + i) * h; im = (i - r) * h; }
+  if constexpr (M == 3) { re = r * s1 + i * c1; im = i * s1 - r * c1; }
+  if constexpr (M == 4) { re = i; im = -r; }
+  if constexpr (M == 6) { re = (i - r) * h; im = -(r + i) * h; }
+  if constexpr (M == 9) { re = -r * c1 - i * s1; im = r * s1 - i * c1; }
+}
+
+__device__ __forceinline__ void fft16(float (&re)[16], float (&im)[16]) {
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1)
+    dft4(re[n1], im[n1], re[n1 + 4], im[n1 + 4], re[n1 + 8], im[n1 + 8], re[n1 + 12], im[n1 + 12]);
+  // T[n1][k2] sits at n1 + 4 k2; twiddle W_16^(n1 k2)
+  mul_w16<1>(re[5], im[5]);
+  mul_w16<2>(re[9], im[9]);
+  mul_w16<3>(re[13], im[13]);
+  mul_w16<2>(re[6], im[6]);
+  mul_w16<4>(re[10], im[10]);
+  mul_w16<6>(re[14], im[14]);
+  mul_w16<3>(re[7], im[7]);
+  mul_w16<6>(re[11], im[11]);
+  mul_w16<9>(re[15], im[15]);
+  float orr[16], oi[16];
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float r0 = re[4 * k2], i0 = im[4 * k2], r1 = re[4 * k2 + 1], i1 = im[4 * k2 + 1];
+    float r2 = re[4 * k2 + 2], i2 = im[4 * k2 + 2], r3 = re[4 * k2 + 3], i3 = im[4 * k2 + 3];
+    dft4(r0, i0, r1, i1, r2, i2, r3, i3);
+    orr[k2] = r0;
+    oi[k2] = i0;
+    orr[k2 + 4] = r1;
+    oi[k2 + 4] = i1;
+    orr[k2 + 8] = r2;
+    oi[k2 + 8] = i2;
+    orr[k2 + 12] = r3;
+    oi[k2 + 12] = i3;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    re[k] = orr[k];
+    im[k] = oi[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-per-row transforms for rows of N = 2048 reals (L = 1024 complex): 64
+// threads, 16 values each, L = 16 x 16 x 4.  Shorter dependent chains per
+// thread than the warp-per-row form, for the same total work.
+//
+// With n = n0 + 64 n1 and k = k1 + 16 k0 (n0 = thread t):
+//   Z[k1 + 16 k0] = sum_n0 W_L^(n0 k1) W_64^(n0 k0) sum_n1 z[n0 + 64 n1] W_16^(n1 k1)
+// pass A: thread t, 16-point DFT over n1, twiddle W_L^(t k1), to shared
+// memory as sA[k1][t];
+// pass B: the 64-point DFT over n0 for each k1 by the 4 threads u = 4 k1 + q
+// (n0 = q + 4 b, k0 = c + 16 d): thread q, 16-point DFT over b, twiddle
+// W_64^(q c), exchange within the 4 threads, and a 4-point DFT over q:
+// thread (k1, q) ends with Z[k1 + 16 c + 256 d] for c = 4 q + i, i, d < 4.
+constexpr int kCtaL = 1024;
+constexpr int kCtaT = 64;
+constexpr int kPitchA = 68;  // float2 per k1 row of sA / sB (64 + 4: no bank conflicts)
+constexpr int kSmemCta = 16 * kPitchA;  // float2; sA, sB and sZ share it
+
+__device__ __forceinline__ int zpad(int k) { return k + 4 * (k >> 6); }
+
+// Forward 1024-point complex DFT of the CTA's row: on entry thread t holds
+// z[t + 64 n1] in (re[n1], im[n1]); on return thread (k1 = t / 4, q = t % 4)
+// holds Z[k1 + 16 (4 q + i) + 256 d] in (zr[4 d + i], zi[4 d + i]).
+__device__ __forceinline__ void cta_fft1024(float (&re)[16], float (&im)[16], float (&zr)[16], float (&zi)[16],
+                                            const float2* __restrict__ tw, float2* sm) {
+  const int t = threadIdx.x;
+  fft16(re, im);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    float2 v = make_float2(re[k1], im[k1]);
+    if (k1 > 0) v = cm(v, __ldg(tw + 2 * t * k1));  // W_1024^(t k1) = W_2048^(2 t k1)
+    sm[k1 * kPitchA + t] = v;
+  }
+  __syncthreads();
+  const int k1 = t >> 2, q = t & 3;
+  float br[16], bi[16];
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const float2 v = sm[k1 * kPitchA + q + 4 * b];
+    br[b] = v.x;
+    bi[b] = v.y;
+  }
+  fft16(br, bi);
+  __syncwarp();  // the group's rows of sA are read before sB overwrites them
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float2 v = make_float2(br[c], bi[c]);
+    if (c > 0 && q > 0) v = cm(v, __ldg(tw + 32 * q * c));  // W_64^(q c)
+    sm[k1 * kPitchA + 4 * c + (q ^ (c >> 2))] = v;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float2 v[4];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) v[qq] = sm[k1 * kPitchA + 4 * (4 * q + i) + (qq ^ q)];
+    // 4-point DFT over qq, W_4 = -i
+    const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+    const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+    const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+    const float2 d13 = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
+    zr[i] = s02.x + s13.x;
+    zi[i] = s02.y + s13.y;
+    zr[4 + i] = d02.x + d13.y;  // d02 - i d13
+    zi[4 + i] = d02.y - d13.x;
+    zr[8 + i] = s02.x - s13.x;
+    zi[8 + i] = s02.y - s13.y;
+    zr[12 + i] = d02.x - d13.y;  // d02 + i d13
+    zi[12 + i] = d02.y + d13.x;
+  }
+}
+
+// Forward transform of row y (N = 2048) by one CTA of 64 threads.
+__global__ void __launch_bounds__(kCtaT) k_rfft_cta(PoissonArgs a) {
+  __shared__ float2 sm[kSmemCta];
+  grid_dep_wait();
+  grid_dep_launch();
+  const int t = threadIdx.x, y = blockIdx.x;
+  const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
+  const float* row = static_cast<const float*>(a.rhoc) + (long long)y * a.P;
+  const float2* rc2 = reinterpret_cast<const float2*>(row);
+  const float nieps = -(float)a.inv_eps;
+  // A row constant c0 is taken out before the transform: the differences are
+  // exact (Sterbenz) and small, so the transform's rounding scales with the
+  // row's variation, and only the m = 0 bin depends on c0.
+  const float c0 = __ldg(row);
+  float re[16], im[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) {
+    const float2 v = rc2[t + 64 * n1];
+    re[n1] = (v.x - c0) * nieps;
+    im[n1] = (v.y - c0) * nieps;
+  }
+  float zr[16], zi[16];
+  cta_fft1024(re, im, zr, zi, tw, sm);
+  if (t == 0) {
+    // m = 0 coefficient, float-float: (Re Z0 + Im Z0) + N c0 (-1/eps), the
+    // product exact by the FMA two-product, N a power of two
+    float s, e;
+    two_sum_f(zr[0], zi[0], s, e);
+    const float p = c0 * nieps, pe = fmaf(c0, nieps, -p);
+    const float P = p * 2048.0f, PE = pe * 2048.0f;
+    float h, l;
+    two_sum_f(s, P, h, l);
+    l += e + PE;
+    two_sum_f(h, l, s, e);
+    static_cast<float2*>(a.spec0)[y] = make_float2(s, e);
+  }
+  __syncthreads();  // every thread has read its part of sB
+  const int k1 = t >> 2, q = t & 3;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      sm[zpad(k1 + 16 * (4 * q + i) + 256 * d)] = make_float2(zr[4 * d + i], zi[4 * d + i]);
+  __syncthreads();
+  // untangle, k and L - k together: S[k] = E_k + W_N^k O_k with
+  // E_k = (Z[k] + Z*[L-k]) / 2, O_k = (Z[k] - Z*[L-k]) / (2i); for L - k the
+  // roles of the two values swap and W_N^(L-k) = -conj(W_N^k)
+  float2* spec = static_cast<float2*>(a.spec) + (long long)y * a.Mp;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = t + 64 * j;  // 0 .. 511
+    const float2 zk = sm[zpad(k)];
+    const float2 zp = sm[zpad((kCtaL - k) & (kCtaL - 1))];
+    const float2 wk = __ldg(tw + k);
+    // E = (zk + conj zp) / 2, D = (zk - conj zp) / 2, O = -i D
+    const float Er = 0.5f * (zk.x + zp.x), Ei = 0.5f * (zk.y - zp.y);
+    const float Dr = 0.5f * (zk.x - zp.x), Di = 0.5f * (zk.y + zp.y);
+    // S[k] = E + w (Di - i Dr)
+    const float2 Sk = make_float2(Er + wk.x * Di + wk.y * Dr, Ei + wk.y * Di - wk.x * Dr);
+    // S[L-k] = E' + w' O' with E' = conj(E), D' = -conj(D), O' = -i D' = Di + i Dr,
+    // w' = -conj(w)
+    const float2 Sp = make_float2(Er - wk.x * Di - wk.y * Dr, -Ei + wk.y * Di - wk.x * Dr);
+    if (k == 0) {
+      spec[0] = make_float2(0.0f, 0.0f);
+      spec[kCtaL] = make_float2(zk.x - zk.y, 0.0f);  // Nyquist: Re Z0 - Im Z0
+    } else {
+      spec[k] = Sk;
+      spec[kCtaL - k] = Sp;
+    }
+  }
+  if (t == 0) {  // k = L/2 is its own partner: S = conj(Z[L/2]) (W_N^(L/2) = -i)
+    const float2 zk = sm[zpad(kCtaL / 2)];
+    spec[kCtaL / 2] = make_float2(zk.x, -zk.y);
+  }
+}
+
+// Inverse transform of row y (N = 2048) -> phi minus its row mean.
+__global__ void __launch_bounds__(kCtaT) k_irfft_cta(PoissonArgs a) {
+  __shared__ float2 sm[kSmemCta];
+  grid_dep_wait();
+  grid_dep_launch();
+  const int t = threadIdx.x, y = blockIdx.x;
+  const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
+  const float2* spec = static_cast<const float2*>(a.spec) + (long long)y * a.Mp;
+  // conj(Z[n]) for n = t + 64 n1, Z[k] = E_k + i O_k,
+  // E_k = (S[k] + S*[L-k]) / 2, O_k = (S[k] - S*[L-k]) / (2 W_N^k), S[0] := 0
+  float re[16], im[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) {
+    const int k = t + 64 * n1;
+    const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec[k];
+    const float2 sp = spec[kCtaL - k];
+    const float2 sc = make_float2(sp.x, -sp.y);
+    const float2 Ev = make_float2(0.5f * (sk.x + sc.x), 0.5f * (sk.y + sc.y));
+    const float2 Dv = make_float2(0.5f * (sk.x - sc.x), 0.5f * (sk.y - sc.y));
+    const float2 wk = __ldg(tw + k);
+    const float2 O = cm(Dv, make_float2(wk.x, -wk.y));
+    re[n1] = Ev.x - O.y;
+    im[n1] = -(Ev.y + O.x);
+  }
+  float zr[16], zi[16];
+  cta_fft1024(re, im, zr, zi, tw, sm);
+  float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(a.dphi) + (long long)y * a.P);
+  const float inL = 1.0f / (float)kCtaL;
+  const int k1 = t >> 2, q = t & 3;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      dphi2[k1 + 16 * (4 * q + i) + 256 * d] = make_float2(zr[4 * d + i] * inL, -zi[4 * d + i] * inL);
+}
+
 template <int E>
 __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
   __shared__ float2 smem[4][E * 33];
+  grid_dep_wait();
+  grid_dep_launch();
   const int warp = threadIdx.x >> 5;
   const int y = blockIdx.x * 4 + warp;
   if (y < a.Ny) rfft_warp_body<E>(a, y, smem[warp]);
@@ -230,6 +482,8 @@ __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
 template <int E>
 __global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
   __shared__ float2 smem[4][E * 33];
+  grid_dep_wait();
+  grid_dep_launch();
   const int warp = threadIdx.x >> 5;
   const int y = blockIdx.x * 4 + warp;
   if (y < a.Ny) irfft_warp_body<E>(a, y, smem[warp]);
@@ -285,12 +539,14 @@ bool fftw_supported(int Nx) { return Nx >= 64 && Nx <= 2048; }
 cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
-    case 64: k_rfft_warp<1><<<g, 128, 0, s>>>(a); break;
-    case 128: k_rfft_warp<2><<<g, 128, 0, s>>>(a); break;
-    case 256: k_rfft_warp<4><<<g, 128, 0, s>>>(a); break;
-    case 512: k_rfft_warp<8><<<g, 128, 0, s>>>(a); break;
-    case 1024: k_rfft_warp<16><<<g, 128, 0, s>>>(a); break;
-    case 2048: k_rfft_warp<32><<<g, 128, 0, s>>>(a); break;
+    case 64: return launch_ex(a.pdl != 0, k_rfft_warp<1>, dim3(g), dim3(128), 0, s, a);
+    case 128: return launch_ex(a.pdl != 0, k_rfft_warp<2>, dim3(g), dim3(128), 0, s, a);
+    case 256: return launch_ex(a.pdl != 0, k_rfft_warp<4>, dim3(g), dim3(128), 0, s, a);
+    case 512: return launch_ex(a.pdl != 0, k_rfft_warp<8>, dim3(g), dim3(128), 0, s, a);
+    case 1024: return launch_ex(a.pdl != 0, k_rfft_warp<16>, dim3(g), dim3(128), 0, s, a);
+    case 2048:
+      if (a.fft_cta) return launch_ex(a.pdl != 0, k_rfft_cta, dim3(a.Ny), dim3(kCtaT), 0, s, a);
+      return launch_ex(a.pdl != 0, k_rfft_warp<32>, dim3(g), dim3(128), 0, s, a);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -299,12 +555,14 @@ cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
 cudaError_t launch_irfft_warp(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
-    case 64: k_irfft_warp<1><<<g, 128, 0, s>>>(a); break;
-    case 128: k_irfft_warp<2><<<g, 128, 0, s>>>(a); break;
-    case 256: k_irfft_warp<4><<<g, 128, 0, s>>>(a); break;
-    case 512: k_irfft_warp<8><<<g, 128, 0, s>>>(a); break;
-    case 1024: k_irfft_warp<16><<<g, 128, 0, s>>>(a); break;
-    case 2048: k_irfft_warp<32><<<g, 128, 0, s>>>(a); break;
+    case 64: return launch_ex(a.pdl != 0, k_irfft_warp<1>, dim3(g), dim3(128), 0, s, a);
+    case 128: return launch_ex(a.pdl != 0, k_irfft_warp<2>, dim3(g), dim3(128), 0, s, a);
+    case 256: return launch_ex(a.pdl != 0, k_irfft_warp<4>, dim3(g), dim3(128), 0, s, a);
+    case 512: return launch_ex(a.pdl != 0, k_irfft_warp<8>, dim3(g), dim3(128), 0, s, a);
+    case 1024: return launch_ex(a.pdl != 0, k_irfft_warp<16>, dim3(g), dim3(128), 0, s, a);
+    case 2048:
+      if (a.fft_cta) return launch_ex(a.pdl != 0, k_irfft_cta, dim3(a.Ny), dim3(kCtaT), 0, s, a);
+      return launch_ex(a.pdl != 0, k_irfft_warp<32>, dim3(g), dim3(128), 0, s, a);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -316,7 +316,54 @@ struct TileScratch {
   R al[256 / MB][MB];
   Cplx<R> br[256 / MB][MB];
   Cplx<R> carry[256 / MB][MB];
+  R wa[MB][8 / MB];        // per-warp composed maps, chained across the warps of one mode
+  Cplx<R> wb[MB][8 / MB];
 };
+
+// Exclusive scan of the chunk maps x -> al x + br over the 256 / MB chunks of
+// each of the MB wavenumbers: carry[c][m] = the value entering chunk c, in
+// chunk order 0, 1, ... (forward sweep) or from the last chunk down
+// (backward sweep).  One warp composes 32 consecutive maps of one wavenumber
+// with a shuffle scan; the 8 / MB warps of a wavenumber are chained through
+// shared memory.  Called by all 256 threads.
+template <class R, int MB, bool BACK>
+__device__ __forceinline__ void chunk_carries(TileScratch<R, MB>& ts) {
+  constexpr int CH = 256 / MB, WPM = CH / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int mo = w / WPM, seg = w % WPM;
+  const int q = seg * 32 + lane;
+  const int c = BACK ? CH - 1 - q : q;
+  R al = ts.al[c][mo];
+  Cplx<R> br = ts.br[c][mo];
+  for (int o = 1; o < 32; o <<= 1) {
+    const R a2 = __shfl_up_sync(0xffffffffu, al, o);
+    const R b2r = __shfl_up_sync(0xffffffffu, br.re, o), b2i = __shfl_up_sync(0xffffffffu, br.im, o);
+    if (lane >= o) {  // the earlier maps first: x -> al (a2 x + b2) + br
+      br = {al * b2r + br.re, al * b2i + br.im};
+      al = al * a2;
+    }
+  }
+  R ea = __shfl_up_sync(0xffffffffu, al, 1);
+  Cplx<R> eb = {__shfl_up_sync(0xffffffffu, br.re, 1), __shfl_up_sync(0xffffffffu, br.im, 1)};
+  if (lane == 0) {
+    ea = R(1);
+    eb = {R(0), R(0)};
+  }
+  Cplx<R> vin = {R(0), R(0)};
+  if constexpr (WPM > 1) {
+    if (lane == 31) {
+      ts.wa[mo][seg] = al;
+      ts.wb[mo][seg] = br;
+    }
+    __syncthreads();
+    for (int k = 0; k < seg; ++k) {
+      const R ak = ts.wa[mo][k];
+      const Cplx<R> bk = ts.wb[mo][k];
+      vin = {ak * vin.re + bk.re, ak * vin.im + bk.im};
+    }
+  }
+  ts.carry[c][mo] = {ea * vin.re + eb.re, ea * vin.im + eb.im};
+}
 
 // One CTA solves wavenumbers m0 .. m0 + MB - 1 of run a (smem_raw: tile
 // storage, ts: chunk-map scratch).  The m = 0 column of tile 0 holds zeros
@@ -369,15 +416,7 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
   s_al[ch][mo] = al;
   s_br[ch][mo] = br;
   __syncthreads();
-  if (threadIdx.x < MB) {  // carries: value entering each chunk
-    Cplx<R> v = {R(0), R(0)};
-    for (int c = 0; c < CH; ++c) {
-      s_carry[c][threadIdx.x] = v;
-      const R ac = s_al[c][threadIdx.x];
-      const Cplx<R> bc = s_br[c][threadIdx.x];
-      v = {ac * v.re + bc.re, ac * v.im + bc.im};
-    }
-  }
+  chunk_carries<R, MB, false>(ts);  // value entering each chunk
   __syncthreads();
   // forward evaluation; compose the backward chunk map on the way
   Cplx<R> x = s_carry[ch][mo];
@@ -395,15 +434,7 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
   s_al[ch][mo] = ab;
   s_br[ch][mo] = bb;
   __syncthreads();
-  if (threadIdx.x < MB) {  // value just above each chunk, from the top down
-    Cplx<R> v = {R(0), R(0)};
-    for (int c = CH - 1; c >= 0; --c) {
-      s_carry[c][threadIdx.x] = v;
-      const R ac = s_al[c][threadIdx.x];
-      const Cplx<R> bc = s_br[c][threadIdx.x];
-      v = {ac * v.re + bc.re, ac * v.im + bc.im};
-    }
-  }
+  chunk_carries<R, MB, true>(ts);  // value just above each chunk, from the top down
   __syncthreads();
   x = s_carry[ch][mo];
   for (int j = j1 - 1; j >= j0; --j) {
@@ -424,6 +455,8 @@ template <class R, int MB>
 __global__ void __launch_bounds__(256) k_modes_tile(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileScratch<R, MB> ts;
+  grid_dep_wait();
+  grid_dep_launch();
   modes_tile_body<R, MB>(a, blockIdx.x * MB, smem_raw, ts);
 }
 
@@ -488,19 +521,50 @@ struct MeanNum<float> {
   __device__ static T down(T a, int o) { return ff_shfl_down(a, o); }
 };
 
-// m = 0 (128 threads, one row chunk each; chunk maps combined by a warp
-// shuffle scan and a scan over the 4 warps) + the step's wall fluxes.
+// m = 0 (NT threads, one row chunk each; chunk maps combined by a warp
+// shuffle scan and a shuffle scan over the warps) + the step's wall fluxes.
 // Arithmetic: FP64 on the plain FP64 path, float-float on the FP32 path.
-template <class R>
+template <class R, int NT>
 struct MeanScratch {
-  typename MeanNum<R>::T wa[4], wb[4], wc_in[4];
-  double fq[2][4];
+  static constexpr int NW = NT / 32;
+  typename MeanNum<R>::T wa[NW], wb[NW], wc_in[NW];
+  double fq[2][NW];
 };
 
-template <class R>
-__device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned char* smem_raw, MeanScratch<R>& ms) {
+// Exclusive scan over the warps of the warp totals (wa, wb) of the chunk maps
+// x -> a x + b: wc_in[w] = value entering warp w's first chunk (in the sweep
+// direction: warp 0 first, or the last warp first when BACK).  Warp 0 only.
+template <class R, int NT, bool BACK>
+__device__ __forceinline__ void mean_warp_carries(MeanScratch<R, NT>& ms) {
   using N = MeanNum<R>;
   using T = typename N::T;
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31;
+  const T one = N::from_f(1.0f), zero = N::from_f(0.0f);
+  const int w = BACK ? NW - 1 - lane : lane;
+  T al = one, br = zero;
+  if (lane < NW) {
+    al = ms.wa[w];
+    br = ms.wb[w];
+  }
+  for (int o = 1; o < NW; o <<= 1) {
+    const T a2 = N::up(al, o), b2 = N::up(br, o);
+    if (lane >= o) {
+      br = N::add(N::mul(al, b2), br);
+      al = N::mul(al, a2);
+    }
+  }
+  T eb = N::up(br, 1);
+  if (lane == 0) eb = zero;
+  if (lane < NW) ms.wc_in[w] = eb;
+}
+
+template <class R, int NT>
+__device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned char* smem_raw,
+                                               MeanScratch<R, NT>& ms) {
+  using N = MeanNum<R>;
+  using T = typename N::T;
+  constexpr int NW = NT / 32;
   auto& wa = ms.wa;
   auto& wb = ms.wb;
   auto& wc_in = ms.wc_in;
@@ -510,7 +574,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   if (a.flux_part) {
     // FP64 totals of the wall fluxes: a shuffle tree over the strips
     double qi = 0.0, qo = 0.0;
-    for (int b = t; b < a.nflux; b += 128) {
+    for (int b = t; b < a.nflux; b += NT) {
       qi += a.flux_part[b];
       qo += a.flux_part[a.nflux + b];
     }
@@ -525,12 +589,17 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
     }
     __syncthreads();
     if (t == 0) {
-      a.flux_acc[0] += (fq[0][0] + fq[0][1]) + (fq[0][2] + fq[0][3]);
-      a.flux_acc[1] += (fq[1][0] + fq[1][1]) + (fq[1][2] + fq[1][3]);
+      double si = 0.0, so = 0.0;
+      for (int w = 0; w < NW; ++w) {
+        si += fq[0][w];
+        so += fq[1][w];
+      }
+      a.flux_acc[0] += si;
+      a.flux_acc[1] += so;
     }
   }
   const float lift = (a.wall_mode == 0 ? 2.0f : 1.0f) * (float)a.Nx * (float)a.phi0;  // exact
-  for (int j = t; j < Ny; j += 128) {
+  for (int j = t; j < Ny; j += NT) {
     T v, p;
     if constexpr (sizeof(R) == 8) {
       v = static_cast<const double*>(a.spec0)[j];
@@ -546,7 +615,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   }
   __syncthreads();
   const T one = N::from_f(1.0f), zero = N::from_f(0.0f);
-  const int C = (Ny + 127) >> 7;
+  const int C = (Ny + NT - 1) / NT;
   const int j0 = min(t * C, Ny), j1 = min(j0 + C, Ny);
   // forward elimination d'_j = r_j (d_j - d'_{j-1}): chunk map x -> al x + br
   T al = one, br = zero;
@@ -566,13 +635,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
     wb[warp] = br;
   }
   __syncthreads();
-  if (t == 0) {
-    T v = zero;
-    for (int w = 0; w < 4; ++w) {
-      wc_in[w] = v;
-      v = N::add(N::mul(wa[w], v), wb[w]);
-    }
-  }
+  if (warp == 0) mean_warp_carries<R, NT, false>(ms);
   __syncthreads();
   T ex_a = N::up(al, 1), ex_b = N::up(br, 1);
   if (lane == 0) {
@@ -601,13 +664,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
     wb[warp] = bb;
   }
   __syncthreads();
-  if (t == 0) {
-    T v = zero;
-    for (int w = 3; w >= 0; --w) {
-      wc_in[w] = v;
-      v = N::add(N::mul(wa[w], v), wb[w]);
-    }
-  }
+  if (warp == 0) mean_warp_carries<R, NT, true>(ms);
   __syncthreads();
   T fa = N::down(ab, 1), fb = N::down(bb, 1);
   if (lane == 31) {
@@ -625,7 +682,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   R* Ebar = static_cast<R*>(a.Ebar);
   const T half = N::from_f(0.5f);
   const T phi0 = N::from_f((float)a.phi0);
-  for (int j = t; j < Ny; j += 128) {
+  for (int j = t; j < Ny; j += NT) {
     const T pc = N::mul(d[j], inN);
     const T pd = (j > 0) ? N::mul(d[j - 1], inN)
                          : ((a.wall_mode == 0) ? N::add(N::add(phi0, phi0), N::neg(pc)) : phi0);
@@ -641,11 +698,13 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   }
 }
 
+constexpr int kMeanThreads = 512;
+
 template <class R>
-__global__ void __launch_bounds__(128) k_mean_mode(PoissonArgs a) {
+__global__ void __launch_bounds__(kMeanThreads) k_mean_mode(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ MeanScratch<R> ms;
-  mean_mode_body<R>(a, smem_raw, ms);
+  __shared__ MeanScratch<R, kMeanThreads> ms;
+  mean_mode_body<R, kMeanThreads>(a, smem_raw, ms);
 }
 
 // Batch kernels: CTAs take (run, tile) items / one CTA per run.
@@ -663,15 +722,15 @@ __global__ void __launch_bounds__(256) k_batch_modes(BatchTables t, int step) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_batch_mean(BatchTables t, int step) {
+__global__ void __launch_bounds__(kMeanThreads) k_batch_mean(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ MeanScratch<float> ms;
+  __shared__ MeanScratch<float, kMeanThreads> ms;
   const int n = t.counts[0];
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
     const BatchRunDesc& rd = t.runs[r];
     if (step >= rd.remaining) continue;
     const PoissonArgs a = rd.pa;
-    mean_mode_body<float>(a, smem_raw, ms);
+    mean_mode_body<float, kMeanThreads>(a, smem_raw, ms);
     __syncthreads();
   }
 }
@@ -694,13 +753,13 @@ cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
   if (a.tile_modes > 0 && a.tile_modes < mb) mb = a.tile_modes;
   const size_t sm = (size_t)a.Ny * mb * (sizeof(Cplx<R>) + sizeof(R));
   const int nm = a.Mh;  // tiles start at m = 0
+  const bool pdl = a.pdl != 0;
   switch (mb) {
-    case 8: k_modes_tile<R, 8><<<(nm + 7) / 8, 256, sm, s>>>(a); break;
-    case 4: k_modes_tile<R, 4><<<(nm + 3) / 4, 256, sm, s>>>(a); break;
-    case 2: k_modes_tile<R, 2><<<(nm + 1) / 2, 256, sm, s>>>(a); break;
-    default: k_modes_tile<R, 1><<<nm, 256, sm, s>>>(a); break;
+    case 8: return launch_ex(pdl, k_modes_tile<R, 8>, dim3((nm + 7) / 8), dim3(256), sm, s, a);
+    case 4: return launch_ex(pdl, k_modes_tile<R, 4>, dim3((nm + 3) / 4), dim3(256), sm, s, a);
+    case 2: return launch_ex(pdl, k_modes_tile<R, 2>, dim3((nm + 1) / 2), dim3(256), sm, s, a);
+    default: return launch_ex(pdl, k_modes_tile<R, 1>, dim3(nm), dim3(256), sm, s, a);
   }
-  return cudaGetLastError();
 }
 
 template <class R>
@@ -716,7 +775,8 @@ int row_blocks(int Nx, int Ny) {
 }
 
 template <class R>
-cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
+                      const cudaEvent_t* marks) {
   const bool warp_fft = (sizeof(R) == 4) && fftw_supported(a.Nx);
   cudaError_t e;
   if (warp_fft) {
@@ -726,14 +786,22 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
+  // optional timing marks: [0] after the forward FFT, [1] after the m >= 1
+  // solve, [2] after the inverse FFT (all on s); [3], [4] around the mean mode
+  auto mark = [&](int k, cudaStream_t st) { return marks ? cudaEventRecord(marks[k], st) : cudaSuccess; };
+  if ((e = mark(0, s)) != cudaSuccess) return e;
   if (side) {
     if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
   }
-  k_mean_mode<R><<<1, 128, 2 * (size_t)a.Ny * sizeof(typename MeanNum<R>::T), side ? side : s>>>(a);
+  const cudaStream_t ms = side ? side : s;
+  if ((e = mark(3, ms)) != cudaSuccess) return e;
+  k_mean_mode<R><<<1, kMeanThreads, 2 * (size_t)a.Ny * sizeof(typename MeanNum<R>::T), ms>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = mark(4, ms)) != cudaSuccess) return e;
   if (side && (e = cudaEventRecord(join, side)) != cudaSuccess) return e;
   if ((e = launch_modes<R>(a, s)) != cudaSuccess) return e;
+  if ((e = mark(1, s)) != cudaSuccess) return e;
   if (warp_fft) {
     e = launch_irfft_warp(a, s);
   } else {
@@ -741,6 +809,7 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
+  if ((e = mark(2, s)) != cudaSuccess) return e;
   if (side && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -785,7 +854,7 @@ cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStr
 }
 
 cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s) {
-  k_batch_mean<<<grid, 128, t.modes_smem, s>>>(t, step);
+  k_batch_mean<<<grid, kMeanThreads, t.modes_smem, s>>>(t, step);
   return cudaGetLastError();
 }
 
@@ -812,8 +881,8 @@ cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f
 }
 
 cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
-                           cudaEvent_t join) {
-  return real_f64 ? poisson_t<double>(a, s, side, fork, join) : poisson_t<float>(a, s, side, fork, join);
+                           cudaEvent_t join, const cudaEvent_t* marks) {
+  return real_f64 ? poisson_t<double>(a, s, side, fork, join, marks) : poisson_t<float>(a, s, side, fork, join, marks);
 }
 
 }  // namespace ehd

@@ -32,16 +32,16 @@ def _rate(t, a):
 
 
 @functools.lru_cache(maxsize=None)
-def _oracle_record(Nx, Ny, T, steps, every):
+def _oracle_record(Nx, Ny, T, steps, every, A=1e-3):
     p = o.setup(Nx, Ny, T, 10, 10, 4000, 0.25, u_ion=2e-3)
-    s = o.init_state(p, [1e-3], [0.0])
+    s = o.init_state(p, [A], [0.0])
     d = o.step(s, steps + 1, diag=True)  # row t holds the state at time t
     t = np.arange(every, steps + 1, every)
     return t, d[t, 5]
 
 
-def _gpu_record(ehd, Nx, Ny, T, steps, every, storage):
-    run = ehd.Run(Nx, Ny, T, 10, 10, 4000, 0.25, storage=storage, u_ion=2e-3, amp=[1e-3], phase=[0.0])
+def _gpu_record(ehd, Nx, Ny, T, steps, every, storage, A=1e-3):
+    run = ehd.Run(Nx, Ny, T, 10, 10, 4000, 0.25, storage=storage, u_ion=2e-3, amp=[A], phase=[0.0])
     t, a = [], []
     for k in range(steps // every):
         run.step(every)
@@ -55,18 +55,23 @@ def _gpu_record(ehd, Nx, Ny, T, steps, every, storage):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_growth_rate_matches_oracle_32x26(storage):
     """32 x 26 (aspect 1.23), C = 10, M = 10, Fe = 4000, 40,000 steps:
-    sigma(T = 180) > 0 within 1 % of the oracle's; sigma(T = 150) < 0, within
-    1 % (FP64) or 10 % of the oracle's (FP32: the decaying roll is 1e-4 of
-    the drift velocity)."""
+    sigma(T = 180) > 0 and sigma(T = 150) < 0, each within 1 % of the
+    oracle's.  FP64 runs the configuration's roll amplitude A = 1e-3 (times
+    the ion drift speed).  FP32 storage rounds populations to about 1e-10,
+    which is 1e-4 of a roll of A = 1e-3 per step and shifts its measured
+    rate by 1 % (T = 180) to 12 % (T = 150, decaying); FP32 is therefore
+    compared at A = 5e-2, where the roll is well above that rounding and the
+    rate difference measured 0.02 % (A = 1e-2, T = 180)."""
     ehd = _ehd()
     steps, every = 40000, 200
-    for T, rel in ((180.0, 0.01), (150.0, 0.01 if storage == "f64" else 0.10)):
-        to, ao = _oracle_record(32, 26, T, steps, every)
-        tg, ag = _gpu_record(ehd, 32, 26, T, steps, every, storage)
+    A = 1e-3 if storage == "f64" else 5e-2
+    for T in (180.0, 150.0):
+        to, ao = _oracle_record(32, 26, T, steps, every, A)
+        tg, ag = _gpu_record(ehd, 32, 26, T, steps, every, storage, A)
         assert np.array_equal(to, tg)
         so, sg = _rate(to, ao), _rate(tg, ag)
         assert np.sign(sg) == np.sign(so) == (1 if T > T_C_PAPER else -1), (T, so, sg)
-        assert abs(sg - so) <= rel * abs(so), (storage, T, so, sg)
+        assert abs(sg - so) <= 0.01 * abs(so), (storage, T, so, sg)
         if storage == "f64":
             np.testing.assert_allclose(ag, ao, rtol=1e-8)
 
@@ -75,13 +80,14 @@ def test_growth_rate_matches_oracle_32x26(storage):
 def test_threshold_sweep_brackets_tc_128x104():
     """The paper's experiment on a 128 x 104 channel (aspect 1.23) with
     FP32 runs advanced together in one batch: T in {150, 160, 170, 180},
-    300,000 steps (5.8 ion transits).  Hard: the roll decays at T = 150 and
+    300,000 steps (5.8 ion transits), roll amplitude A = 1e-2 (linear, and
+    well above FP32 storage rounding).  Hard: the roll decays at T = 150 and
     grows at T = 180.  Reported: T_c from linear interpolation of sigma(T)."""
     ehd = _ehd()
     Ts = (150.0, 160.0, 170.0, 180.0)
     steps, tick = 300000, 1000
     batch = ehd.Batch(len(Ts), max_nx=128, max_ny=104)
-    runs = [ehd.Run(128, 104, T, 10, 10, 4000, 0.25, storage="f32", u_ion=2e-3, amp=[1e-3], phase=[0.0])
+    runs = [ehd.Run(128, 104, T, 10, 10, 4000, 0.25, storage="f32", u_ion=2e-3, amp=[1e-2], phase=[0.0])
             for T in Ts]
     for r in runs:
         batch.add(r, steps)
