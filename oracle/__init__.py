@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
         ("M", ctypes.c_double), ("Fe", ctypes.c_double),
         ("Lambda", ctypes.c_double), ("Lambda_g", ctypes.c_double),
         ("u_ion", ctypes.c_double),
-        ("wall_mode", ctypes.c_int),
+        ("wall_mode", ctypes.c_int), ("x_symbol", ctypes.c_int),
         ("periodic_y", ctypes.c_int), ("no_poisson", ctypes.c_int),
         ("no_force", ctypes.c_int),
         ("ext_E", ctypes.c_double * 2), ("ext_F", ctypes.c_double * 2),
@@ -93,7 +93,7 @@ def lib():
         L.orc_dft.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
         L.orc_fft.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int]
         L.orc_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
-        L.orc_poisson_general.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        L.orc_poisson_general.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_poisson.argtypes = [pp, dp, dp]
         L.orc_efield.argtypes = [pp, dp, dp, dp]
@@ -113,12 +113,13 @@ def _dp(a: np.ndarray):
 
 def setup(Nx, Ny, T, C, M, Fe, Lambda, Lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
           periodic_y=0, no_poisson=0, no_force=0, ext_E=(0.0, 0.0),
-          ext_F=(0.0, 0.0)) -> Params:
+          ext_F=(0.0, 0.0), x_symbol=0) -> Params:
     p = Params()
     p.Nx, p.Ny = int(Nx), int(Ny)
     p.T, p.C, p.M, p.Fe = float(T), float(C), float(M), float(Fe)
     p.Lambda, p.Lambda_g, p.u_ion = float(Lambda), float(Lambda_g), float(u_ion)
     p.wall_mode = int(wall_mode)
+    p.x_symbol = int(x_symbol)
     p.periodic_y, p.no_poisson, p.no_force = int(periodic_y), int(no_poisson), int(no_force)
     p.ext_E[0], p.ext_E[1] = float(ext_E[0]), float(ext_E[1])
     p.ext_F[0], p.ext_F[1] = float(ext_F[0]), float(ext_F[1])
@@ -167,12 +168,13 @@ def thomas(a, b, c, d) -> np.ndarray:
     return dre + 1j * dim
 
 
-def poisson_general(src: np.ndarray, wall_mode=0, phi_bottom=0.0, phi_top=0.0):
-    """Solve [Dx^2 + Dy^2] phi = src on an Ny x Nx grid (Sec. IV.3)."""
+def poisson_general(src: np.ndarray, wall_mode=0, phi_bottom=0.0, phi_top=0.0, x_symbol=0):
+    """Solve [Dx^2 + Dy^2] phi = src on an Ny x Nx grid (Sec. IV.3); Dx^2 is
+    spectral (Eq. 20, x_symbol 0) or the 3-point difference (x_symbol 1)."""
     src = np.ascontiguousarray(src, dtype=np.float64)
     Ny, Nx = src.shape
     phi = np.empty_like(src)
-    lib().orc_poisson_general(Nx, Ny, wall_mode, phi_bottom, phi_top, _dp(src), _dp(phi))
+    lib().orc_poisson_general(Nx, Ny, wall_mode, x_symbol, phi_bottom, phi_top, _dp(src), _dp(phi))
     return phi
 
 

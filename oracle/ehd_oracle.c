@@ -225,8 +225,9 @@ void orc_thomas(int n, const double* a, const double* b, const double* c,
  * a tridiagonal system (its eigenvalues are the -4 sin^2 symbols of Eq. 24,
  * which is why it equals the odd-extension transform of Eqs. 21-25).
  * Inverse DFT, real part. */
-void orc_poisson_general(int Nx, int Ny, int wall_mode, double phi_bottom,
-                         double phi_top, const double* src, double* phi) {
+void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
+                         double phi_bottom, double phi_top, const double* src,
+                         double* phi) {
   size_t nc = (size_t)Nx * Ny;
   double* sre = (double*)malloc(sizeof(double) * nc); /* [m][y] */
   double* sim = (double*)malloc(sizeof(double) * nc);
@@ -257,7 +258,11 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, double phi_bottom,
   for (int m = 0; m < Nx; ++m) {
     int ms = (m <= Nx / 2) ? m : m - Nx; /* signed wavenumber */
     double kx = 2.0 * OPI * (double)ms / (double)Nx;
-    double kappa = kx * kx;
+    double kappa = kx * kx; /* Eq. 20 */
+    if (x_symbol == 1) {    /* 3-point difference in x: 4 sin^2(pi m / Nx) */
+      double sx = sin(OPI * (double)ms / (double)Nx);
+      kappa = 4.0 * sx * sx;
+    }
     for (int j = 0; j < Ny; ++j) {
       a[j] = 1.0;
       c[j] = 1.0;
@@ -307,7 +312,8 @@ void orc_poisson(const orc_params* p, const double* rhoc, double* phi) {
   size_t nc = (size_t)p->Nx * p->Ny;
   double* s = (double*)malloc(sizeof(double) * nc);
   for (size_t k = 0; k < nc; ++k) s[k] = -rhoc[k] / p->eps; /* Eq. 4 */
-  orc_poisson_general(p->Nx, p->Ny, p->wall_mode, p->phi0, 0.0, s, phi);
+  orc_poisson_general(p->Nx, p->Ny, p->wall_mode, p->x_symbol, p->phi0, 0.0, s,
+                      phi);
   free(s);
 }
 

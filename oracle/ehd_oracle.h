@@ -16,6 +16,9 @@ typedef struct {
   double Lambda_g;     /* charge magic parameter, Eq. 17 */
   double u_ion;        /* lattice ion drift speed mu_b dphi0 / H */
   int wall_mode;       /* 0 halfway walls, 1 node walls of Eq. 21 */
+  int x_symbol;        /* x second derivative: 0 spectral -kappa_m (Eq. 20),
+                          1 second-order difference -4 sin^2(pi m / Nx), the
+                          symbol of the 3-point stencil (Eq. 24's form in x) */
   /* hooks used only by the oracle's own pins (all zero for the method) */
   int periodic_y;      /* y periodic, no walls (requires no_poisson) */
   int no_poisson;      /* E = ext_E instead of -grad phi */
@@ -38,8 +41,9 @@ void orc_dft(int n, const double* re, const double* im, double* ore,
 void orc_fft(int n, double* re, double* im, int sign);
 void orc_thomas(int n, const double* a, const double* b, const double* c,
                 double* dre, double* dim);
-void orc_poisson_general(int Nx, int Ny, int wall_mode, double phi_bottom,
-                         double phi_top, const double* src, double* phi);
+void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
+                         double phi_bottom, double phi_top, const double* src,
+                         double* phi);
 void orc_poisson(const orc_params* p, const double* rhoc, double* phi);
 void orc_efield(const orc_params* p, const double* phi, double* Ex,
                 double* Ey);
