@@ -524,6 +524,80 @@ def run_precision(args):
     return 0
 
 
+def _table2():
+    rows = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table2_hydrostatic.txt")) as fh:
+        for ln in fh:
+            if ln.strip() and not ln.startswith("#"):
+                C, ra, ya, eE, erc = map(float, ln.split())
+                rows[C] = {"rho_a": ra, "y_a": ya, "eL2_Ey": eE, "eL2_rhoc": erc}
+    return rows
+
+
+def run_hydrostatic(args):
+    """Sec. V.1: the no-flow steady state at NY = 100, Fe = 4000 against Eqs.
+    27-28 for a sweep of the injection strength C (Table II prints C = 0.1
+    and 10); plain FP64 path."""
+    import time as _t
+
+    import torch
+
+    from paper_1812_05711_gb300 import studies
+
+    torch.cuda.set_device(0)
+    tab = _table2()
+    rows = []
+    t0 = _t.perf_counter()
+    for C in (0.1, 0.3, 1.0, 3.0, 10.0):
+        r = studies.hydrostatic(C)
+        rows.append({"C": C, "eL2_Ey": r["eL2_Ey"], "eL2_rhoc": r["eL2_rhoc"], "rho_a": r["rho_a"],
+                     "y_a": r["y_a"], "paper": tab.get(C)})
+    el = _t.perf_counter() - t0
+    line = {"metric": "hydrostatic e_L2 vs Eqs. 27-28", "value": rows[0]["eL2_Ey"], "unit": "relative L2",
+            "n_gpus": 1, "steps": 30000, "warmup": 0, "ms_per_step": None, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "hydrostatic-16x100-Fe4000", "u_ion": 0.01, "seconds": el},
+            "table": rows, "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_bifurcation(args):
+    """Sec. V.2 (FIG. 3): electric Nusselt number Ne(T) on the branch that
+    starts from a small roll and on the branch continued downwards from a
+    finite-amplitude state; T_c and T_f by linear interpolation."""
+    import time as _t
+
+    import torch
+
+    from paper_1812_05711_gb300 import studies
+
+    torch.cuda.set_device(0)
+    Ts = [100.0 + 5.0 * k for k in range(17)] + [190.0, 200.0, 220.0]
+    t0 = _t.perf_counter()
+    r = studies.nusselt_sweep(Ts, Nx=64, Ny=52, u_ion=5e-3, steps=200000, window=40000)
+    el = _t.perf_counter() - t0
+
+    def crossing(branch, level, rising):
+        pts = sorted(branch)
+        for (t0_, n0), (t1_, n1) in zip(pts, pts[1:]):
+            if (n0 - level) * (n1 - level) <= 0 and n0 != n1:
+                return t0_ + (t1_ - t0_) * (level - n0) / (n1 - n0)
+        return None
+
+    Tc = crossing(r["lower"], 1.01, True)
+    Tf = crossing(r["upper"], 1.01, False)
+    line = {"metric": "Ne(T) thresholds", "value": Tc, "unit": "T", "n_gpus": 1, "steps": 200000, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": None, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "bifurcation-64x52", "u_ion": 5e-3, "seconds": el},
+            "T_c_onset": Tc, "T_f": Tf, "paper": {"T_c": 163.4, "T_f": 108.7},
+            "lower": r["lower"], "upper": r["upper"], "I_h": r["I_h"],
+            "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,9 +607,11 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="channel", choices=["channel", "batch", "serve", "fp64", "precision"],
+    ap.add_argument("--workload", default="channel",
+                    choices=["channel", "batch", "serve", "fp64", "precision", "hydrostatic", "bifurcation"],
                     help="channel: 2048x1680 headline (default); batch: 64 uneven runs; serve: request stream; "
-                         "fp64: 128x104 plain FP64; precision: 1024x840 storage variants")
+                         "fp64: 128x104 plain FP64; precision: 1024x840 storage variants; "
+                         "hydrostatic: Table II e_L2 for a C sweep; bifurcation: Ne(T) both branches")
     ap.add_argument("--tick", type=int, default=100, help="steps per batch tick (batch / serve)")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serving stream")
     ap.add_argument("--fp64-requests", type=int, default=4, help="prefix served by the plain FP64 path")
@@ -556,6 +632,10 @@ def main():
         return run_fp64(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "hydrostatic":
+        return run_hydrostatic(args)
+    if args.workload == "bifurcation":
+        return run_bifurcation(args)
     return run_ours(args)
 
 

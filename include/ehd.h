@@ -93,6 +93,10 @@ typedef struct {
                        charge density itself (default); 1: one thread per
                        node, push form, charge density summed by a separate
                        kernel.  Same results up to rounding order. */
+  int x_symbol;     /* x second derivative of the Poisson solve: 0 spectral,
+                       -(2 pi m / Nx)^2 (Eq. 20, default); 1 the 3-point
+                       difference -4 sin^2(pi m / Nx), so that the solve
+                       inverts the 5-point Laplacian. */
 } ehd_options;
 
 /* Fill *opt with the defaults above. */

@@ -53,6 +53,7 @@ class Options(ctypes.Structure):
         ("pert_phase", ctypes.c_double * MAX_PERT_MODES),
         ("stream", ctypes.c_void_p),
         ("step_kernel", ctypes.c_int),
+        ("x_symbol", ctypes.c_int),
     ]
 
 
@@ -265,7 +266,7 @@ def ehd_last_error() -> str:
 
 # ------------------------------------------------------------ convenience
 def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
-                 amp=(), phase=(), stream=None, step_kernel=0) -> Options:
+                 amp=(), phase=(), stream=None, step_kernel=0, x_symbol=0) -> Options:
     o = ehd_default_options()
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if compute is None:
@@ -283,6 +284,7 @@ def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mo
         o.pert_phase[k] = float(p)
     o.stream = stream
     o.step_kernel = int(step_kernel)
+    o.x_symbol = int(x_symbol)
     return o
 
 
@@ -295,14 +297,15 @@ class Run:
     """
 
     def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
-                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=0):
+                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=0,
+                 x_symbol=0):
         self.Nx, self.Ny = int(Nx), int(Ny)
         self._stream_obj = None
         if stream is None and torch_stream:
             import torch
             self._stream_obj = torch.cuda.Stream()
             stream = self._stream_obj.cuda_stream
-        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel)
+        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel, x_symbol)
         self.handle = ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt)
 
     # lifecycle

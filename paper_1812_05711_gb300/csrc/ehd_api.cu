@@ -414,6 +414,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   if (o.compute == EHD_COMPUTE_F64 && o.storage != EHD_STORE_F64)
     return fail(EHD_EINVAL, "FP64 compute needs FP64 storage");
   if (o.wall_mode != 0 && o.wall_mode != 1) return fail(EHD_EINVAL, "wall_mode must be 0 or 1");
+  if (o.x_symbol != 0 && o.x_symbol != 1) return fail(EHD_EINVAL, "x_symbol must be 0 or 1");
   if (o.n_modes < 0 || o.n_modes > EHD_MAX_PERT_MODES) return fail(EHD_EINVAL, "n_modes out of range");
   if (o.step_kernel != 0 && o.step_kernel != 1) return fail(EHD_EINVAL, "step_kernel must be 0 or 1");
 
@@ -550,7 +551,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     std::vector<double> piv((size_t)r->Mp * Ny, 1.0), piv0(Ny);
     for (int m = 0; m < r->Mh; ++m) {
       const double kx = 2.0 * kPi * (double)m / (double)Nx;
-      const double diag = -(2.0 + kx * kx);
+      const double sx = std::sin(kPi * (double)m / (double)Nx);
+      const double kappa = (o.x_symbol == 1) ? 4.0 * sx * sx : kx * kx;  // Eq. 20, or the 3-point symbol
+      const double diag = -(2.0 + kappa);
       const double corner = diag - (r->wall_mode == 0 ? 1.0 : 0.0);
       double prev = 0.0;
       for (int j = 0; j < Ny; ++j) {

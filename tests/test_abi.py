@@ -51,6 +51,10 @@ def test_create_rejects_bad_options():
     o = ehd.make_options("f32", u_ion=-1.0)
     with pytest.raises(ehd.EhdError):
         ehd.ehd_create(128, 104, 200, 10, 10, 4000, 0.25, o)
+    o = ehd.make_options("f32", x_symbol=2)
+    with pytest.raises(ehd.EhdError) as ei:
+        ehd.ehd_create(128, 104, 200, 10, 10, 4000, 0.25, o)
+    assert "x_symbol" in str(ei.value)
 
 
 def test_footprint_scales_with_storage():

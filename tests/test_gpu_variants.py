@@ -1,0 +1,83 @@
+"""Variants of the step against the oracle (GPU, through the C ABI): the
+fluid magic parameter Lambda of Eq. 17 (1/12 as printed in Sec. IV.2, 3/16,
+1/4), the single-relaxation-time limit Lambda = (tau+ - 1/2)^2 (tau- =
+tau+), and the 3-point x symbol of the Poisson solve."""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+
+gpu = pytest.mark.gpu
+
+
+def _ehd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1812_05711_gb300 as ehd
+    return ehd
+
+
+def _scaled_err(p, A, B):
+    sc = {"rho": 1.0, "ux": p.u_ion, "uy": p.u_ion, "rho_c": p.rho0, "phi": 1.0, "Ex": 1.0 / p.H, "Ey": 1.0 / p.H}
+    return max(float(np.abs(A[k] - B[k]).max() / sc[k]) for k in A)
+
+
+def _compare(ehd, Lam, storage="f64", x_symbol=0, steps=300, T=200.0):
+    Nx, Ny = 64, 52
+    amp, ph = wl.roll(41, 1e-2)
+    p = o.setup(Nx, Ny, T, 10, 10, 4000, Lam, u_ion=5e-3, x_symbol=x_symbol)
+    s = o.init_state(p, amp, ph)
+    run = ehd.Run(Nx, Ny, T, 10, 10, 4000, Lam, storage=storage, u_ion=5e-3, amp=amp, phase=ph,
+                  x_symbol=x_symbol)
+    par = run.params()
+    run.step(steps)
+    o.step(s, steps)
+    e = _scaled_err(p, run.fields(), o.fields(s))
+    run.close()
+    return p, par, e
+
+
+@gpu
+@pytest.mark.parametrize("Lam", [1.0 / 12.0, 3.0 / 16.0, 0.25])
+def test_lambda_variants_fp64_parity(Lam):
+    ehd = _ehd()
+    p, par, e = _compare(ehd, Lam)
+    assert par["tau_m"] == pytest.approx(p.tau_m, rel=1e-13)
+    assert e <= 1e-12, e
+
+
+@gpu
+def test_srt_limit_fp64_parity():
+    """Lambda = (tau+ - 1/2)^2 gives tau- = tau+: the TRT collision is the
+    single-relaxation-time (BGK) one."""
+    ehd = _ehd()
+    p0 = o.setup(64, 52, 200.0, 10, 10, 4000, 0.25, u_ion=5e-3)
+    Lam = (p0.tau_p - 0.5) ** 2
+    p, par, e = _compare(ehd, Lam)
+    assert par["tau_m"] == pytest.approx(par["tau_p"], rel=1e-12)
+    assert e <= 1e-12, e
+
+
+@gpu
+@pytest.mark.parametrize("storage,bound", [("f64", 1e-12), ("f32", 2e-5)])
+def test_three_point_x_symbol_parity(storage, bound):
+    ehd = _ehd()
+    p, _, e = _compare(ehd, 0.25, storage=storage, x_symbol=1)
+    assert e <= bound, e
+
+
+@gpu
+def test_x_symbol_changes_the_solution():
+    """The two symbols give measurably different states (the option is live)."""
+    ehd = _ehd()
+    amp, ph = wl.roll(41, 1e-2)
+    runs = [ehd.Run(64, 52, 200.0, 10, 10, 4000, 0.25, storage="f64", u_ion=5e-3, amp=amp, phase=ph,
+                    x_symbol=k) for k in (0, 1)]
+    for r in runs:
+        r.step(300)
+    A, B = runs[0].fields(), runs[1].fields()
+    assert np.abs(A["Ex"] - B["Ex"]).max() > 1e-9 * np.abs(A["Ex"]).max()
+    for r in runs:
+        r.close()
