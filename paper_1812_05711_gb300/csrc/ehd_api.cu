@@ -388,9 +388,9 @@ ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
   const size_t P = (size_t)((Nx + 31) / 32 * 32), Mh = (size_t)Nx / 2 + 1;
   const size_t rs = (storage == 0) ? 8 : 4;  // worst case for the compute type
   size_t b = 4 * 9 * (size_t)Ny * P * storage_bytes(storage);  // f, g ping-pong
-  b += (size_t)Ny * P * rs;                                    // dphi
-  b += (size_t)Ny * Mh * 2 * rs + Mh * (size_t)Ny * rs;        // spectrum, pivots
-  b += (size_t)Ny * (8 + 8 + 8 + rs + 4) + (size_t)Nx * rs;    // per-row, twiddles
+  b += 2 * (size_t)Ny * P * rs;                                // dphi, rho_c
+  b += (size_t)Ny * (Mh + 3) * 3 * rs;                         // spectrum, pivots (pitch Mp)
+  b += (size_t)Ny * (8 + 8 + 8 + rs + 4) + (size_t)(Nx + 1024) * 2 * rs;  // per-row, twiddles
   b += 64 * 1024;                                              // small buffers
   *bytes = b;
   return EHD_OK;
@@ -505,7 +505,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->spec0 = run_alloc(r, Ny * sizeof(double));
   r->rfac = run_alloc(r, (size_t)r->Mp * Ny * r->rsz);
   r->rfac0 = run_alloc(r, Ny * sizeof(double));
-  r->tw = run_alloc(r, (size_t)Nx * 2 * r->rsz);
+  // twiddles exp(-2 pi i q / Nx), q < Nx; FP32 rows of 2048 append the
+  // first-pass twiddles of the CTA transform, [k1 < 16][t < 64]
+  r->tw = run_alloc(r, (size_t)(Nx + (Nx == 2048 && !r->real_f64 ? 1024 : 0)) * 2 * r->rsz);
   if (shifted) r->rch = static_cast<float*>(run_alloc(r, Ny * sizeof(float)));
   r->step_kernel = o.step_kernel;
   r->cols_per_lane = 2;
@@ -547,6 +549,13 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
       twd[2 * q] = std::cos(ang);
       twd[2 * q + 1] = -std::sin(ang);
     }
+    if (Nx == 2048 && !r->real_f64)  // exp(-2 pi i t k1 / 1024) at [k1][t], t < 64, k1 < 16
+      for (int k1 = 0; k1 < 16; ++k1)
+        for (int t = 0; t < 64; ++t) {
+          const double ang = 2.0 * kPi * (double)(t * k1) / 1024.0;
+          twd.push_back(std::cos(ang));
+          twd.push_back(-std::sin(ang));
+        }
     // reciprocal Thomas pivots, [Ny][Mp] (row-major, wavenumber fastest)
     std::vector<double> piv((size_t)r->Mp * Ny, 1.0), piv0(Ny);
     for (int m = 0; m < r->Mh; ++m) {

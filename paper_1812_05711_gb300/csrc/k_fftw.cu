@@ -312,10 +312,11 @@ __device__ __forceinline__ void cta_fft1024(float (&re)[16], float (&im)[16], fl
                                             const float2* __restrict__ tw, float2* sm) {
   const int t = threadIdx.x;
   fft16(re, im);
+  const float2* __restrict__ tw1 = tw + 2 * kCtaL;  // W_1024^(t k1) at [k1][t]
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) {
     float2 v = make_float2(re[k1], im[k1]);
-    if (k1 > 0) v = cm(v, __ldg(tw + 2 * t * k1));  // W_1024^(t k1) = W_2048^(2 t k1)
+    if (k1 > 0) v = cm(v, __ldg(tw1 + k1 * kCtaT + t));
     sm[k1 * kPitchA + t] = v;
   }
   __syncthreads();

@@ -311,24 +311,24 @@ __global__ void __launch_bounds__(256) k_irfft_rows(PoissonArgs a) {
 // A CTA holds MB wavenumbers x Ny rows in shared memory; thread (chunk, mode)
 // composes the affine maps of its chunk of rows, the chunk maps are combined
 // in order, then each chunk is evaluated from its carried-in value.
-template <class R, int MB>
+template <class R, int MB, int NT>
 struct TileScratch {
-  R al[256 / MB][MB];
-  Cplx<R> br[256 / MB][MB];
-  Cplx<R> carry[256 / MB][MB];
-  R wa[MB][8 / MB];        // per-warp composed maps, chained across the warps of one mode
-  Cplx<R> wb[MB][8 / MB];
+  R al[NT / MB][MB];
+  Cplx<R> br[NT / MB][MB];
+  Cplx<R> carry[NT / MB][MB];
+  R wa[MB][NT / 32 / MB];  // per-warp composed maps, chained across the warps of one mode
+  Cplx<R> wb[MB][NT / 32 / MB];
 };
 
-// Exclusive scan of the chunk maps x -> al x + br over the 256 / MB chunks of
+// Exclusive scan of the chunk maps x -> al x + br over the NT / MB chunks of
 // each of the MB wavenumbers: carry[c][m] = the value entering chunk c, in
 // chunk order 0, 1, ... (forward sweep) or from the last chunk down
 // (backward sweep).  One warp composes 32 consecutive maps of one wavenumber
-// with a shuffle scan; the 8 / MB warps of a wavenumber are chained through
-// shared memory.  Called by all 256 threads.
-template <class R, int MB, bool BACK>
-__device__ __forceinline__ void chunk_carries(TileScratch<R, MB>& ts) {
-  constexpr int CH = 256 / MB, WPM = CH / 32;
+// with a shuffle scan; the NT / 32 / MB warps of a wavenumber are chained
+// through shared memory.  Called by all NT threads.
+template <class R, int MB, int NT, bool BACK>
+__device__ __forceinline__ void chunk_carries(TileScratch<R, MB, NT>& ts) {
+  constexpr int CH = NT / MB, WPM = CH / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int mo = w / WPM, seg = w % WPM;
   const int q = seg * 32 + lane;
@@ -368,10 +368,10 @@ __device__ __forceinline__ void chunk_carries(TileScratch<R, MB>& ts) {
 // One CTA solves wavenumbers m0 .. m0 + MB - 1 of run a (smem_raw: tile
 // storage, ts: chunk-map scratch).  The m = 0 column of tile 0 holds zeros
 // and is never stored.
-template <class R, int MB>
+template <class R, int MB, int NT>
 __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, unsigned char* smem_raw,
-                                                TileScratch<R, MB>& ts) {
-  constexpr int CH = 256 / MB;
+                                                TileScratch<R, MB, NT>& ts) {
+  constexpr int CH = NT / MB;
   auto& s_al = ts.al;
   auto& s_br = ts.br;
   auto& s_carry = ts.carry;
@@ -388,12 +388,12 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
     constexpr int RPR = MB * (int)sizeof(R) / RB;        // chunks per row, pivots
     constexpr int CE = CB / (int)sizeof(Cplx<R>) > 0 ? CB / (int)sizeof(Cplx<R>) : 1;
     constexpr int RE = RB / (int)sizeof(R);
-    for (int idx = threadIdx.x; idx < Ny * CPR; idx += 256) {
+    for (int idx = threadIdx.x; idx < Ny * CPR; idx += NT) {
       const int j = idx / CPR, c = idx % CPR;
       const int m = m0 + c * CE;
       if (m < Mp) cp_async_chunk<CB>(d + j * MB + c * CE, spec + (long long)j * Mp + m);
     }
-    for (int idx = threadIdx.x; idx < Ny * RPR; idx += 256) {
+    for (int idx = threadIdx.x; idx < Ny * RPR; idx += NT) {
       const int j = idx / RPR, c = idx % RPR;
       const int m = m0 + c * RE;
       if (m < Mp) cp_async_chunk<RB>(rt + j * MB + c * RE, rf + (long long)j * Mp + m);
@@ -416,7 +416,7 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
   s_al[ch][mo] = al;
   s_br[ch][mo] = br;
   __syncthreads();
-  chunk_carries<R, MB, false>(ts);  // value entering each chunk
+  chunk_carries<R, MB, NT, false>(ts);  // value entering each chunk
   __syncthreads();
   // forward evaluation; compose the backward chunk map on the way
   Cplx<R> x = s_carry[ch][mo];
@@ -434,7 +434,7 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
   s_al[ch][mo] = ab;
   s_br[ch][mo] = bb;
   __syncthreads();
-  chunk_carries<R, MB, true>(ts);  // value just above each chunk, from the top down
+  chunk_carries<R, MB, NT, true>(ts);  // value just above each chunk, from the top down
   __syncthreads();
   x = s_carry[ch][mo];
   for (int j = j1 - 1; j >= j0; --j) {
@@ -444,20 +444,23 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
     d[j * MB + mo] = x;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < Ny * MB; idx += 256) {
+  for (int idx = threadIdx.x; idx < Ny * MB; idx += NT) {
     const int j = idx / MB, mo2 = idx % MB;
     const int m = m0 + mo2;
     if (m >= 1 && m < Mh) spec[(long long)j * Mp + m] = d[idx];
   }
 }
 
+// threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
+constexpr int kTileThreads = 256;
+
 template <class R, int MB>
-__global__ void __launch_bounds__(256) k_modes_tile(PoissonArgs a) {
+__global__ void __launch_bounds__(kTileThreads) k_modes_tile(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ TileScratch<R, MB> ts;
+  __shared__ TileScratch<R, MB, kTileThreads> ts;
   grid_dep_wait();
   grid_dep_launch();
-  modes_tile_body<R, MB>(a, blockIdx.x * MB, smem_raw, ts);
+  modes_tile_body<R, MB, kTileThreads>(a, blockIdx.x * MB, smem_raw, ts);
 }
 
 // Float-float ("double-single") numbers for the FP32 path: value = hi + lo
@@ -708,16 +711,16 @@ __global__ void __launch_bounds__(kMeanThreads) k_mean_mode(PoissonArgs a) {
 }
 
 // Batch kernels: CTAs take (run, tile) items / one CTA per run.
-__global__ void __launch_bounds__(256) k_batch_modes(BatchTables t, int step) {
+__global__ void __launch_bounds__(kTileThreads) k_batch_modes(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ TileScratch<float, kBatchTileModes> ts;
+  __shared__ TileScratch<float, kBatchTileModes, kTileThreads> ts;
   const int n = t.counts[3];
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = t.tile_items[it];
     const BatchRunDesc& rd = t.runs[w.x];
     if (step >= rd.remaining) continue;  // whole CTA
     const PoissonArgs a = rd.pa;
-    modes_tile_body<float, kBatchTileModes>(a, w.y, smem_raw, ts);
+    modes_tile_body<float, kBatchTileModes, kTileThreads>(a, w.y, smem_raw, ts);
     __syncthreads();
   }
 }
@@ -755,10 +758,10 @@ cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
   const int nm = a.Mh;  // tiles start at m = 0
   const bool pdl = a.pdl != 0;
   switch (mb) {
-    case 8: return launch_ex(pdl, k_modes_tile<R, 8>, dim3((nm + 7) / 8), dim3(256), sm, s, a);
-    case 4: return launch_ex(pdl, k_modes_tile<R, 4>, dim3((nm + 3) / 4), dim3(256), sm, s, a);
-    case 2: return launch_ex(pdl, k_modes_tile<R, 2>, dim3((nm + 1) / 2), dim3(256), sm, s, a);
-    default: return launch_ex(pdl, k_modes_tile<R, 1>, dim3(nm), dim3(256), sm, s, a);
+    case 8: return launch_ex(pdl, k_modes_tile<R, 8>, dim3((nm + 7) / 8), dim3(kTileThreads), sm, s, a);
+    case 4: return launch_ex(pdl, k_modes_tile<R, 4>, dim3((nm + 3) / 4), dim3(kTileThreads), sm, s, a);
+    case 2: return launch_ex(pdl, k_modes_tile<R, 2>, dim3((nm + 1) / 2), dim3(kTileThreads), sm, s, a);
+    default: return launch_ex(pdl, k_modes_tile<R, 1>, dim3(nm), dim3(kTileThreads), sm, s, a);
   }
 }
 
@@ -849,7 +852,7 @@ cudaError_t rhoc_t(const void* g, long long plane, int Nx, int Ny, int P, const 
 }  // namespace
 
 cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s) {
-  k_batch_modes<<<grid, 256, t.modes_smem, s>>>(t, step);
+  k_batch_modes<<<grid, kTileThreads, t.modes_smem, s>>>(t, step);
   return cudaGetLastError();
 }
 
