@@ -83,6 +83,8 @@ struct ehd_run {
   void* rfac = nullptr;
   void* rfac0 = nullptr;
   void* tw = nullptr;
+  void* rx_dn = nullptr;  // slab-boundary charge partials of the march form, [Ny/4 + 2][P] each
+  void* rx_up = nullptr;
   float* rch = nullptr;
   double* flux_part = nullptr;
   int nxb = 0;
@@ -223,6 +225,8 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.sf = r->sf;
   a.wall_mode = r->wall_mode;
   a.rhoc_out = r->rhoc;
+  a.rhoc_dn = r->rx_dn;
+  a.rhoc_up = r->rx_up;
   a.slab_rows = r->slab_rows;
   a.nstrips = r->nstrips;
   a.ring_depth = r->ring_depth;
@@ -231,6 +235,8 @@ StepArgs step_args(const ehd_run* r, int cur) {
   return a;
 }
 
+// with_flux: the charge density comes from a step (wall-flux partials
+// pending, and the march form's slab-boundary partials when it ran)
 PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   PoissonArgs a{};
   a.Nx = r->Nx;
@@ -240,6 +246,9 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.Mp = r->Mp;
   a.log2Nx = r->log2Nx;
   a.rhoc = r->rhoc;
+  a.rhoc_dn = r->rx_dn;
+  a.rhoc_up = r->rx_up;
+  a.xslab = (with_flux && r->step_kernel == 0 && r->cols_per_lane == 2) ? r->slab_rows : 0;
   a.inv_eps = 1.0 / r->eps;
   a.spec = r->spec;
   a.spec0 = r->spec0;
@@ -391,6 +400,7 @@ ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
   b += 2 * (size_t)Ny * P * rs;                                // dphi, rho_c
   b += (size_t)Ny * (Mh + 3) * 3 * rs;                         // spectrum, pivots (pitch Mp)
   b += (size_t)Ny * (8 + 8 + 8 + rs + 4) + (size_t)(Nx + 1024) * 2 * rs;  // per-row, twiddles
+  b += 2 * (size_t)(Ny / 4 + 2) * P * rs;                      // slab-boundary charge partials
   b += 64 * 1024;                                              // small buffers
   *bytes = b;
   return EHD_OK;
@@ -509,6 +519,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   // first-pass twiddles of the CTA transform, [k1 < 16][t < 64]
   r->tw = run_alloc(r, (size_t)(Nx + (Nx == 2048 && !r->real_f64 ? 1024 : 0)) * 2 * r->rsz);
   if (shifted) r->rch = static_cast<float*>(run_alloc(r, Ny * sizeof(float)));
+  r->rx_dn = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
+  r->rx_up = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->step_kernel = o.step_kernel;
   r->cols_per_lane = 2;
   r->nstrips = march_strips(Nx, r->cols_per_lane);
@@ -517,7 +529,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
       run_alloc(r, 2 * (size_t)std::max(march_strips(Nx, 1), step_flux_blocks(Nx)) * sizeof(double)));
   r->small = static_cast<double*>(run_alloc(r, 16 * sizeof(double) + 64));
   r->red_part = static_cast<double*>(run_alloc(r, (size_t)reduce_state_blocks() * 6 * sizeof(double)));
-  bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->phibar && r->Ebar && r->spec && r->spec0 &&
+  bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->rx_dn && r->rx_up && r->phibar &&
+            r->Ebar && r->spec && r->spec0 &&
             r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part;
   if (!ok) {
     destroy_quiet(r);
@@ -661,7 +674,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
   if (!r) return fail(EHD_EINVAL, "run is NULL");
   switch (param) {
     case EHD_TUNE_SLAB_ROWS:
-      if (value < 1 || value > r->Ny) return fail(EHD_EINVAL, "slab rows must be in [1, Ny]");
+      if (value < std::min(4, r->Ny) || value > r->Ny) return fail(EHD_EINVAL, "slab rows must be in [min(4, Ny), Ny]");
       r->slab_rows = value;
       break;
     case EHD_TUNE_RING_DEPTH:
@@ -1147,6 +1160,7 @@ ehd_status ehd_batch_tick(ehd_batch* b, int steps) {
     }
     d.pa = poisson_args(r, true);
     d.pa.nflux = d.sa[0].nstrips;
+    d.pa.xslab = b->slab_rows;
     d.cur0 = r->cur;
     d.remaining = (int)std::min<long>(steps, b->remaining[i]);
     d.E = r->Nx / 64;
@@ -1210,7 +1224,8 @@ ehd_status ehd_batch_tune(ehd_batch* b, int param, int value) {
   if (!b) return fail(EHD_EINVAL, "batch is NULL");
   switch (param) {
     case EHD_BATCH_SLAB_ROWS:
-      if (value < 0 || value > b->max_ny) return fail(EHD_EINVAL, "slab rows must be in [0, max_ny]");
+      if (value != 0 && (value < 4 || value > b->max_ny))
+        return fail(EHD_EINVAL, "slab rows must be 0 (automatic) or in [4, max_ny]");
       b->slab_rows_fixed = value;
       b->dirty = true;
       break;

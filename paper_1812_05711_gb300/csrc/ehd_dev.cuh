@@ -102,7 +102,9 @@ struct StepArgs {
   double mub, rho0, sf;      // ion mobility, injected density, f shift (1 or 0)
   int wall_mode;
   // march form only
-  void* rhoc_out;            // R [Ny][P]: rho_c of the new state
+  void* rhoc_out;            // R [Ny][P]: rho_c of the new state (slab-boundary rows: partial, see rhoc_dn)
+  void* rhoc_dn;             // R [nslab][P]: row b*slab_rows - 1, charge of the populations pushed down by slab b
+  void* rhoc_up;             // R [nslab][P]: row b*slab_rows, charge of the populations pushed up by slab b - 1
   int slab_rows;             // rows per warp slab
   int nstrips;               // 32-column strips (30 owned columns each)
   int ring_depth;            // rows staged ahead by cp.async (2, 3, 4 or 6)
@@ -114,6 +116,9 @@ struct PoissonArgs {
   int Nx, Ny, P, Mh, log2Nx;
   int Mp;                    // row pitch of the spectrum and pivot tables (Mh rounded up to 4)
   const void* rhoc;          // charge density, R [Ny][P]
+  const void* rhoc_dn;       // slab-boundary partials of the march form (see StepArgs), added to rhoc
+  const void* rhoc_up;
+  int xslab;                 // slab height of those partials; 0: rhoc is complete
   double inv_eps;            // 1 / eps
   void* spec;                // half spectrum, complex R [Ny][Mp]
   void* spec0;               // row sums (m = 0), [Ny]: double, or float (hi, lo) pairs when R = float
@@ -132,6 +137,22 @@ struct PoissonArgs {
   int pdl;                   // launch the main-stream kernels with programmatic dependent launch
   int fft_cta;               // rows of 2048: one CTA of 64 threads per row (else one warp per row)
 };
+
+// Charge density of row y as the Poisson solve sees it: the step kernel's
+// march form leaves, at each slab boundary, the populations that cross it to
+// the slab that computed them, together with their share of the new charge
+// density (rhoc_dn for the row below the boundary, rhoc_up for the row
+// above).  The readers add main + dn + up, in this order.
+template <class R>
+__device__ __forceinline__ void rhoc_partials(const PoissonArgs& a, int y, const R*& dn, const R*& up) {
+  dn = nullptr;
+  up = nullptr;
+  if (a.xslab > 0) {
+    const int S = a.xslab;
+    if ((y + 1) % S == 0 && y + 1 < a.Ny) dn = static_cast<const R*>(a.rhoc_dn) + (long long)((y + 1) / S) * a.P;
+    if (y % S == 0 && y > 0) up = static_cast<const R*>(a.rhoc_up) + (long long)(y / S) * a.P;
+  }
+}
 
 struct FieldArgs {
   int Nx, Ny, P;

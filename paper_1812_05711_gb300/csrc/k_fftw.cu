@@ -121,12 +121,24 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
   constexpr int L = 32 * E, N = 2 * L;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
   const float2* rc2 = reinterpret_cast<const float2*>(static_cast<const float*>(a.rhoc) + (long long)y * a.P);
+  const float *rdn, *rup;
+  rhoc_partials<float>(a, y, rdn, rup);
   const float ieps = (float)a.inv_eps;
   float re[E], im[E];
   float shi = 0.0f, slo = 0.0f;
 #pragma unroll
   for (int n2 = 0; n2 < E; ++n2) {
-    const float2 v = rc2[lane + 32 * n2];
+    float2 v = rc2[lane + 32 * n2];
+    if (rdn) {
+      const float2 d = reinterpret_cast<const float2*>(rdn)[lane + 32 * n2];
+      v.x += d.x;
+      v.y += d.y;
+    }
+    if (rup) {
+      const float2 u = reinterpret_cast<const float2*>(rup)[lane + 32 * n2];
+      v.x += u.x;
+      v.y += u.y;
+    }
     re[n2] = -v.x * ieps;
     im[n2] = -v.y * ieps;
     float s, e;
@@ -367,15 +379,29 @@ __global__ void __launch_bounds__(kCtaT) k_rfft_cta(PoissonArgs a) {
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
   const float* row = static_cast<const float*>(a.rhoc) + (long long)y * a.P;
   const float2* rc2 = reinterpret_cast<const float2*>(row);
+  const float *rdn, *rup;
+  rhoc_partials<float>(a, y, rdn, rup);
   const float nieps = -(float)a.inv_eps;
   // A row constant c0 is taken out before the transform: the differences are
   // exact (Sterbenz) and small, so the transform's rounding scales with the
   // row's variation, and only the m = 0 bin depends on c0.
-  const float c0 = __ldg(row);
+  float c0 = __ldg(row);
+  if (rdn) c0 += __ldg(rdn);
+  if (rup) c0 += __ldg(rup);
   float re[16], im[16];
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1) {
-    const float2 v = rc2[t + 64 * n1];
+    float2 v = rc2[t + 64 * n1];
+    if (rdn) {
+      const float2 d = reinterpret_cast<const float2*>(rdn)[t + 64 * n1];
+      v.x += d.x;
+      v.y += d.y;
+    }
+    if (rup) {
+      const float2 u = reinterpret_cast<const float2*>(rup)[t + 64 * n1];
+      v.x += u.x;
+      v.y += u.y;
+    }
     re[n1] = (v.x - c0) * nieps;
     im[n1] = (v.y - c0) * nieps;
   }

@@ -494,7 +494,15 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
   const R mub = (R)a.mub, rho0 = (R)a.rho0, sf = (R)a.sf;
   const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
   const R W1 = (R)kW1, W2 = (R)kW2;
-  const int rs = max(y0 - 1, 0), re = min(y1, Ny - 1);
+  // the walk covers the slab's own rows; populations that cross a slab
+  // boundary are written by the slab that computes them (pushed into the
+  // neighbouring slab's first or last row), with their share of that row's
+  // charge density in rhoc_dn / rhoc_up, so no slab reads its neighbours' rows
+  const int rs = y0, re = y1 - 1;
+  const bool push_dn = y0 > 0, push_up = y1 < Ny;
+  R* __restrict__ rx_dn = static_cast<R*>(a.rhoc_dn);
+  R* __restrict__ rx_up = static_cast<R*>(a.rhoc_up);
+  R sy_last = R(0);
 
   // carried rows, [k][j]: H (c_y = 0) of row r-1, U (c_y = +1) of rows r-1, r
   R Hm[6][2] = {}, Um[6][2] = {}, Uc[6][2] = {};
@@ -633,72 +641,97 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
                  ((double)Store<S>::rt(n6) - (double)Store<S>::rt(g8c[j]));
       }
     }
-    if (r - 1 >= y0 && owned) {
-      // c_y = -1 completes row r - 1
+    // c_y = -1: populations of row r moving down into row r - 1
+    R n4[2], n7[2], n8[2];
+    {
       const R sh = sy - s_dn;
-      const long long c = row - P + xc;
-      R n4[2], n7[2], n8[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         n4[j] = g4c[j] + W1 * sh;
         n7[j] = Pg7[j] + W2 * sh;
         n8[j] = Pg8[j] + W2 * sh;
       }
+    }
+    if (r > y0 && owned) {
+      // the down-movers complete row r - 1; its up-movers came from below the
+      // slab (pushed there) when r - 1 is the first row of a slab above y = 0
+      const bool ups = !(r - 1 == y0 && push_dn);
+      const long long c = row - P + xc;
       Pair<S>::st(fo + c, Hm[0][0], Hm[0][1]);
       Pair<S>::st(fo + pl + c, Hm[1][0], Hm[1][1]);
-      Pair<S>::st(fo + 2 * pl + c, Um[0][0], Um[0][1]);
       Pair<S>::st(fo + 3 * pl + c, Hm[2][0], Hm[2][1]);
       Pair<S>::st(fo + 4 * pl + c, f4c[0], f4c[1]);
-      Pair<S>::st(fo + 5 * pl + c, Um[1][0], Um[1][1]);
-      Pair<S>::st(fo + 6 * pl + c, Um[2][0], Um[2][1]);
       Pair<S>::st(fo + 7 * pl + c, Pf7[0], Pf7[1]);
       Pair<S>::st(fo + 8 * pl + c, Pf8[0], Pf8[1]);
       Pair<S>::st(go + c, Hm[3][0], Hm[3][1]);
       Pair<S>::st(go + pl + c, Hm[4][0], Hm[4][1]);
-      Pair<S>::st(go + 2 * pl + c, Um[3][0], Um[3][1]);
       Pair<S>::st(go + 3 * pl + c, Hm[5][0], Hm[5][1]);
       Pair<S>::st(go + 4 * pl + c, n4[0], n4[1]);
-      Pair<S>::st(go + 5 * pl + c, Um[4][0], Um[4][1]);
-      Pair<S>::st(go + 6 * pl + c, Um[5][0], Um[5][1]);
+      Pair<S>::st(go + 7 * pl + c, n7[0], n7[1]);
+      Pair<S>::st(go + 8 * pl + c, n8[0], n8[1]);
+      if (ups) {
+        Pair<S>::st(fo + 2 * pl + c, Um[0][0], Um[0][1]);
+        Pair<S>::st(fo + 5 * pl + c, Um[1][0], Um[1][1]);
+        Pair<S>::st(fo + 6 * pl + c, Um[2][0], Um[2][1]);
+        Pair<S>::st(go + 2 * pl + c, Um[3][0], Um[3][1]);
+        Pair<S>::st(go + 5 * pl + c, Um[4][0], Um[4][1]);
+        Pair<S>::st(go + 6 * pl + c, Um[5][0], Um[5][1]);
+      }
+      R q[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const R h = (Store<S>::rt(Hm[3][j]) + Store<S>::rt(Hm[4][j])) + Store<S>::rt(Hm[5][j]);
+        const R d = (Store<S>::rt(n4[j]) + Store<S>::rt(n7[j])) + Store<S>::rt(n8[j]);
+        const R u = ups ? (Store<S>::rt(Um[3][j]) + Store<S>::rt(Um[4][j])) + Store<S>::rt(Um[5][j]) : R(0);
+        q[j] = s_dn + ((h + u) + d);
+      }
+      Pair<R>::st(rho_out + c, q[0], q[1]);
+    }
+    if (r == y0 && push_dn && owned) {
+      // push the down-movers of the slab's first row into the row below
+      const long long c = row - P + xc;
+      Pair<S>::st(fo + 4 * pl + c, f4c[0], f4c[1]);
+      Pair<S>::st(fo + 7 * pl + c, Pf7[0], Pf7[1]);
+      Pair<S>::st(fo + 8 * pl + c, Pf8[0], Pf8[1]);
+      Pair<S>::st(go + 4 * pl + c, n4[0], n4[1]);
       Pair<S>::st(go + 7 * pl + c, n7[0], n7[1]);
       Pair<S>::st(go + 8 * pl + c, n8[0], n8[1]);
       R q[2];
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
-        q[j] = s_dn + (((Store<S>::rt(Hm[3][j]) + Store<S>::rt(Hm[4][j])) +
-                        (Store<S>::rt(Um[3][j]) + Store<S>::rt(Hm[5][j]))) +
-                       ((Store<S>::rt(n4[j]) + Store<S>::rt(Um[4][j])) +
-                        (Store<S>::rt(Um[5][j]) + Store<S>::rt(n7[j]))) +
-                       Store<S>::rt(n8[j]));
-      Pair<R>::st(rho_out + c, q[0], q[1]);
+      for (int j = 0; j < 2; ++j) q[j] = (Store<S>::rt(n4[j]) + Store<S>::rt(n7[j])) + Store<S>::rt(n8[j]);
+      Pair<R>::st(rx_dn + (long long)slab * P + xc, q[0], q[1]);
     }
-    if (r == Ny - 1 && r >= y0 && r < y1 && owned) {
+    if (r == Ny - 1 && owned) {
       // collector: f bounces back; g leaves and re-enters from its own row
+      const bool ups = !(r == y0 && push_dn);
       const long long c = row + xc;
       Pair<S>::st(fo + c, f0c[0], f0c[1]);
       Pair<S>::st(fo + pl + c, Pf1[0], Pf1[1]);
-      Pair<S>::st(fo + 2 * pl + c, Uc[0][0], Uc[0][1]);
       Pair<S>::st(fo + 3 * pl + c, Pf3[0], Pf3[1]);
       Pair<S>::st(fo + 4 * pl + c, f2c[0], f2c[1]);
-      Pair<S>::st(fo + 5 * pl + c, Uc[1][0], Uc[1][1]);
-      Pair<S>::st(fo + 6 * pl + c, Uc[2][0], Uc[2][1]);
       Pair<S>::st(fo + 7 * pl + c, f5c[0], f5c[1]);
       Pair<S>::st(fo + 8 * pl + c, f6c[0], f6c[1]);
       Pair<S>::st(go + c, g0c[0], g0c[1]);
       Pair<S>::st(go + pl + c, Pg1[0], Pg1[1]);
-      Pair<S>::st(go + 2 * pl + c, Uc[3][0], Uc[3][1]);
       Pair<S>::st(go + 3 * pl + c, Pg3[0], Pg3[1]);
       Pair<S>::st(go + 4 * pl + c, g4c[0], g4c[1]);
-      Pair<S>::st(go + 5 * pl + c, Uc[4][0], Uc[4][1]);
-      Pair<S>::st(go + 6 * pl + c, Uc[5][0], Uc[5][1]);
       Pair<S>::st(go + 7 * pl + c, Pg7[0], Pg7[1]);
       Pair<S>::st(go + 8 * pl + c, Pg8[0], Pg8[1]);
+      if (ups) {
+        Pair<S>::st(fo + 2 * pl + c, Uc[0][0], Uc[0][1]);
+        Pair<S>::st(fo + 5 * pl + c, Uc[1][0], Uc[1][1]);
+        Pair<S>::st(fo + 6 * pl + c, Uc[2][0], Uc[2][1]);
+        Pair<S>::st(go + 2 * pl + c, Uc[3][0], Uc[3][1]);
+        Pair<S>::st(go + 5 * pl + c, Uc[4][0], Uc[4][1]);
+        Pair<S>::st(go + 6 * pl + c, Uc[5][0], Uc[5][1]);
+      }
       R q[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        q[j] = sy + (((Store<S>::rt(g0c[j]) + Store<S>::rt(Pg1[j])) + (Store<S>::rt(Uc[3][j]) + Store<S>::rt(Pg3[j]))) +
-                     ((Store<S>::rt(g4c[j]) + Store<S>::rt(Uc[4][j])) + (Store<S>::rt(Uc[5][j]) + Store<S>::rt(Pg7[j]))) +
-                     Store<S>::rt(Pg8[j]));
+        const R h = (Store<S>::rt(g0c[j]) + Store<S>::rt(Pg1[j])) + Store<S>::rt(Pg3[j]);
+        const R d = (Store<S>::rt(g4c[j]) + Store<S>::rt(Pg7[j])) + Store<S>::rt(Pg8[j]);
+        const R u = ups ? (Store<S>::rt(Uc[3][j]) + Store<S>::rt(Uc[4][j])) + Store<S>::rt(Uc[5][j]) : R(0);
+        q[j] = sy + ((h + u) + d);
         qout += ((double)Store<S>::rt(g2c[j]) + (double)Store<S>::rt(g5c[j])) + (double)Store<S>::rt(g6c[j]);
         qout -= ((double)Store<S>::rt(g4c[j]) + (double)Store<S>::rt(g7c[j])) + (double)Store<S>::rt(g8c[j]);
       }
@@ -720,8 +753,46 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       pm[j] = pc[j];
       pc[j] = pn[j];
     }
+    sy_last = sy;
   }
   cp_async_wait<0>();
+  if (push_up && owned) {
+    // the slab's last row lacks only its down-movers (pushed by the slab
+    // above); its own up-movers go into the first row of the slab above
+    const bool ups = !(re == y0 && push_dn);
+    const long long c = (long long)re * P + xc;
+    Pair<S>::st(fo + c, Hm[0][0], Hm[0][1]);
+    Pair<S>::st(fo + pl + c, Hm[1][0], Hm[1][1]);
+    Pair<S>::st(fo + 3 * pl + c, Hm[2][0], Hm[2][1]);
+    Pair<S>::st(go + c, Hm[3][0], Hm[3][1]);
+    Pair<S>::st(go + pl + c, Hm[4][0], Hm[4][1]);
+    Pair<S>::st(go + 3 * pl + c, Hm[5][0], Hm[5][1]);
+    if (ups) {
+      Pair<S>::st(fo + 2 * pl + c, Um[0][0], Um[0][1]);
+      Pair<S>::st(fo + 5 * pl + c, Um[1][0], Um[1][1]);
+      Pair<S>::st(fo + 6 * pl + c, Um[2][0], Um[2][1]);
+      Pair<S>::st(go + 2 * pl + c, Um[3][0], Um[3][1]);
+      Pair<S>::st(go + 5 * pl + c, Um[4][0], Um[4][1]);
+      Pair<S>::st(go + 6 * pl + c, Um[5][0], Um[5][1]);
+    }
+    R q[2], e[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const R h = (Store<S>::rt(Hm[3][j]) + Store<S>::rt(Hm[4][j])) + Store<S>::rt(Hm[5][j]);
+      const R u = ups ? (Store<S>::rt(Um[3][j]) + Store<S>::rt(Um[4][j])) + Store<S>::rt(Um[5][j]) : R(0);
+      q[j] = sy_last + (h + u);
+      e[j] = (Store<S>::rt(Uc[3][j]) + Store<S>::rt(Uc[4][j])) + Store<S>::rt(Uc[5][j]);
+    }
+    Pair<R>::st(rho_out + c, q[0], q[1]);
+    const long long cu = c + P;
+    Pair<S>::st(fo + 2 * pl + cu, Uc[0][0], Uc[0][1]);
+    Pair<S>::st(fo + 5 * pl + cu, Uc[1][0], Uc[1][1]);
+    Pair<S>::st(fo + 6 * pl + cu, Uc[2][0], Uc[2][1]);
+    Pair<S>::st(go + 2 * pl + cu, Uc[3][0], Uc[3][1]);
+    Pair<S>::st(go + 5 * pl + cu, Uc[4][0], Uc[4][1]);
+    Pair<S>::st(go + 6 * pl + cu, Uc[5][0], Uc[5][1]);
+    Pair<R>::st(rx_up + (long long)(slab + 1) * P + xc, e[0], e[1]);
+  }
   if (bad) atomicOr(a.err, 1);
   if (y0 == 0) {
     double v = qin;

@@ -162,21 +162,25 @@ __global__ void __launch_bounds__(256) k_rfft_rows(PoissonArgs a) {
   const Cplx<R>* gtw = static_cast<const Cplx<R>*>(a.tw);
   for (int q = threadIdx.x; q < N; q += 256) stw[q] = gtw[q];
   const R* __restrict__ rc = static_cast<const R*>(a.rhoc) + (long long)(live ? y : 0) * a.P;
+  const R *rdn, *rup;
+  rhoc_partials<R>(a, live ? y : 0, rdn, rup);
   const R ieps = (R)a.inv_eps;
   // s = -rho_c / eps packed as complex pairs; per-thread partial sum
   R part = R(0);
   for (int n = tr; n < L; n += T) {
     R s0 = R(0), s1 = R(0);
     if (live) {
-      if constexpr (sizeof(R) == 4) {
-        const float2 v = reinterpret_cast<const float2*>(rc)[n];
-        s0 = -v.x * ieps;
-        s1 = -v.y * ieps;
-      } else {
-        const double2 v = reinterpret_cast<const double2*>(rc)[n];
-        s0 = -v.x * ieps;
-        s1 = -v.y * ieps;
+      R v0 = rc[2 * n], v1 = rc[2 * n + 1];
+      if (rdn) {
+        v0 += rdn[2 * n];
+        v1 += rdn[2 * n + 1];
       }
+      if (rup) {
+        v0 += rup[2 * n];
+        v1 += rup[2 * n + 1];
+      }
+      s0 = -v0 * ieps;
+      s1 = -v1 * ieps;
     }
     A[pidx(n)] = {s0, s1};
     part += s0 + s1;

@@ -242,3 +242,21 @@ def test_march_and_node_parallel_forms_agree(storage, tol):
     ftol = 1e-11 if storage == "f64" else 1e-6
     assert d1["q_in"] == pytest.approx(d2["q_in"], rel=ftol)
     assert d1["q_out"] == pytest.approx(d2["q_out"], rel=ftol)
+
+
+@gpu
+@pytest.mark.parametrize("slab", [4, 5, 17, 51, 52])
+def test_slab_heights_fp64_parity(slab):
+    """The march form walks slabs of rows and pushes the populations that
+    cross a slab boundary into the neighbouring slab's rows (with their share
+    of the charge density); every slab height, including a one-row slab at
+    the collector (51 of 52 rows), gives the oracle's state."""
+    w = wl.small_channel(64, seed=29)
+    ehd, p, s, run = _pair(w, u_ion=5e-3)
+    ehd.ehd_tune(run.handle, "slab_rows", slab)
+    run.step(120)
+    o.step(s, 120)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, (slab, e)
+    F = o.fields(s)
+    assert run.diagnostics()["charge"] == pytest.approx(F["rho_c"].sum(), rel=1e-13)

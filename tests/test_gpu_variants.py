@@ -81,3 +81,31 @@ def test_x_symbol_changes_the_solution():
     assert np.abs(A["Ex"] - B["Ex"]).max() > 1e-9 * np.abs(A["Ex"]).max()
     for r in runs:
         r.close()
+
+
+@gpu
+def test_launch_shape_knobs_keep_results():
+    """ehd_tune only changes how work is cut and launched: programmatic
+    dependent launch is bitwise neutral; the warp-per-row transforms and
+    other tile widths agree with the defaults to FP32 rounding."""
+    ehd = _ehd()
+    amp, ph = wl.roll(23, 1e-2)
+    w = wl.Workload("knobs-2048x40", 2048, 40, 190.0, amp=amp, phase=ph)
+
+    def run_with(**tune):
+        r = ehd.Run(*w.args(), storage="f32", amp=w.amp, phase=w.phase)
+        for k, v in tune.items():
+            ehd.ehd_tune(r.handle, k, v)
+        r.step(40)
+        F = r.fields()
+        r.close()
+        return F
+
+    base = run_with()
+    pdl = run_with(pdl=1)
+    for k in base:
+        assert np.array_equal(base[k], pdl[k]), k
+    p = o.setup(*w.args())
+    for tune in (dict(fft_cta=0), dict(tile_modes=4), dict(tile_modes=1), dict(step_kernel=1)):
+        e = _scaled_err(p, run_with(**tune), base)
+        assert e <= 2e-6, (tune, e)
