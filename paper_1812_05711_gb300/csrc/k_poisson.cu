@@ -528,42 +528,69 @@ struct MeanNum<float> {
   __device__ static T down(T a, int o) { return ff_shfl_down(a, o); }
 };
 
-// m = 0 (NT threads, one row chunk each; chunk maps combined by a warp
-// shuffle scan and a shuffle scan over the warps) + the step's wall fluxes.
+// m = 0 (the row means) + the step's wall fluxes.  For m = 0 the system of
+// Eq. 25 is the 1-D discrete Poisson equation phi_{j-1} - 2 phi_j + phi_{j+1}
+// = s_j with the wall ghosts of the closure, whose solution is a double
+// prefix sum: with D_j = phi_{j+1} - phi_j (j = -1 .. Ny-1),
+//   D_j = D_{-1} + S_j,  S_j = sum_{k<=j} s_k,
+//   phi_j = phi_{-1} + (j+1) D_{-1} + T_j,  T_j = sum_{k<j} S_k,
+// and the two wall conditions fix phi_{-1} and D_{-1}.  Both sums are block
+// scans (per-thread chunks, warp shuffles, one warp over the warp totals).
 // Arithmetic: FP64 on the plain FP64 path, float-float on the FP32 path.
+// Barrier among the first NT threads of the CTA (all of it when the CTA has
+// NT threads): the mean mode may run on a sub-block of a larger CTA.
+template <int NT>
+__device__ __forceinline__ void sub_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"n"(NT) : "memory");
+}
+
 template <class R, int NT>
 struct MeanScratch {
   static constexpr int NW = NT / 32;
-  typename MeanNum<R>::T wa[NW], wb[NW], wc_in[NW];
+  typename MeanNum<R>::T wsum[NW], woff[NW], tot[2];
   double fq[2][NW];
 };
 
-// Exclusive scan over the warps of the warp totals (wa, wb) of the chunk maps
-// x -> a x + b: wc_in[w] = value entering warp w's first chunk (in the sweep
-// direction: warp 0 first, or the last warp first when BACK).  Warp 0 only.
-template <class R, int NT, bool BACK>
-__device__ __forceinline__ void mean_warp_carries(MeanScratch<R, NT>& ms) {
+// Inclusive prefix sum of v[0..Ny) in place (all NT threads; chunk [j0, j1)
+// per thread); returns the total.
+template <class R, int NT>
+__device__ __forceinline__ typename MeanNum<R>::T block_prefix_sum(typename MeanNum<R>::T* v, int j0, int j1,
+                                                                   MeanScratch<R, NT>& ms) {
   using N = MeanNum<R>;
   using T = typename N::T;
   constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31;
-  const T one = N::from_f(1.0f), zero = N::from_f(0.0f);
-  const int w = BACK ? NW - 1 - lane : lane;
-  T al = one, br = zero;
-  if (lane < NW) {
-    al = ms.wa[w];
-    br = ms.wb[w];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  T acc = N::from_f(0.0f);
+  for (int j = j0; j < j1; ++j) {
+    acc = N::add(acc, v[j]);
+    v[j] = acc;
   }
-  for (int o = 1; o < NW; o <<= 1) {
-    const T a2 = N::up(al, o), b2 = N::up(br, o);
-    if (lane >= o) {
-      br = N::add(N::mul(al, b2), br);
-      al = N::mul(al, a2);
+  T incl = acc;  // inclusive scan of the chunk totals over the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = N::up(incl, o);
+    if (lane >= o) incl = N::add(incl, u);
+  }
+  if (lane == 31) ms.wsum[warp] = incl;
+  sub_sync<NT>();
+  if (warp == 0) {
+    T w = lane < NW ? ms.wsum[lane] : N::from_f(0.0f);
+    for (int o = 1; o < NW; o <<= 1) {
+      const T u = N::up(w, o);
+      if (lane >= o) w = N::add(w, u);
     }
+    T ex = N::up(w, 1);
+    if (lane == 0) ex = N::from_f(0.0f);
+    if (lane < NW) ms.woff[lane] = ex;
+    if (lane == NW - 1) ms.tot[0] = w;
   }
-  T eb = N::up(br, 1);
-  if (lane == 0) eb = zero;
-  if (lane < NW) ms.wc_in[w] = eb;
+  sub_sync<NT>();
+  T ex = N::up(incl, 1);  // chunks of the earlier lanes of this warp
+  if (lane == 0) ex = N::from_f(0.0f);
+  const T off = N::add(ms.woff[warp], ex);
+  for (int j = j0; j < j1; ++j) v[j] = N::add(v[j], off);
+  const T total = ms.tot[0];
+  sub_sync<NT>();
+  return total;
 }
 
 template <class R, int NT>
@@ -572,11 +599,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   using N = MeanNum<R>;
   using T = typename N::T;
   constexpr int NW = NT / 32;
-  auto& wa = ms.wa;
-  auto& wb = ms.wb;
-  auto& wc_in = ms.wc_in;
-  T* d = reinterpret_cast<T*>(smem_raw);  // [Ny] right-hand side, then solution
-  T* r = d + a.Ny;                        // [Ny] reciprocal pivots
+  T* v = reinterpret_cast<T*>(smem_raw);  // [Ny]: s, then S, then T
   const int Ny = a.Ny, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (a.flux_part) {
     // FP64 totals of the wall fluxes: a shuffle tree over the strips
@@ -594,7 +617,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
       fq[0][warp] = qi;
       fq[1][warp] = qo;
     }
-    __syncthreads();
+    sub_sync<NT>();
     if (t == 0) {
       double si = 0.0, so = 0.0;
       for (int w = 0; w < NW; ++w) {
@@ -605,113 +628,67 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
       a.flux_acc[1] += so;
     }
   }
-  const float lift = (a.wall_mode == 0 ? 2.0f : 1.0f) * (float)a.Nx * (float)a.phi0;  // exact
   for (int j = t; j < Ny; j += NT) {
-    T v, p;
     if constexpr (sizeof(R) == 8) {
-      v = static_cast<const double*>(a.spec0)[j];
-      p = static_cast<const double*>(a.rfac0)[j];
+      v[j] = static_cast<const double*>(a.spec0)[j];
     } else {
-      const float2 sv = static_cast<const float2*>(a.spec0)[j], pv = static_cast<const float2*>(a.rfac0)[j];
-      v = {sv.x, sv.y};
-      p = {pv.x, pv.y};
+      const float2 sv = static_cast<const float2*>(a.spec0)[j];
+      v[j] = {sv.x, sv.y};
     }
-    if (j == 0) v = N::add(v, N::from_f(-lift));
-    d[j] = v;
-    r[j] = p;
   }
-  __syncthreads();
-  const T one = N::from_f(1.0f), zero = N::from_f(0.0f);
+  sub_sync<NT>();
   const int C = (Ny + NT - 1) / NT;
   const int j0 = min(t * C, Ny), j1 = min(j0 + C, Ny);
-  // forward elimination d'_j = r_j (d_j - d'_{j-1}): chunk map x -> al x + br
-  T al = one, br = zero;
-  for (int j = j0; j < j1; ++j) {
-    al = N::mul(N::neg(r[j]), al);
-    br = N::mul(r[j], N::add(d[j], N::neg(br)));
+  T* Sv = v + Ny;  // [Ny]: copy of S
+  // S_j (inclusive), kept in Sv; then v[j] = sum_{k<=j} S_k = T_{j+1}
+  block_prefix_sum<R, NT>(v, j0, j1, ms);
+  for (int j = j0; j < j1; ++j) Sv[j] = v[j];
+  const T T_all = block_prefix_sum<R, NT>(v, j0, j1, ms);   // T_Ny
+  const T T_last = (Ny >= 2) ? v[Ny - 2] : N::from_f(0.0f);  // T_{Ny-1}
+  // wall values in spectral units: W = Nx phi0 at the injector, 0 at the collector
+  const T W = N::mul(N::from_f((float)a.Nx), N::from_f((float)a.phi0));
+  T Dm, Pm;  // D_{-1}, phi_{-1}
+  if (a.wall_mode == 0) {
+    // phi_{-1} + phi_0 = 2W, phi_Ny + phi_{Ny-1} = 0
+    const T num = N::add(N::add(W, W), N::add(T_all, T_last));
+    Dm = N::mul(N::neg(num), N::from(1.0 / (2.0 * Ny)));
+    Pm = N::add(W, N::neg(N::mul(Dm, N::from_f(0.5f))));
+  } else {
+    // phi_{-1} = W, phi_Ny = 0
+    Dm = N::mul(N::neg(N::add(W, T_all)), N::from(1.0 / (double)(Ny + 1)));
+    Pm = W;
   }
-  for (int o = 1; o < 32; o <<= 1) {
-    const T a2 = N::up(al, o), b2 = N::up(br, o);
-    if (lane >= o) {
-      br = N::add(N::mul(al, b2), br);
-      al = N::mul(al, a2);
-    }
-  }
-  if (lane == 31) {
-    wa[warp] = al;
-    wb[warp] = br;
-  }
-  __syncthreads();
-  if (warp == 0) mean_warp_carries<R, NT, false>(ms);
-  __syncthreads();
-  T ex_a = N::up(al, 1), ex_b = N::up(br, 1);
-  if (lane == 0) {
-    ex_a = one;
-    ex_b = zero;
-  }
-  T x = N::add(N::mul(ex_a, wc_in[warp]), ex_b);
-  // evaluate; compose the back-substitution map x_j = d'_j - r_j x_{j+1}
-  T ab = one, bb = zero;
-  for (int j = j0; j < j1; ++j) {
-    x = N::mul(r[j], N::add(d[j], N::neg(x)));
-    d[j] = x;
-    bb = N::add(bb, N::mul(ab, x));
-    ab = N::mul(N::neg(ab), r[j]);
-  }
-  for (int o = 1; o < 32; o <<= 1) {
-    const T a2 = N::down(ab, o), b2 = N::down(bb, o);
-    if (lane + o < 32) {
-      bb = N::add(N::mul(ab, b2), bb);
-      ab = N::mul(ab, a2);
-    }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    wa[warp] = ab;
-    wb[warp] = bb;
-  }
-  __syncthreads();
-  if (warp == 0) mean_warp_carries<R, NT, true>(ms);
-  __syncthreads();
-  T fa = N::down(ab, 1), fb = N::down(bb, 1);
-  if (lane == 31) {
-    fa = one;
-    fb = zero;
-  }
-  x = N::add(N::mul(fa, wc_in[warp]), fb);
-  for (int j = j1 - 1; j >= j0; --j) {
-    x = N::add(d[j], N::neg(N::mul(r[j], x)));
-    d[j] = x;
-  }
-  __syncthreads();
-  // phibar = x / Nx (Nx a power of two: exact scaling), E_y = -(phibar_{j+1} - phibar_{j-1}) / 2
+  // phi_j = phi_{-1} + (j+1) D_{-1} + T_j,  E_j = -(2 D_{-1} + S_j + S_{j-1}) / 2
   const T inN = N::from_f(1.0f / (float)a.Nx);
   R* Ebar = static_cast<R*>(a.Ebar);
-  const T half = N::from_f(0.5f);
-  const T phi0 = N::from_f((float)a.phi0);
-  for (int j = t; j < Ny; j += NT) {
-    const T pc = N::mul(d[j], inN);
-    const T pd = (j > 0) ? N::mul(d[j - 1], inN)
-                         : ((a.wall_mode == 0) ? N::add(N::add(phi0, phi0), N::neg(pc)) : phi0);
-    const T pu = (j < Ny - 1) ? N::mul(d[j + 1], inN) : ((a.wall_mode == 0) ? N::neg(pc) : zero);
-    const T ey = N::mul(N::neg(half), N::add(pu, N::neg(pd)));
+  const T mhalf = N::from_f(-0.5f);
+  for (int j = j0; j < j1; ++j) {
+    const T Tj = (j > 0) ? v[j - 1] : N::from_f(0.0f);
+    const T Sj = Sv[j], Sjm1 = (j > 0) ? Sv[j - 1] : N::from_f(0.0f);
+    const T phi = N::add(N::add(Pm, N::mul(N::from((double)(j + 1)), Dm)), Tj);
+    const T ey = N::mul(mhalf, N::add(N::add(Dm, Dm), N::add(Sj, Sjm1)));
+    const T pc = N::mul(phi, inN), ec = N::mul(ey, inN);
     if constexpr (sizeof(R) == 8) {
       static_cast<double*>(a.phibar)[j] = pc;
-      Ebar[j] = ey;
+      Ebar[j] = ec;
     } else {
       static_cast<float2*>(a.phibar)[j] = make_float2(pc.hi, pc.lo);
-      Ebar[j] = ey.hi + ey.lo;
+      Ebar[j] = ec.hi + ec.lo;
     }
   }
 }
 
+// threads of the mean mode: 128 up to 1024 rows (shorter scans over the
+// warps), 512 above (shorter per-thread chunks)
 constexpr int kMeanThreads = 512;
+constexpr int kMeanThreadsSmall = 128;
+constexpr int kMeanSmallRows = 1024;
 
-template <class R>
-__global__ void __launch_bounds__(kMeanThreads) k_mean_mode(PoissonArgs a) {
+template <class R, int NT>
+__global__ void __launch_bounds__(NT) k_mean_mode(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ MeanScratch<R, kMeanThreads> ms;
-  mean_mode_body<R, kMeanThreads>(a, smem_raw, ms);
+  __shared__ MeanScratch<R, NT> ms;
+  mean_mode_body<R, NT>(a, smem_raw, ms);
 }
 
 // Batch kernels: CTAs take (run, tile) items / one CTA per run.
@@ -732,12 +709,17 @@ __global__ void __launch_bounds__(kTileThreads) k_batch_modes(BatchTables t, int
 __global__ void __launch_bounds__(kMeanThreads) k_batch_mean(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ MeanScratch<float, kMeanThreads> ms;
+  __shared__ MeanScratch<float, kMeanThreadsSmall> ms_small;
   const int n = t.counts[0];
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
     const BatchRunDesc& rd = t.runs[r];
     if (step >= rd.remaining) continue;
     const PoissonArgs a = rd.pa;
-    mean_mode_body<float, kMeanThreads>(a, smem_raw, ms);
+    if (a.Ny <= kMeanSmallRows) {  // the same thread count as the run alone
+      if (threadIdx.x < kMeanThreadsSmall) mean_mode_body<float, kMeanThreadsSmall>(a, smem_raw, ms_small);
+    } else {
+      mean_mode_body<float, kMeanThreads>(a, smem_raw, ms);
+    }
     __syncthreads();
   }
 }
@@ -803,7 +785,11 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
   }
   const cudaStream_t ms = side ? side : s;
   if ((e = mark(3, ms)) != cudaSuccess) return e;
-  k_mean_mode<R><<<1, kMeanThreads, 2 * (size_t)a.Ny * sizeof(typename MeanNum<R>::T), ms>>>(a);
+  const size_t msm = 2 * (size_t)a.Ny * sizeof(typename MeanNum<R>::T);
+  if (a.Ny <= kMeanSmallRows)
+    k_mean_mode<R, kMeanThreadsSmall><<<1, kMeanThreadsSmall, msm, ms>>>(a);
+  else
+    k_mean_mode<R, kMeanThreads><<<1, kMeanThreads, msm, ms>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(4, ms)) != cudaSuccess) return e;
   if (side && (e = cudaEventRecord(join, side)) != cudaSuccess) return e;
@@ -839,7 +825,8 @@ cudaError_t set_attrs_t() {
   cudaError_t e;
   if ((e = allow_max_dynamic_smem(k_rfft_rows<R>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_irfft_rows<R>)) != cudaSuccess) return e;
-  if ((e = allow_max_dynamic_smem(k_mean_mode<R>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreads>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreadsSmall>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2>)) != cudaSuccess) return e;
