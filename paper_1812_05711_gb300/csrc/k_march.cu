@@ -815,8 +815,10 @@ __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
 }
 
 // Batch: every warp of a fixed grid takes march items (run, strip, slab) in
-// turn; runs whose budget in the tick is used up are skipped.
-__global__ void __launch_bounds__(128) k_batch_march(BatchTables t, int step) {
+// turn; runs whose budget in the tick is used up are skipped.  Bounded to
+// three CTAs per SM (168 registers, a few bytes spilled): at 180 registers
+// only two fit and the batch step takes 320 instead of 280 us.
+__global__ void __launch_bounds__(128, 3) k_batch_march(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char march_smem[];
   constexpr int NST = 2;
   unsigned char* ring = march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<float, float, NST>::kBytesPerWarp;
