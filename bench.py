@@ -574,8 +574,11 @@ def run_bifurcation(args):
 
     torch.cuda.set_device(0)
     Ts = [100.0 + 5.0 * k for k in range(17)] + [190.0, 200.0, 220.0]
+    Nx = args.grid
+    Ny = wl.ny_for(Nx)
+    steps = 200000 * Nx // 64  # the same number of ion transits on every grid
     t0 = _t.perf_counter()
-    r = studies.nusselt_sweep(Ts, Nx=64, Ny=52, u_ion=5e-3, steps=200000, window=40000)
+    r = studies.nusselt_sweep(Ts, Nx=Nx, Ny=Ny, u_ion=5e-3, steps=steps, window=steps // 5)
     el = _t.perf_counter() - t0
 
     def crossing(branch, level, rising):
@@ -587,10 +590,10 @@ def run_bifurcation(args):
 
     Tc = crossing(r["lower"], 1.01, True)
     Tf = crossing(r["upper"], 1.01, False)
-    line = {"metric": "Ne(T) thresholds", "value": Tc, "unit": "T", "n_gpus": 1, "steps": 200000, "warmup": 0,
+    line = {"metric": "Ne(T) thresholds", "value": Tc, "unit": "T", "n_gpus": 1, "steps": steps, "warmup": 0,
             "ms_per_step": None, "higher_is_better": None, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "bifurcation-64x52", "u_ion": 5e-3, "seconds": el},
+            "config": {"workload": f"bifurcation-{Nx}x{Ny}", "u_ion": 5e-3, "steps_per_T": steps, "seconds": el},
             "T_c_onset": Tc, "T_f": Tf, "paper": {"T_c": 163.4, "T_f": 108.7},
             "lower": r["lower"], "upper": r["upper"], "I_h": r["I_h"],
             "roofline": None, "e2e": None, "cpu_baseline": None}
@@ -617,6 +620,7 @@ def main():
     ap.add_argument("--fp64-requests", type=int, default=4, help="prefix served by the plain FP64 path")
     ap.add_argument("--hbm-gb", type=float, default=200.0, help="HBM budget of the server")
     ap.add_argument("--oracle-steps", type=int, default=50, help="precision: steps compared with the oracle")
+    ap.add_argument("--grid", type=int, default=64, help="bifurcation: Nx of the channel (Ny = 0.82 Nx)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -394,14 +394,26 @@ ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
   if (!bytes) return fail(EHD_EINVAL, "bytes is NULL");
   if (Nx < 16 || Nx > 4096 || (Nx & (Nx - 1)) || Ny < 2 || Ny > 8192 || storage < 0 || storage > 3)
     return fail(EHD_EINVAL, "unsupported size or storage");
-  const size_t P = (size_t)((Nx + 31) / 32 * 32), Mh = (size_t)Nx / 2 + 1;
+  const size_t P = (size_t)((Nx + 31) / 32 * 32), Mp = ((size_t)Nx / 2 + 1 + 3) / 4 * 4;
   const size_t rs = (storage == 0) ? 8 : 4;  // worst case for the compute type
-  size_t b = 4 * 9 * (size_t)Ny * P * storage_bytes(storage);  // f, g ping-pong
-  b += 2 * (size_t)Ny * P * rs;                                // dphi, rho_c
-  b += (size_t)Ny * (Mh + 3) * 3 * rs;                         // spectrum, pivots (pitch Mp)
-  b += (size_t)Ny * (8 + 8 + 8 + rs + 4) + (size_t)(Nx + 1024) * 2 * rs;  // per-row, twiddles
-  b += 2 * (size_t)(Ny / 4 + 2) * P * rs;                      // slab-boundary charge partials
-  b += 64 * 1024;                                              // small buffers
+  const size_t ny = (size_t)Ny, plane = ny * P;
+  // the buffers ehd_create allocates, each rounded as a caching allocator
+  // carves it (2 MiB above 1 MiB, 512 B below), so that the sum bounds what
+  // a run holds whichever allocator serves it
+  const size_t bufs[] = {
+      9 * plane * storage_bytes(storage), 9 * plane * storage_bytes(storage),  // f ping-pong
+      9 * plane * storage_bytes(storage), 9 * plane * storage_bytes(storage),  // g ping-pong
+      plane * rs, plane * rs,                                                  // dphi, rho_c
+      ny * 8, ny * rs, ny * Mp * 2 * rs, ny * 8, Mp * ny * rs, ny * 8,         // phibar .. rfac0
+      (size_t)(Nx + 1024) * 2 * rs, ny * 4,                                    // twiddles, shifts
+      (ny / 4 + 2) * P * rs, (ny / 4 + 2) * P * rs,                            // slab-boundary shares
+      2 * (size_t)std::max(march_strips(Nx, 1), step_flux_blocks(Nx)) * 8,    // flux partials
+      16 * 8 + 64, (size_t)reduce_state_blocks() * 6 * 8};
+  size_t b = 0;
+  for (size_t v : bufs) {
+    const size_t g = (v > (1u << 20)) ? (2u << 20) : 512;
+    b += (v + g - 1) / g * g;
+  }
   *bytes = b;
   return EHD_OK;
 }
