@@ -52,10 +52,21 @@ template <> struct Store<__nv_bfloat16> {
     return (R)__bfloat162float(__float2bfloat16_rn((float)v));
   }
 };
+// FP16 keeps the shifted populations scaled by 2^12: they are small (of the
+// order of the flow's departure from the hydrostatic state, 1e-7 .. 1e-2)
+// and would otherwise fall below FP16's normal range (6.1e-5); the scaled
+// values stay far below its largest finite value.  Powers of two scale exactly.
+constexpr float kHalfScale = 4096.0f, kHalfUnscale = 1.0f / 4096.0f;
 template <> struct Store<__half> {
-  template <class R> __device__ __forceinline__ static R ld(const __half* p) { return (R)__half2float(__ldg(p)); }
-  template <class R> __device__ __forceinline__ static void st(__half* p, R v) { *p = __float2half_rn((float)v); }
-  template <class R> __device__ __forceinline__ static R rt(R v) { return (R)__half2float(__float2half_rn((float)v)); }
+  template <class R> __device__ __forceinline__ static R ld(const __half* p) {
+    return (R)(__half2float(__ldg(p)) * kHalfUnscale);
+  }
+  template <class R> __device__ __forceinline__ static void st(__half* p, R v) {
+    *p = __float2half_rn((float)v * kHalfScale);
+  }
+  template <class R> __device__ __forceinline__ static R rt(R v) {
+    return (R)(__half2float(__float2half_rn((float)v * kHalfScale)) * kHalfUnscale);
+  }
 };
 
 template <class R> struct Cplx { R re, im; };

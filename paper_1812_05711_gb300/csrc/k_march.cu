@@ -417,14 +417,16 @@ struct Pair<__nv_bfloat16> {
   }
 };
 template <>
-struct Pair<__half> {
+struct Pair<__half> {  // scaled by 2^12 like Store<__half>
   template <class R>
-  __device__ static void st(__half* p, R a, R b) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn((float)a, (float)b); }
+  __device__ static void st(__half* p, R a, R b) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn((float)a * kHalfScale, (float)b * kHalfScale);
+  }
   template <class R>
   __device__ static void ld(const __half* p, R& a, R& b) {
     const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
-    a = (R)v.x;
-    b = (R)v.y;
+    a = (R)(v.x * kHalfUnscale);
+    b = (R)(v.y * kHalfUnscale);
   }
 };
 
