@@ -47,7 +47,7 @@ typedef enum {
 /* Storage type of the populations.  F64 storage with F64 compute is the plain
  * double-precision path of the paper (Sec. IV.4); every other combination
  * computes in FP32 on populations stored shifted by their rest equilibrium
- * (f_i - w_i and g_i - w_i rho_c,hydrostatic(y)). */
+ * (f_i - w_i rho_hydrostatic(y) and g_i - w_i rho_c,hydrostatic(y)). */
 typedef enum {
   EHD_STORE_F64 = 0,
   EHD_STORE_F32 = 1,
@@ -155,7 +155,14 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * small grids; 0, the default: plain stream order, since early-resident CTAs
  * unbalance the one-wave grids of large runs), EHD_TUNE_FFT_CTA (FP32 rows
  * of 2048: 1, the default, one CTA of 64 threads per row; 0, one warp per
- * row).
+ * row), EHD_TUNE_Y_SOLVER (the y solve of the wavenumbers m >= 1: 0, the
+ * default, one tridiagonal per wavenumber (Eq. 18); 1, the literal form of
+ * Sec. IV.3: odd extension of each spectrum column in y to NE = 2 Ny points
+ * (walls halfway, the default) or 2 Ny + 2 (walls on nodes) (Eqs. 21-22), a
+ * complex FFT of length NE, division by -(kappa_m + 4 sin^2(pi k / NE))
+ * (Eqs. 20, 24), inverse FFT, first Ny points (Eq. 25); NE must have no
+ * prime factor above 13 and one column must fit in shared memory, and
+ * runs in a batch keep 0; the mean mode m = 0 is solved as before).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -165,6 +172,7 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_TILE_MODES 5
 #define EHD_TUNE_PDL 6
 #define EHD_TUNE_FFT_CTA 7
+#define EHD_TUNE_Y_SOLVER 8
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

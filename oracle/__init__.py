@@ -14,6 +14,7 @@ through ctypes.  Functions and the passages they follow:
 * :func:`dft` / :func:`fft` -- Eq. 19
 * :func:`thomas`           -- tridiagonal solve used per wavenumber (Eq. 18)
 * :func:`poisson`          -- Sec. IV.3 (Eqs. 18-25)
+* :func:`poisson_oddext`   -- Sec. IV.3 literally (Eqs. 19-25, odd extension)
 * :func:`init_state`       -- Eqs. 27-29
 * :func:`step`             -- Eqs. 5-17 and Table I
 * :func:`fields`           -- Eqs. 5-7 and E = -grad phi
@@ -95,6 +96,8 @@ def lib():
         L.orc_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
         L.orc_poisson_general.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_poisson_oddext.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_poisson.argtypes = [pp, dp, dp]
         L.orc_efield.argtypes = [pp, dp, dp, dp]
         L.orc_perturbation.argtypes = [pp, ctypes.c_int, dp, dp, ctypes.c_double,
@@ -175,6 +178,17 @@ def poisson_general(src: np.ndarray, wall_mode=0, phi_bottom=0.0, phi_top=0.0, x
     Ny, Nx = src.shape
     phi = np.empty_like(src)
     lib().orc_poisson_general(Nx, Ny, wall_mode, x_symbol, phi_bottom, phi_top, _dp(src), _dp(phi))
+    return phi
+
+
+def poisson_oddext(src: np.ndarray, wall_mode=0, phi_bottom=0.0, phi_top=0.0, x_symbol=0):
+    """The same solve as :func:`poisson_general` in the literal form of
+    Sec. IV.3: odd extension in y (Eqs. 21-22), 2-D transform, division by
+    the symbol (Eqs. 20, 24), inverse, first half (Eq. 25)."""
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    Ny, Nx = src.shape
+    phi = np.empty_like(src)
+    lib().orc_poisson_oddext(Nx, Ny, wall_mode, x_symbol, phi_bottom, phi_top, _dp(src), _dp(phi))
     return phi
 
 

@@ -308,6 +308,97 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
   free(dim);
 }
 
+/* Sec. IV.3 as the paper prints it, without the tridiagonal: the source is
+ * extended oddly in y (Eqs. 21-22) to NE rows -- NE = 2 Ny antisymmetric about
+ * the half node below row 0 and above row Ny - 1 (walls halfway between
+ * nodes, the default reading), or NE = 2 Ny + 2 with zero rows on the wall
+ * nodes j = -1 and j = Ny (wall_mode 1, Eq. 21 as printed) -- transformed
+ * along x (Eq. 19) and along y, divided by the symbol of the discrete
+ * Laplacian, -(kappa_m + 4 sin^2(pi k / NE)) (Eqs. 20, 24), transformed back
+ * and cut to the first Ny rows (Eq. 25).  The odd extension has no mean, so
+ * the (m, k) = (0, 0) coefficient is zero.  Non-zero wall potentials enter
+ * as the linear profile between the walls (it has zero discrete Laplacian and
+ * takes the wall values), added to the homogeneous solution. */
+void orc_poisson_oddext(int Nx, int Ny, int wall_mode, int x_symbol,
+                        double phi_bottom, double phi_top, const double* src,
+                        double* phi) {
+  const int NE = (wall_mode == 0) ? 2 * Ny : 2 * Ny + 2;
+  const int off = (wall_mode == 0) ? 0 : 1; /* extended row of source row 0 */
+  const int nmax = (NE > Nx) ? NE : Nx;
+  size_t ne = (size_t)NE * Nx;
+  double* er = (double*)calloc(ne, sizeof(double)); /* [NE][Nx] */
+  double* ei = (double*)calloc(ne, sizeof(double));
+  double* rre = (double*)malloc(sizeof(double) * nmax);
+  double* rim = (double*)malloc(sizeof(double) * nmax);
+  double* tre = (double*)malloc(sizeof(double) * nmax);
+  double* tim = (double*)malloc(sizeof(double) * nmax);
+  /* odd extension: row off + j holds s_j, row NE - 1 - j holds -s_j */
+  for (int j = 0; j < Ny; ++j)
+    for (int x = 0; x < Nx; ++x) {
+      er[(size_t)(off + j) * Nx + x] = src[(size_t)j * Nx + x];
+      er[(size_t)(NE - 1 - j) * Nx + x] = -src[(size_t)j * Nx + x];
+    }
+  for (int pass = 0; pass < 2; ++pass) {
+    const int sign = (pass == 0) ? -1 : +1;
+    /* along x, every extended row */
+    for (int k = 0; k < NE; ++k) {
+      memcpy(rre, er + (size_t)k * Nx, sizeof(double) * Nx);
+      memcpy(rim, ei + (size_t)k * Nx, sizeof(double) * Nx);
+      transform_row(Nx, rre, rim, tre, tim, sign);
+      memcpy(er + (size_t)k * Nx, rre, sizeof(double) * Nx);
+      memcpy(ei + (size_t)k * Nx, rim, sizeof(double) * Nx);
+    }
+    /* along y, every column */
+    for (int m = 0; m < Nx; ++m) {
+      for (int k = 0; k < NE; ++k) {
+        rre[k] = er[(size_t)k * Nx + m];
+        rim[k] = ei[(size_t)k * Nx + m];
+      }
+      transform_row(NE, rre, rim, tre, tim, sign);
+      for (int k = 0; k < NE; ++k) {
+        er[(size_t)k * Nx + m] = rre[k];
+        ei[(size_t)k * Nx + m] = rim[k];
+      }
+    }
+    if (pass == 1) break;
+    /* divide by the symbol */
+    for (int k = 0; k < NE; ++k) {
+      const int ks = (k <= NE / 2) ? k : k - NE;
+      const double sy = sin(OPI * (double)ks / (double)NE);
+      for (int m = 0; m < Nx; ++m) {
+        const int ms = (m <= Nx / 2) ? m : m - Nx;
+        const double kx = 2.0 * OPI * (double)ms / (double)Nx;
+        double kappa = kx * kx;
+        if (x_symbol == 1) {
+          const double sx = sin(OPI * (double)ms / (double)Nx);
+          kappa = 4.0 * sx * sx;
+        }
+        const double den = -(kappa + 4.0 * sy * sy);
+        const size_t q = (size_t)k * Nx + m;
+        if (k == 0 && m == 0) {
+          er[q] = 0.0;
+          ei[q] = 0.0;
+        } else {
+          er[q] /= den;
+          ei[q] /= den;
+        }
+      }
+    }
+  }
+  const double scale = 1.0 / ((double)NE * (double)Nx);
+  for (int j = 0; j < Ny; ++j) {
+    const double t = (wall_mode == 0) ? (j + 0.5) / (double)Ny : (j + 1.0) / (double)(Ny + 1);
+    const double lift = phi_bottom + (phi_top - phi_bottom) * t;
+    for (int x = 0; x < Nx; ++x) phi[(size_t)j * Nx + x] = er[(size_t)(off + j) * Nx + x] * scale + lift;
+  }
+  free(er);
+  free(ei);
+  free(rre);
+  free(rim);
+  free(tre);
+  free(tim);
+}
+
 void orc_poisson(const orc_params* p, const double* rhoc, double* phi) {
   size_t nc = (size_t)p->Nx * p->Ny;
   double* s = (double*)malloc(sizeof(double) * nc);

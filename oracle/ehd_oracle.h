@@ -44,6 +44,9 @@ void orc_thomas(int n, const double* a, const double* b, const double* c,
 void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
                          double phi_bottom, double phi_top, const double* src,
                          double* phi);
+void orc_poisson_oddext(int Nx, int Ny, int wall_mode, int x_symbol,
+                        double phi_bottom, double phi_top, const double* src,
+                        double* phi);
 void orc_poisson(const orc_params* p, const double* rhoc, double* phi);
 void orc_efield(const orc_params* p, const double* phi, double* Ex,
                 double* Ey);

@@ -63,7 +63,7 @@ struct ehd_run {
   // lattice parameters
   double T = 0, C = 0, M = 0, Fe = 0, Lambda = 0, Lambda_g = 0, u_ion = 0;
   double H = 0, mub = 0, eps = 0, nu = 0, rho0 = 0, Dc = 0, phi0 = 1.0;
-  double tau_p = 0, tau_m = 0, taug_p = 0, taug_m = 0, rho_a = 0, y_a = 0, sf = 0;
+  double tau_p = 0, tau_m = 0, taug_p = 0, taug_m = 0, rho_a = 0, y_a = 0;
   // device state
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -85,7 +85,8 @@ struct ehd_run {
   void* tw = nullptr;
   void* rx_dn = nullptr;  // slab-boundary charge partials of the march form, [Ny/4 + 2][P] each
   void* rx_up = nullptr;
-  float* rch = nullptr;
+  float* rch = nullptr;  // [Ny] hydrostatic charge of each row (FP32), shifted storage only
+  double fb = 0, fd = 0; // f shift fb + fd y: the hydrostatic density ramp, fd rounded to FP32
   double* flux_part = nullptr;
   int nxb = 0;
   double* small = nullptr;  // [0] q_in sum, [1] q_out sum, [2..7] last reduction
@@ -99,6 +100,9 @@ struct ehd_run {
   int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
   int pdl = 0;         // programmatic dependent launch between the Poisson kernels (off: see ehd_tune)
   int fft_cta = 1;     // rows of 2048: CTA-per-row transforms
+  int y_solver = 0;    // y solve of m >= 1: 0 tridiagonal, 1 odd-extension transform
+  int NE = 0, nfac = -1, fac[16] = {};  // odd-extension length and radices (nfac < 0: unsupported)
+  void* oddt = nullptr;  // its tables: complex R [NE] twiddles, R [NE] y symbol, R [Mh] x symbol
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -214,6 +218,9 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.dphi = r->dphi;
   a.Ebar = r->Ebar;
   a.rch = r->rch;
+  a.fb = r->fb;
+  a.fd = r->fd;
+  a.fdq = -r->fd * r->tau_m;
   a.flux_part = r->flux_part;
   a.err = r->err;
   a.wp = 1.0 / r->tau_p;
@@ -222,7 +229,6 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.gwm = 1.0 / r->taug_m;
   a.mub = r->mub;
   a.rho0 = r->rho0;
-  a.sf = r->sf;
   a.wall_mode = r->wall_mode;
   a.rhoc_out = r->rhoc;
   a.rhoc_dn = r->rx_dn;
@@ -266,6 +272,15 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.tile_modes = r->tile_modes;
   a.pdl = r->pdl;
   a.fft_cta = r->fft_cta;
+  a.y_solver = r->y_solver;
+  a.NE = r->NE;
+  a.nfac = r->nfac;
+  for (int k = 0; k < 16; ++k) a.fac[k] = r->fac[k];
+  if (r->oddt) {
+    a.twy = r->oddt;
+    a.symy = static_cast<const char*>(r->oddt) + 2 * (size_t)r->NE * r->rsz;
+    a.kap = static_cast<const char*>(r->oddt) + 3 * (size_t)r->NE * r->rsz;
+  }
   return a;
 }
 
@@ -289,7 +304,8 @@ FieldArgs field_args(const ehd_run* r) {
   a.phibar = r->phibar;
   a.Ebar = r->Ebar;
   a.rch = r->rch;
-  a.sf = r->sf;
+  a.fb = r->fb;
+  a.fd = r->fd;
   a.mub = r->mub;
   a.wall_mode = r->wall_mode;
   return a;
@@ -408,7 +424,8 @@ ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
       (size_t)(Nx + 1024) * 2 * rs, ny * 4,                                    // twiddles, shifts
       (ny / 4 + 2) * P * rs, (ny / 4 + 2) * P * rs,                            // slab-boundary shares
       2 * (size_t)std::max(march_strips(Nx, 1), step_flux_blocks(Nx)) * 8,    // flux partials
-      16 * 8 + 64, (size_t)reduce_state_blocks() * 6 * 8};
+      16 * 8 + 64, (size_t)reduce_state_blocks() * 6 * 8,
+      (3 * (2 * ny + 2) + (size_t)Nx / 2 + 1) * rs};                         // odd-extension tables
   size_t b = 0;
   for (size_t v : bufs) {
     const size_t g = (v > (1u << 20)) ? (2u << 20) : 512;
@@ -485,7 +502,6 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_EINVAL, "hydrostatic profile has no solution");
   }
   const bool shifted = !r->real_f64;
-  r->sf = shifted ? 1.0 : 0.0;
 
   DeviceGuard dg(r->device);
   ehd_status st = EHD_OK;
@@ -507,6 +523,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   {
     cudaError_t e = poisson_set_attributes();
     if (e == cudaSuccess) e = march_set_attributes();
+    if (e == cudaSuccess) e = oddext_set_attributes();
     if (e != cudaSuccess) {
       destroy_quiet(r);
       return fail(EHD_ECUDA, "setting the shared-memory limit of the Poisson kernels: %s", cudaGetErrorString(e));
@@ -531,6 +548,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   // first-pass twiddles of the CTA transform, [k1 < 16][t < 64]
   r->tw = run_alloc(r, (size_t)(Nx + (Nx == 2048 && !r->real_f64 ? 1024 : 0)) * 2 * r->rsz);
   if (shifted) r->rch = static_cast<float*>(run_alloc(r, Ny * sizeof(float)));
+  r->NE = (r->wall_mode == 0) ? 2 * Ny : 2 * Ny + 2;
+  r->nfac = oddext_factors(r->NE, r->fac, 16);
+  if (r->nfac > 0) r->oddt = run_alloc(r, (3 * (size_t)r->NE + r->Mh) * r->rsz);
   r->rx_dn = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->rx_up = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->step_kernel = o.step_kernel;
@@ -543,7 +563,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->red_part = static_cast<double*>(run_alloc(r, (size_t)reduce_state_blocks() * 6 * sizeof(double)));
   bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->rx_dn && r->rx_up && r->phibar &&
             r->Ebar && r->spec && r->spec0 &&
-            r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part;
+            r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part &&
+            (r->nfac <= 0 || r->oddt);
   if (!ok) {
     destroy_quiet(r);
     return fail(EHD_ENOMEM, "device allocation failed");
@@ -606,6 +627,27 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
       st = upload(r, r->tw, twf.data(), twf.size() * 4);
       if (st == EHD_OK) st = upload(r, r->rfac, pivf.data(), pivf.size() * 4);
     }
+    if (st == EHD_OK && r->oddt) {
+      // odd-extension tables: exp(-2 pi i t / NE), 4 sin^2(pi k / NE), kappa_m
+      const int NE = r->NE;
+      std::vector<double> tab(3 * (size_t)NE + r->Mh);
+      for (int t = 0; t < NE; ++t) {
+        const double ang = 2.0 * kPi * (double)t / (double)NE, sy = std::sin(kPi * (double)t / (double)NE);
+        tab[2 * t] = std::cos(ang);
+        tab[2 * t + 1] = -std::sin(ang);
+        tab[2 * (size_t)NE + t] = 4.0 * sy * sy;
+      }
+      for (int m = 0; m < r->Mh; ++m) {
+        const double kx = 2.0 * kPi * (double)m / (double)Nx, sx = std::sin(kPi * (double)m / (double)Nx);
+        tab[3 * (size_t)NE + m] = (o.x_symbol == 1) ? 4.0 * sx * sx : kx * kx;
+      }
+      if (r->real_f64) {
+        st = upload(r, r->oddt, tab.data(), tab.size() * 8);
+      } else {
+        std::vector<float> tf(tab.begin(), tab.end());
+        st = upload(r, r->oddt, tf.data(), tf.size() * 4);
+      }
+    }
     if (st == EHD_OK) {
       if (r->real_f64) {
         st = upload(r, r->rfac0, piv0.data(), Ny * sizeof(double));
@@ -628,6 +670,12 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     std::vector<double> rho_h(Ny), rc_h(Ny), Eh(Ny), sY(Ny), cY(Ny), Sx(nx, 0.0), Cy(nx, 0.0);
     std::vector<float> rchf(Ny);
     const double Fh = 2.0 * r->rho_a * r->rho_a / r->eps;  // rho_c E of Eqs. 27-28, constant
+    if (shifted) {
+      // f shift: the hydrostatic density 1 + 3 Fh (y - H/2) of row y, its
+      // slope rounded to FP32 so that the kernels add the row change exactly
+      r->fd = (double)(float)(3.0 * Fh);
+      r->fb = 1.0 + r->fd * (0.5 - 0.5 * r->H);
+    }
     for (int j = 0; j < Ny; ++j) {
       const double y = j + 0.5, s = std::sqrt(y + r->y_a);
       rc_h[j] = r->rho_a / s;                       // Eq. 27
@@ -667,7 +715,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
       cudaError_t e = cudaMemsetAsync(r->small, 0, 16 * sizeof(double) + 64, r->stream);
       if (e == cudaSuccess)
         e = launch_init(p, p + Ny, p + 2 * Ny, p + 3 * Ny, p + 4 * Ny, p + 5 * Ny, p + 5 * Ny + nx, Fh, r->mub,
-                        r->f[0], r->g[0], r->storage, Nx, Ny, r->P, r->rch, r->sf, r->stream);
+                        r->f[0], r->g[0], r->storage, Nx, Ny, r->P, r->rch, r->fb, r->fd, r->stream);
       if (e == cudaSuccess) e = enqueue_poisson(r, 0, false);
       if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
       if (e != cudaSuccess) st = fail(EHD_ECUDA, "initialisation: %s", cudaGetErrorString(e));
@@ -707,6 +755,20 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "CTA-per-row transforms must be 0 or 1");
       r->fft_cta = value;
       break;
+    case EHD_TUNE_Y_SOLVER: {
+      if (value != 0 && value != 1) return fail(EHD_EINVAL, "y solver must be 0 (tridiagonal) or 1 (odd extension)");
+      if (value == 1) {
+        if (r->batch) return fail(EHD_EINVAL, "runs in a batch use the tridiagonal y solve");
+        if (r->nfac <= 0)
+          return fail(EHD_EINVAL, "odd-extension length %d has a prime factor above 13", r->NE);
+        int optin = 0;
+        EHD_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, r->device));
+        if (oddext_smem_bytes(r->NE, r->real_f64) > (size_t)optin)
+          return fail(EHD_EINVAL, "odd-extension column of %d points exceeds shared memory", r->NE);
+      }
+      r->y_solver = value;
+      break;
+    }
     case EHD_TUNE_COLS_PER_LANE:
       if (value != 1 && value != 2) return fail(EHD_EINVAL, "columns per lane must be 1 or 2");
       if (value == 2 && r->ring_depth == 6) r->ring_depth = 3;
@@ -741,6 +803,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_TILE_MODES: return r->tile_modes;
     case EHD_TUNE_PDL: return r->pdl;
     case EHD_TUNE_FFT_CTA: return r->fft_cta;
+    case EHD_TUNE_Y_SOLVER: return r->y_solver;
   }
   return -1;
 }
@@ -879,13 +942,13 @@ ehd_status ehd_load(ehd_run* r, const double* f_host, const double* g_host) {
     e = cudaMemcpyAsync(stage, f_host + i * n, n * sizeof(double), cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess)
       e = launch_load_plane(stage, static_cast<char*>(r->f[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
-                            r->P, 0.0, nullptr, r->sf * w[i], r->stream);
+                            r->P, w[i], nullptr, r->fb, r->fd, r->stream);
   }
   for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
     e = cudaMemcpyAsync(stage, g_host + i * n, n * sizeof(double), cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess)
       e = launch_load_plane(stage, static_cast<char*>(r->g[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
-                            r->P, w[i], r->rch, 0.0, r->stream);
+                            r->P, w[i], r->rch, 0.0, 0.0, r->stream);
   }
   if (e == cudaSuccess) e = enqueue_poisson(r, r->cur, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
@@ -910,8 +973,8 @@ ehd_status ehd_save(ehd_run* r, double* f_host, double* g_host) {
     const void* base = set == 0 ? r->f[r->cur] : r->g[r->cur];
     for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
       e = launch_save_plane(static_cast<const char*>(base) + i * plane * sb, stage, r->storage, r->Nx, r->Ny, r->P,
-                            set == 0 ? 0.0 : w[i], set == 0 ? nullptr : r->rch, set == 0 ? r->sf * w[i] : 0.0,
-                            r->stream);
+                            w[i], set == 0 ? nullptr : r->rch, set == 0 ? r->fb : 0.0,
+                            set == 0 ? r->fd : 0.0, r->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(host + i * n, stage, n * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
     }
@@ -1124,6 +1187,7 @@ ehd_status ehd_batch_add(ehd_batch* b, ehd_run* r, long steps) {
   if (r->batch) return fail(EHD_EINVAL, "run is already in a batch");
   if (r->storage != EHD_STORE_F32 || r->real_f64 || r->step_kernel != 0)
     return fail(EHD_EINVAL, "batches take FP32-storage, FP32-compute runs in the march form");
+  if (r->y_solver != 0) return fail(EHD_EINVAL, "batches take runs with the tridiagonal y solve");
   if (r->Nx < 64 || r->Nx > b->max_nx || r->Ny > b->max_ny) return fail(EHD_EINVAL, "run size exceeds the batch limits");
   if (r->device != b->device) return fail(EHD_EINVAL, "run and batch are on different devices");
   if ((int)b->members.size() >= b->max_runs) return fail(EHD_EBUSY, "batch is full");

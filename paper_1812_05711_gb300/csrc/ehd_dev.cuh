@@ -110,7 +110,8 @@ struct StepArgs {
   double* flux_part;         // [2][nxb] per-CTA injected / collected charge
   int* err;                  // bit 0: non-finite density or charge
   double wp, wm, gwp, gwm;   // omega+, omega-, omega_g+, omega_g-
-  double mub, rho0, sf;      // ion mobility, injected density, f shift (1 or 0)
+  double mub, rho0;          // ion mobility, injected density
+  double fb, fd, fdq;        // f shift r(y) = fb + fd y (fd an FP32 value), and -fd / omega- (0 when unshifted)
   int wall_mode;
   // march form only
   void* rhoc_out;            // R [Ny][P]: rho_c of the new state (slab-boundary rows: partial, see rhoc_dn)
@@ -147,6 +148,14 @@ struct PoissonArgs {
   int tile_modes;            // wavenumbers per CTA of the mode solve (8, 4, 2, 1; 0 = largest that fits)
   int pdl;                   // launch the main-stream kernels with programmatic dependent launch
   int fft_cta;               // rows of 2048: one CTA of 64 threads per row (else one warp per row)
+  // y solve of the wavenumbers m >= 1: 0 per-wavenumber tridiagonal (k_modes_tile),
+  // 1 odd-extension transform of length NE (k_modes_oddext, Eqs. 21-25)
+  int y_solver;
+  int NE, nfac;              // odd-extension length, number of its radices
+  int fac[16];               // radices of NE in stage order
+  const void* twy;           // complex R [NE]: exp(-2 pi i t / NE)
+  const void* symy;          // R [NE]: 4 sin^2(pi k / NE)
+  const void* kap;           // R [Mh]: kappa_m, the x symbol of wavenumber m
 };
 
 // Charge density of row y as the Poisson solve sees it: the step kernel's
@@ -174,7 +183,8 @@ struct FieldArgs {
   const void* phibar;        // double, or float (hi, lo) pairs when R = float
   const void* Ebar;
   const float* rch;
-  double sf, mub;
+  double fb, fd;             // f shift r(y) = fb + fd y
+  double mub;
   int wall_mode;
 };
 
@@ -232,6 +242,13 @@ cudaError_t march_set_attributes();
 // between the fork and join events when side != nullptr.
 cudaError_t launch_poisson(const PoissonArgs& a, bool real_f64, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
                            cudaEvent_t join, const cudaEvent_t* marks = nullptr);
+// Odd-extension y solve (k_oddext.cu): radices of n (4, 2, 3, 5, 7, 11, 13;
+// at most cap of them) into fac, their count, or -1 if n has another factor;
+// the shared memory one CTA needs; the launch over m = 1 .. Mh - 1.
+int oddext_factors(int n, int* fac, int cap);
+size_t oddext_smem_bytes(int NE, bool real_f64);
+cudaError_t launch_modes_oddext(const PoissonArgs& a, bool real_f64, cudaStream_t s);
+cudaError_t oddext_set_attributes();
 // rho_c = sum_i g_i (+ the row shift) into the charge plane.
 cudaError_t launch_rhoc(const void* g, long long plane, int storage, bool real_f64, int Nx, int Ny, int P,
                         const float* rch, void* rhoc, cudaStream_t s);
@@ -247,12 +264,12 @@ cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, 
                                 double* out, int* err, cudaStream_t s);
 int reduce_state_blocks();
 cudaError_t launch_load_plane(const double* src, void* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double sconst, cudaStream_t s);
+                              const float* rch, double c0, double c1, cudaStream_t s);
 cudaError_t launch_save_plane(const void* src, double* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double sconst, cudaStream_t s);
+                              const float* rch, double c0, double c1, cudaStream_t s);
 cudaError_t launch_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY,
                         const double* cY, const double* Sx, const double* Cy, double Fh, double mub,
-                        void* f, void* g, int storage, int Nx, int Ny, int P, const float* rch, double sf,
-                        cudaStream_t s);
+                        void* f, void* g, int storage, int Nx, int Ny, int P, const float* rch, double fb,
+                        double fd, cudaStream_t s);
 
 }  // namespace ehd

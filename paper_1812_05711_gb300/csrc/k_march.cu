@@ -38,6 +38,24 @@ __device__ __forceinline__ void trt_f2(R& fi, R& fo, R w, R drho, R rho, R cu, R
   fo = fo + A - B;
 }
 
+// trt_f2 for a pair that crosses rows (fi moves up, fo down) in storage
+// shifted by a density ramp r(y) = r(0) + dr y: with dq = -dr / omega- the
+// antisymmetric part hands fi its storage offset change -w dr and fo +w dr,
+// at no extra instruction (dq is added inside the product w (3 rho cu + dq)).
+template <class R>
+__device__ __forceinline__ void trt_f2y(R& fi, R& fo, R w, R drho, R rho, R cu, R usq15, R cF, R uF3, R wp, R wm,
+                                        R cp, R cm, R dq) {
+  const R ep = w * (drho + rho * (R(4.5) * cu * cu - usq15));
+  const R em = w * (rho * R(3) * cu + dq);
+  const R Fp = w * (R(9) * cu * cF - uF3);
+  const R Fm = w * R(3) * cF;
+  const R sp = R(0.5) * (fi + fo), sm = R(0.5) * (fi - fo);
+  const R A = cp * Fp - wp * (sp - ep);
+  const R B = cm * Fm - wm * (sm - em);
+  fi = fi + A + B;
+  fo = fo + A - B;
+}
+
 template <class R>
 __device__ __forceinline__ void trt_g2(R& gi, R& go, R w, R drc, R rc, R cv, R vsq15, R wp, R wm) {
   const R ep = w * (drc + rc * (R(4.5) * cv * cv - vsq15));
@@ -109,9 +127,10 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
   const float* __restrict__ rch = a.rch;
   const R wp = (R)a.wp, wm = (R)a.wm, gwp = (R)a.gwp, gwm = (R)a.gwm;
   const R cp = R(1) - R(0.5) * wp, cm = R(1) - R(0.5) * wm;
-  const R mub = (R)a.mub, rho0 = (R)a.rho0, sf = (R)a.sf;
+  const R mub = (R)a.mub, rho0 = (R)a.rho0;
   const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
   const R W0 = (R)kW0, W1 = (R)kW1, W2 = (R)kW2;
+  const R fb = (R)a.fb, fd = (R)a.fd;  // f shift fb + fd y: a row up changes it by fd
 
   const int rs = max(y0 - 1, 0), re = min(y1, Ny - 1);
   // carried registers: H (c_y = 0) of row r-1, U (c_y = +1) of rows r-1 and r
@@ -218,7 +237,7 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
     R f0 = F[0], f1 = F[1], f2 = F[2], f3 = F[3], f4 = F[4], f5 = F[5], f6 = F[6], f7 = F[7], f8 = F[8];
     R g0 = G[0], g1 = G[1], g2 = G[2], g3 = G[3], g4 = G[4], g5 = G[5], g6 = G[6], g7 = G[7], g8 = G[8];
     const R drho = ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
-    const R rho = sf + drho;
+    const R rho = (fb + fd * (R)r) + drho;
     const R jx = (f1 - f3) + (f5 - f7) + (f8 - f6);
     const R jy = (f2 - f4) + (f5 - f7) + (f6 - f8);
     const R drc = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + (g6 + g7)) + g8;
@@ -249,13 +268,13 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
     const R P1g = from_left(g1), P5g = from_left(g5), P8g = from_left(g8);
     const R P3g = from_right(g3), P6g = from_right(g6), P7g = from_right(g7);
 
-    // c_y = +1: into row r + 1 (shift of the charge moves with the row)
+    // c_y = +1: into row r + 1 (the shifts of density and charge move with the row)
     R Un[6];
     {
-      const R sh = sy - s_up;
-      Un[0] = f2;
-      Un[1] = P5f;
-      Un[2] = P6f;
+      const R sh = sy - s_up, fh = -fd;
+      Un[0] = f2 + W1 * fh;
+      Un[1] = P5f + W2 * fh;
+      Un[2] = P6f + W2 * fh;
       Un[3] = g2 + W1 * sh;
       Un[4] = P5g + W2 * sh;
       Un[5] = P6g + W2 * sh;
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
     }
     // c_y = -1: into row r - 1, which is then complete
     if (r - 1 >= y0) {
-      const R sh = sy - s_dn;
+      const R sh = sy - s_dn, fh = fd;
       const long long c = row - P + xc;
       if (owned) {
         const R n4 = g4 + W1 * sh, n7 = P7g + W2 * sh, n8 = P8g + W2 * sh;
@@ -290,11 +309,11 @@ __global__ void __launch_bounds__(128) k_march(StepArgs a) {
         Store<S>::st(fo + pl + c, Hm[1]);
         Store<S>::st(fo + 2 * pl + c, Um[0]);
         Store<S>::st(fo + 3 * pl + c, Hm[2]);
-        Store<S>::st(fo + 4 * pl + c, f4);
+        Store<S>::st(fo + 4 * pl + c, f4 + W1 * fh);
         Store<S>::st(fo + 5 * pl + c, Um[1]);
         Store<S>::st(fo + 6 * pl + c, Um[2]);
-        Store<S>::st(fo + 7 * pl + c, P7f);
-        Store<S>::st(fo + 8 * pl + c, P8f);
+        Store<S>::st(fo + 7 * pl + c, P7f + W2 * fh);
+        Store<S>::st(fo + 8 * pl + c, P8f + W2 * fh);
         Store<S>::st(go + c, Hm[3]);
         Store<S>::st(go + pl + c, Hm[4]);
         Store<S>::st(go + 2 * pl + c, Um[3]);
@@ -438,7 +457,7 @@ struct March2Stages {
 };
 
 template <class S, class R>
-__device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R sy, R sf, R mub, R wp, R wm,
+__device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R sy, R sf, R dq, R mub, R wp, R wm,
                                              R cp, R cm, R gwp, R gwm, bool& bad) {
   const R W0 = (R)kW0, W1 = (R)kW1, W2 = (R)kW2;
   const R drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
@@ -457,9 +476,9 @@ __device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R
   const R uF3 = R(3) * (ux * Fx + uy * Fy);
   f[0] = f[0] - wp * (f[0] - W0 * (drho - rho * usq15)) - cp * W0 * uF3;
   trt_f2<R>(f[1], f[3], W1, drho, rho, ux, usq15, Fx, uF3, wp, wm, cp, cm);
-  trt_f2<R>(f[2], f[4], W1, drho, rho, uy, usq15, Fy, uF3, wp, wm, cp, cm);
-  trt_f2<R>(f[5], f[7], W2, drho, rho, ux + uy, usq15, Fx + Fy, uF3, wp, wm, cp, cm);
-  trt_f2<R>(f[6], f[8], W2, drho, rho, uy - ux, usq15, Fy - Fx, uF3, wp, wm, cp, cm);
+  trt_f2y<R>(f[2], f[4], W1, drho, rho, uy, usq15, Fy, uF3, wp, wm, cp, cm, dq);
+  trt_f2y<R>(f[5], f[7], W2, drho, rho, ux + uy, usq15, Fx + Fy, uF3, wp, wm, cp, cm, dq);
+  trt_f2y<R>(f[6], f[8], W2, drho, rho, uy - ux, usq15, Fy - Fx, uF3, wp, wm, cp, cm, dq);
   const R vsq15 = R(1.5) * (vx * vx + vy * vy);
   g[0] = g[0] - gwp * (g[0] - W0 * (drc - rc * vsq15));
   trt_g2<R>(g[1], g[3], W1, drc, rc, vx, vsq15, gwp, gwm);
@@ -493,9 +512,13 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
   const float* __restrict__ rch = a.rch;
   const R wp = (R)a.wp, wm = (R)a.wm, gwp = (R)a.gwp, gwm = (R)a.gwm;
   const R cp = R(1) - R(0.5) * wp, cm = R(1) - R(0.5) * wm;
-  const R mub = (R)a.mub, rho0 = (R)a.rho0, sf = (R)a.sf;
+  const R mub = (R)a.mub, rho0 = (R)a.rho0;
   const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
   const R W1 = (R)kW1, W2 = (R)kW2;
+  // f shift r(y) = fb + fd y (its FP32 rounding enters rho only, the row
+  // change fd is exact); the wall rows undo the row change folded into f
+  const R fb = (R)a.fb, fd = (R)a.fd, fdq = (R)a.fdq;
+  const R wd1 = W1 * fd, wd2 = W2 * fd;
   // the walk covers the slab's own rows; populations that cross a slab
   // boundary are written by the slab that computes them (pushed into the
   // neighbouring slab's first or last row), with their share of that row's
@@ -573,6 +596,7 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
     const R sy = rch ? (R)__shfl_sync(0xffffffffu, ex_f, 2) : R(0);
     const R s_up = (rch && r + 1 < Ny) ? (R)__shfl_sync(0xffffffffu, ex_f, 3) : sy;
     const R s_dn = (rch && r > 0) ? (R)__shfl_sync(0xffffffffu, ex_f, 4) : sy;
+    const R sf = fb + fd * (R)r;
     // E = -grad phi at both nodes of the pair
     const R pWl = from_left(pc[1]);   // phi(xc - 1)
     const R pEr = from_right(pc[0]);  // phi(xc + 2)
@@ -587,8 +611,8 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       g1[i] = G[i][1];
     }
     bool b0, b1;
-    collide_node<S, R>(f0, g0, Ex0, Ey0, sy, sf, mub, wp, wm, cp, cm, gwp, gwm, b0);
-    collide_node<S, R>(f1, g1, Ex1, Ey1, sy, sf, mub, wp, wm, cp, cm, gwp, gwm, b1);
+    collide_node<S, R>(f0, g0, Ex0, Ey0, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b0);
+    collide_node<S, R>(f1, g1, Ex1, Ey1, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b1);
     if (owned && (b0 || b1)) bad = true;
     // pulled values at (xc, xc + 1): x-shift by c_x
     // c_x = +1 (1, 5, 8): [0] from the left lane's second node, [1] own first
@@ -604,7 +628,8 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
     const R f0c[2] = {f0[0], f1[0]}, g0c[2] = {g0[0], g1[0]};
     const R f2c[2] = {f0[2], f1[2]}, g2c[2] = {g0[2], g1[2]};
     const R f4c[2] = {f0[4], f1[4]}, g4c[2] = {g0[4], g1[4]};
-    // own (unshifted) values used by the wall rules
+    // own (unshifted in x) values used by the wall rules; f5..f8 carry the
+    // row change of the shift, which a bounce within the row undoes
     const R f5c[2] = {f0[5], f1[5]}, f6c[2] = {f0[6], f1[6]}, f7c[2] = {f0[7], f1[7]}, f8c[2] = {f0[8], f1[8]};
     const R g5c[2] = {g0[5], g1[5]}, g6c[2] = {g0[6], g1[6]}, g7c[2] = {g0[7], g1[7]}, g8c[2] = {g0[8], g1[8]};
     R Un[6][2];
@@ -631,9 +656,9 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
         const R n2 = -(g4c[j] + R(2) * W1 * sy) + R(2) * W1 * rho0 * (R(1) + R(4.5) * c2 * c2 - w15);
         const R n5 = -(g7c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c5 * c5 - w15);
         const R n6 = -(g8c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c6 * c6 - w15);
-        Uc[0][j] = f4c[j];
-        Uc[1][j] = f7c[j];
-        Uc[2][j] = f8c[j];
+        Uc[0][j] = f4c[j] - wd1;
+        Uc[1][j] = f7c[j] - wd2;
+        Uc[2][j] = f8c[j] - wd2;
         Uc[3][j] = n2;
         Uc[4][j] = n5;
         Uc[5][j] = n6;
@@ -710,9 +735,9 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       Pair<S>::st(fo + c, f0c[0], f0c[1]);
       Pair<S>::st(fo + pl + c, Pf1[0], Pf1[1]);
       Pair<S>::st(fo + 3 * pl + c, Pf3[0], Pf3[1]);
-      Pair<S>::st(fo + 4 * pl + c, f2c[0], f2c[1]);
-      Pair<S>::st(fo + 7 * pl + c, f5c[0], f5c[1]);
-      Pair<S>::st(fo + 8 * pl + c, f6c[0], f6c[1]);
+      Pair<S>::st(fo + 4 * pl + c, f2c[0] + wd1, f2c[1] + wd1);
+      Pair<S>::st(fo + 7 * pl + c, f5c[0] + wd2, f5c[1] + wd2);
+      Pair<S>::st(fo + 8 * pl + c, f6c[0] + wd2, f6c[1] + wd2);
       Pair<S>::st(go + c, g0c[0], g0c[1]);
       Pair<S>::st(go + pl + c, Pg1[0], Pg1[1]);
       Pair<S>::st(go + 3 * pl + c, Pg3[0], Pg3[1]);

@@ -24,9 +24,10 @@ __device__ Macro macro_at(const FieldArgs& a, int x, int y) {
   const S* f = static_cast<const S*>(a.f);
   const S* g = static_cast<const S*>(a.g);
   const double sy = a.rch ? (double)a.rch[y] : 0.0;
+  const double sfy = a.fb + a.fd * y;
   double rho = 0, jx = 0, jy = 0, rc = 0;
   for (int i = 0; i < 9; ++i) {
-    const double fi = (double)Store<S>::template ld<R>(f + i * a.plane + c) + a.sf * wgt(i);
+    const double fi = (double)Store<S>::template ld<R>(f + i * a.plane + c) + wgt(i) * sfy;
     const double gi = (double)Store<S>::template ld<R>(g + i * a.plane + c) + wgt(i) * sy;
     rho += fi;
     jx += cxi(i) * fi;
@@ -117,25 +118,25 @@ __global__ void k_reduce_final(const double* part, int nblk, double* out, int* e
   if (t[5] > 0) atomicOr(err, 1);
 }
 
-// value_stored = value - sconst - shift_w * rch[y]
+// value_stored = value - shift_w (rch[y] + c0 + c1 y)   (rch may be null)
 template <class S>
 __global__ void k_load_plane(const double* src, S* dst, int Nx, int Ny, int P, double shift_w, const float* rch,
-                             double sconst) {
+                             double c0, double c1) {
   const long long n = (long long)Nx * Ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % Nx), y = (int)(k / Nx);
-    const double sh = sconst + (rch ? shift_w * (double)rch[y] : 0.0);
+    const double sh = shift_w * ((rch ? (double)rch[y] : 0.0) + c0 + c1 * y);
     Store<S>::st(dst + (long long)y * P + x, src[k] - sh);
   }
 }
 
 template <class S>
 __global__ void k_save_plane(const S* src, double* dst, int Nx, int Ny, int P, double shift_w, const float* rch,
-                             double sconst) {
+                             double c0, double c1) {
   const long long n = (long long)Nx * Ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % Nx), y = (int)(k / Nx);
-    const double sh = sconst + (rch ? shift_w * (double)rch[y] : 0.0);
+    const double sh = shift_w * ((rch ? (double)rch[y] : 0.0) + c0 + c1 * y);
     dst[k] = Store<S>::template ld<double>(src + (long long)y * P + x) + sh;
   }
 }
@@ -147,7 +148,7 @@ __global__ void k_save_plane(const S* src, double* dst, int Nx, int Ny, int P, d
 template <class S>
 __global__ void k_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY, const double* cY,
                        const double* Sx, const double* Cy, double Fh, double mub, S* f, S* g, int Nx, int Ny, int P,
-                       const float* rch, double sf) {
+                       const float* rch, double fb, double fd) {
   const long long n = (long long)Nx * Ny;
   const long long pl = (long long)Ny * P;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -158,6 +159,7 @@ __global__ void k_init(const double* rho_h, const double* rc_h, const double* Eh
     const double gx = ux, gy = uy + mub * Eh[y];
     const double fu2 = fx * fx + fy * fy, gu2 = gx * gx + gy * gy;
     const double sy = rch ? (double)rch[y] : 0.0;
+    const double sfy = fb + fd * y;
     const long long c = (long long)y * P + x;
     for (int i = 0; i < 9; ++i) {
       const double w = wgt(i);
@@ -165,7 +167,7 @@ __global__ void k_init(const double* rho_h, const double* rc_h, const double* Eh
       const double gc = cxi(i) * gx + cyi(i) * gy;
       const double feq = w * rho * (1.0 + 3.0 * fc + 4.5 * fc * fc - 1.5 * fu2);
       const double geq = w * rc * (1.0 + 3.0 * gc + 4.5 * gc * gc - 1.5 * gu2);
-      Store<S>::st(f + i * pl + c, feq - sf * w);
+      Store<S>::st(f + i * pl + c, feq - w * sfy);
       Store<S>::st(g + i * pl + c, geq - w * sy);
     }
   }
@@ -215,30 +217,31 @@ cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, 
 }
 
 cudaError_t launch_load_plane(const double* src, void* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double sconst, cudaStream_t s) {
+                              const float* rch, double c0, double c1, cudaStream_t s) {
   return by_storage(storage, false, [&](auto* sp, auto*) {
     using S = std::remove_pointer_t<decltype(sp)>;
-    k_load_plane<S><<<kGrid, kBlock, 0, s>>>(src, static_cast<S*>(dst), Nx, Ny, P, shift_w, rch, sconst);
+    k_load_plane<S><<<kGrid, kBlock, 0, s>>>(src, static_cast<S*>(dst), Nx, Ny, P, shift_w, rch, c0, c1);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_save_plane(const void* src, double* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double sconst, cudaStream_t s) {
+                              const float* rch, double c0, double c1, cudaStream_t s) {
   return by_storage(storage, false, [&](auto* sp, auto*) {
     using S = std::remove_pointer_t<decltype(sp)>;
-    k_save_plane<S><<<kGrid, kBlock, 0, s>>>(static_cast<const S*>(src), dst, Nx, Ny, P, shift_w, rch, sconst);
+    k_save_plane<S><<<kGrid, kBlock, 0, s>>>(static_cast<const S*>(src), dst, Nx, Ny, P, shift_w, rch, c0, c1);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY,
                         const double* cY, const double* Sx, const double* Cy, double Fh, double mub, void* f,
-                        void* g, int storage, int Nx, int Ny, int P, const float* rch, double sf, cudaStream_t s) {
+                        void* g, int storage, int Nx, int Ny, int P, const float* rch, double fb, double fd,
+                        cudaStream_t s) {
   return by_storage(storage, false, [&](auto* sp, auto*) {
     using S = std::remove_pointer_t<decltype(sp)>;
     k_init<S><<<kGrid, kBlock, 0, s>>>(rho_h, rc_h, Eh, sY, cY, Sx, Cy, Fh, mub, static_cast<S*>(f),
-                                       static_cast<S*>(g), Nx, Ny, P, rch, sf);
+                                       static_cast<S*>(g), Nx, Ny, P, rch, fb, fd);
     return cudaGetLastError();
   });
 }

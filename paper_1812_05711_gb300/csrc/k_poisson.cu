@@ -793,7 +793,8 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(4, ms)) != cudaSuccess) return e;
   if (side && (e = cudaEventRecord(join, side)) != cudaSuccess) return e;
-  if ((e = launch_modes<R>(a, s)) != cudaSuccess) return e;
+  e = (a.y_solver == 1) ? launch_modes_oddext(a, sizeof(R) == 8, s) : launch_modes<R>(a, s);
+  if (e != cudaSuccess) return e;
   if ((e = mark(1, s)) != cudaSuccess) return e;
   if (warp_fft) {
     e = launch_irfft_warp(a, s);

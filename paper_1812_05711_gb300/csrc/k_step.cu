@@ -12,11 +12,12 @@
 // The per-CTA wall fluxes are added, in a fixed order, to the run's FP64
 // totals by the mean-mode kernel of the Poisson solve that follows.
 //
-// Shifted storage (FP32 compute): f~_i = f_i - w_i and g~_i = g_i - w_i s(y)
-// with s(y) the hydrostatic charge of the row; the TRT collision is applied to
-// the shifted values (the shift is symmetric in i, so only the equilibrium's
-// rest part changes), and a population moving between rows picks up
-// w_i (s(y) - s(y')).  Plain FP64 uses shift 0 and the same code.
+// Shifted storage (FP32 compute): f~_i = f_i - w_i r(y) and g~_i = g_i - w_i s(y)
+// with r(y) and s(y) the hydrostatic density and charge of the row; the TRT
+// collision is applied to the shifted values (the shift is symmetric in i, so
+// only the equilibrium's rest part changes), and a population moving between
+// rows picks up w_i (r(y) - r(y')) or w_i (s(y) - s(y')).  Plain FP64 uses
+// shifts 0 and the same code.
 #include "ehd_dev.cuh"
 
 namespace ehd {
@@ -79,7 +80,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a, int rows) {
   const float* __restrict__ rch = a.rch;
   const R wp = (R)a.wp, wm = (R)a.wm, gwp = (R)a.gwp, gwm = (R)a.gwm;
   const R cp = R(1) - R(0.5) * wp, cm = R(1) - R(0.5) * wm;
-  const R mub = (R)a.mub, rho0 = (R)a.rho0, sf = (R)a.sf;
+  const R mub = (R)a.mub, rho0 = (R)a.rho0;
+  const R fb = (R)a.fb, fd = (R)a.fd;  // f shift fb + fd y: a row up changes it by fd
   const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
   const R W0 = (R)kW0, W1 = (R)kW1, W2 = (R)kW2;
   double qin = 0.0, qout = 0.0;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a, int rows) {
       const R Ex = R(-0.5) * (pE - pW);
       const R Ey = __ldg(Ebar + y) - R(0.5) * (pN - pS);
       const R sy = rch ? (R)__ldg(rch + y) : R(0);
+      const R sf = fb + fd * (R)y;
       // moments, Eqs. 5-7
       const R drho = ((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7)) + f8;
       const R rho = sf + drho;
@@ -146,12 +149,13 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a, int rows) {
       Store<S>::st(go + 3 * pl + yo + xl, g3);
       if (y + 1 < Ny) {
         const R sh = rch ? sy - (R)__ldg(rch + y + 1) : R(0);
+        const R fh = -fd;
         const long long yu = yo + P;
-        Store<S>::st(fo + 2 * pl + yu + x, f2);
+        Store<S>::st(fo + 2 * pl + yu + x, f2 + W1 * fh);
         Store<S>::st(go + 2 * pl + yu + x, g2 + W1 * sh);
-        Store<S>::st(fo + 5 * pl + yu + xr, f5);
+        Store<S>::st(fo + 5 * pl + yu + xr, f5 + W2 * fh);
         Store<S>::st(go + 5 * pl + yu + xr, g5 + W2 * sh);
-        Store<S>::st(fo + 6 * pl + yu + xl, f6);
+        Store<S>::st(fo + 6 * pl + yu + xl, f6 + W2 * fh);
         Store<S>::st(go + 6 * pl + yu + xl, g6 + W2 * sh);
       } else {
         // collector: f bounces back into its own node, g leaves the channel
@@ -168,12 +172,13 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a, int rows) {
       }
       if (y > 0) {
         const R sh = rch ? sy - (R)__ldg(rch + y - 1) : R(0);
+        const R fh = fd;
         const long long yd = yo - P;
-        Store<S>::st(fo + 4 * pl + yd + x, f4);
+        Store<S>::st(fo + 4 * pl + yd + x, f4 + W1 * fh);
         Store<S>::st(go + 4 * pl + yd + x, g4 + W1 * sh);
-        Store<S>::st(fo + 7 * pl + yd + xl, f7);
+        Store<S>::st(fo + 7 * pl + yd + xl, f7 + W2 * fh);
         Store<S>::st(go + 7 * pl + yd + xl, g7 + W2 * sh);
-        Store<S>::st(fo + 8 * pl + yd + xr, f8);
+        Store<S>::st(fo + 8 * pl + yd + xr, f8 + W2 * fh);
         Store<S>::st(go + 8 * pl + yd + xr, g8 + W2 * sh);
       } else {
         // injector: halfway bounce-back of f; anti-bounce-back of g imposing

@@ -90,6 +90,44 @@ def test_poisson_equals_odd_extension_fft(wall_mode, shape):
 
 
 @pytest.mark.parametrize("wall_mode", [0, 1])
+@pytest.mark.parametrize("x_symbol", [0, 1])
+def test_poisson_oddext_eigenmode_closed_form(wall_mode, x_symbol):
+    """The oracle's literal odd-extension solve (Eqs. 19-25) on one
+    eigenfunction of the discrete Laplacian with Dirichlet walls,
+    s = sin(pi k (j + 1/2) / Ny) cos(2 pi m x / Nx) (walls halfway) or
+    sin(pi k (j + 1) / (Ny + 1)) cos(...) (walls on nodes), returns s divided
+    by its eigenvalue -(kappa_m + 4 sin^2(pi k / NE)), NE = 2 Ny or 2 Ny + 2."""
+    Ny, Nx, k, m = 18, 12, 5, 3
+    j = np.arange(Ny)[:, None]
+    x = np.arange(Nx)[None, :]
+    if wall_mode == 0:
+        NE, yk = 2 * Ny, np.sin(np.pi * k * (j + 0.5) / Ny)
+    else:
+        NE, yk = 2 * Ny + 2, np.sin(np.pi * k * (j + 1.0) / (Ny + 1))
+    src = yk * np.cos(2 * np.pi * m * x / Nx)
+    kappa = (2 * np.pi * m / Nx) ** 2 if x_symbol == 0 else 4 * np.sin(np.pi * m / Nx) ** 2
+    lam = -(kappa + 4 * np.sin(np.pi * k / NE) ** 2)
+    for solve in (o.poisson_oddext, o.poisson_general):
+        phi = solve(src, wall_mode=wall_mode, x_symbol=x_symbol)
+        assert np.abs(phi - src / lam).max() <= 1e-13 * np.abs(src / lam).max()
+
+
+@pytest.mark.parametrize("wall_mode", [0, 1])
+@pytest.mark.parametrize("shape", [(24, 16), (33, 20), (10, 122)])
+def test_poisson_oddext_oracle_equals_numpy_and_tridiagonal(wall_mode, shape):
+    """The oracle's literal solve equals this file's numpy restatement of
+    Eqs. 21-25 and the per-mode tridiagonal, with wall potentials lifted."""
+    rng = np.random.default_rng(41)
+    src = rng.standard_normal(shape)
+    phi = o.poisson_oddext(src, wall_mode=wall_mode)
+    ref = _odd_extension_solve(src, wall_mode)
+    assert np.abs(phi - ref).max() <= 1e-12 * np.abs(ref).max()
+    a = o.poisson_oddext(src, wall_mode=wall_mode, phi_bottom=0.8, phi_top=-0.3)
+    b = o.poisson_general(src, wall_mode=wall_mode, phi_bottom=0.8, phi_top=-0.3)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("wall_mode", [0, 1])
 def test_poisson_wall_potential_lift(wall_mode):
     """With phi0 on the injector the solution is the homogeneous one plus the
     discrete-harmonic linear profile between the walls (reading: lifting)."""
