@@ -469,6 +469,53 @@ def run_fp64(args):
     return 0
 
 
+def run_ysolve(args):
+    """The two y solves of the Poisson equation side by side: the
+    per-wavenumber tridiagonal and the literal odd-extension transform of
+    Eqs. 21-25, on the 2048x1680 FP32 channel (NE = 3360) and the 1024x840
+    plain FP64 channel (NE = 1680).  Whole graph-launched steps (CUDA events
+    on the run's stream) and, from ehd_step_profile, the Poisson solve and its
+    m >= 1 part.  The line's value is the odd-extension FP32 channel."""
+    import torch
+
+    import paper_1812_05711_gb300 as ehd
+
+    torch.cuda.set_device(0)
+    out = {}
+    value = ms_value = None
+    for w, st, K in ((wl.large_channel(), "f32", args.steps), (wl.precision_channel(), "f64", max(args.steps // 10, 20))):
+        run = ehd.Run(*w.args(), storage=st, amp=w.amp, phase=w.phase)
+        stream = torch.cuda.ExternalStream(ehd.ehd_stream(run.handle))
+        res = {}
+        for ys, name in ((0, "tridiagonal"), (1, "odd_extension")):
+            ehd.ehd_tune(run.handle, "y_solver", ys)
+            run.step(args.warmup)
+            run.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run.step(K)
+            e1.record(stream)
+            run.sync()
+            ms = e0.elapsed_time(e1) / K
+            prof = ehd.ehd_step_profile(run.handle, min(K, 200))
+            n = prof["steps"]
+            res[name] = {"glups": _cells(w) / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                         "poisson_us": 1e3 * prof["poisson_ms"] / n, "y_solve_us": 1e3 * prof["modes_ms"] / n,
+                         "fft_x_us": 1e3 * (prof["fft_fwd_ms"] + prof["fft_inv_ms"]) / n}
+            if st == "f32" and ys == 1:
+                value, ms_value = res[name]["glups"], ms
+        run.close()
+        out[f"{w.name}-{st}"] = res
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "channel-2048x1680-oddext", "Nx": 2048, "Ny": 1680, "storage": "f32",
+                       "compute": "f32", "y_solver": "odd_extension"},
+            "y_solvers": out, "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision(args):
     """1024x840, T = 170: every storage (FP64 / FP32 / BF16 / FP16, FP32
     compute) against the plain FP64 GPU path after K steps, and against the
@@ -611,10 +658,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="channel",
-                    choices=["channel", "batch", "serve", "fp64", "precision", "hydrostatic", "bifurcation"],
+                    choices=["channel", "batch", "serve", "fp64", "precision", "hydrostatic", "bifurcation",
+                             "ysolve"],
                     help="channel: 2048x1680 headline (default); batch: 64 uneven runs; serve: request stream; "
                          "fp64: 128x104 plain FP64; precision: 1024x840 storage variants; "
-                         "hydrostatic: Table II e_L2 for a C sweep; bifurcation: Ne(T) both branches")
+                         "hydrostatic: Table II e_L2 for a C sweep; bifurcation: Ne(T) both branches; "
+                         "ysolve: tridiagonal vs odd-extension y solve of the Poisson equation")
     ap.add_argument("--tick", type=int, default=100, help="steps per batch tick (batch / serve)")
     ap.add_argument("--requests", type=int, default=200, help="requests in the serving stream")
     ap.add_argument("--fp64-requests", type=int, default=4, help="prefix served by the plain FP64 path")
@@ -640,6 +689,8 @@ def main():
         return run_hydrostatic(args)
     if args.workload == "bifurcation":
         return run_bifurcation(args)
+    if args.workload == "ysolve":
+        return run_ysolve(args)
     return run_ours(args)
 
 
