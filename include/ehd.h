@@ -66,7 +66,7 @@ typedef enum { EHD_COMPUTE_F64 = 0, EHD_COMPUTE_F32 = 1 } ehd_compute;
 #define EHD_FIELD_UY (1u << 2)
 #define EHD_FIELD_RHOC (1u << 3)  /* charge density, Eq. 6 */
 #define EHD_FIELD_PHI (1u << 4)   /* electric potential, Eq. 4 */
-#define EHD_FIELD_EX (1u << 5)    /* E = -grad phi (central differences) */
+#define EHD_FIELD_EX (1u << 5)    /* E = -grad phi (central differences; E_x spectral with ex_spectral) */
 #define EHD_FIELD_EY (1u << 6)
 #define EHD_FIELD_ALL 0x7Fu
 
@@ -97,6 +97,14 @@ typedef struct {
                        -(2 pi m / Nx)^2 (Eq. 20, default); 1 the 3-point
                        difference -4 sin^2(pi m / Nx), so that the solve
                        inverts the 5-point Laplacian. */
+  int ex_spectral;  /* E_x = -d phi / dx: 0 central difference (default);
+                       1 spectral, the inverse x-transform of -i k_m phi_m
+                       (k_m = 2 pi m / Nx, Nyquist mode dropped), formed by the
+                       Poisson solve into a plane that the march form reads.
+                       Needs the march form with 2 columns per lane and ring
+                       depth 2; refused in batches.  The run then holds two
+                       more arrays, [Ny][P] and [Ny][Mp] complex, beyond
+                       ehd_footprint. */
 } ehd_options;
 
 /* Fill *opt with the defaults above. */

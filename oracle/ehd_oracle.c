@@ -408,7 +408,38 @@ void orc_poisson(const orc_params* p, const double* rhoc, double* phi) {
   free(s);
 }
 
-/* E = -grad phi, central differences; wall ghosts as in the Poisson closure. */
+/* E = -grad phi, central differences; wall ghosts as in the Poisson closure.
+ * With ex_spectral, E_x is the exact derivative of the row's trigonometric
+ * interpolant instead: X_m = DFT(phi row) (Eq. 19), E_x = inverse DFT of
+ * -i k_m X_m with k_m = 2 pi m / Nx for the signed wavenumber m, the Nyquist
+ * coefficient (m = Nx/2) set to zero so that E_x stays real. */
+static void ex_spectral_rows(int Nx, int Ny, const double* phi, double* Ex) {
+  double* re = (double*)malloc(sizeof(double) * Nx);
+  double* im = (double*)malloc(sizeof(double) * Nx);
+  double* tre = (double*)malloc(sizeof(double) * Nx);
+  double* tim = (double*)malloc(sizeof(double) * Nx);
+  for (int y = 0; y < Ny; ++y) {
+    for (int x = 0; x < Nx; ++x) {
+      re[x] = phi[(size_t)y * Nx + x];
+      im[x] = 0.0;
+    }
+    transform_row(Nx, re, im, tre, tim, -1);
+    for (int m = 0; m < Nx; ++m) {
+      const int ms = (m <= Nx / 2) ? m : m - Nx;
+      const double k = (2 * ms == Nx) ? 0.0 : 2.0 * OPI * (double)ms / (double)Nx;
+      const double r = re[m], i = im[m];
+      re[m] = k * i; /* -i k (r + i i') = k i' - i k r */
+      im[m] = -k * r;
+    }
+    transform_row(Nx, re, im, tre, tim, +1);
+    for (int x = 0; x < Nx; ++x) Ex[(size_t)y * Nx + x] = re[x] / (double)Nx;
+  }
+  free(re);
+  free(im);
+  free(tre);
+  free(tim);
+}
+
 void orc_efield(const orc_params* p, const double* phi, double* Ex,
                 double* Ey) {
   int Nx = p->Nx, Ny = p->Ny;
@@ -430,6 +461,7 @@ void orc_efield(const orc_params* p, const double* phi, double* Ex,
       Ey[(size_t)y * Nx + x] = -(pu - pd) / 2.0;
     }
   }
+  if (p->ex_spectral) ex_spectral_rows(Nx, Ny, phi, Ex);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -19,6 +19,8 @@ typedef struct {
   int x_symbol;        /* x second derivative: 0 spectral -kappa_m (Eq. 20),
                           1 second-order difference -4 sin^2(pi m / Nx), the
                           symbol of the 3-point stencil (Eq. 24's form in x) */
+  int ex_spectral;     /* E_x = -d phi / dx: 0 central difference, 1 spectral
+                          (-i k_m times the x-transform of phi, Nyquist mode 0) */
   /* hooks used only by the oracle's own pins (all zero for the method) */
   int periodic_y;      /* y periodic, no walls (requires no_poisson) */
   int no_poisson;      /* E = ext_E instead of -grad phi */

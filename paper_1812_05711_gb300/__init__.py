@@ -54,6 +54,7 @@ class Options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("step_kernel", ctypes.c_int),
         ("x_symbol", ctypes.c_int),
+        ("ex_spectral", ctypes.c_int),
     ]
 
 
@@ -266,7 +267,7 @@ def ehd_last_error() -> str:
 
 # ------------------------------------------------------------ convenience
 def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
-                 amp=(), phase=(), stream=None, step_kernel=0, x_symbol=0) -> Options:
+                 amp=(), phase=(), stream=None, step_kernel=0, x_symbol=0, ex_spectral=0) -> Options:
     o = ehd_default_options()
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if compute is None:
@@ -285,6 +286,7 @@ def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mo
     o.stream = stream
     o.step_kernel = int(step_kernel)
     o.x_symbol = int(x_symbol)
+    o.ex_spectral = int(ex_spectral)
     return o
 
 
@@ -298,14 +300,15 @@ class Run:
 
     def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
                  u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=0,
-                 x_symbol=0):
+                 x_symbol=0, ex_spectral=0):
         self.Nx, self.Ny = int(Nx), int(Ny)
         self._stream_obj = None
         if stream is None and torch_stream:
             import torch
             self._stream_obj = torch.cuda.Stream()
             stream = self._stream_obj.cuda_stream
-        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel, x_symbol)
+        opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel, x_symbol,
+                           ex_spectral)
         self.handle = ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt)
 
     # lifecycle

@@ -103,6 +103,9 @@ struct ehd_run {
   int y_solver = 0;    // y solve of m >= 1: 0 tridiagonal, 1 odd-extension transform
   int NE = 0, nfac = -1, fac[16] = {};  // odd-extension length and radices (nfac < 0: unsupported)
   void* oddt = nullptr;  // its tables: complex R [NE] twiddles, R [NE] y symbol, R [Mh] x symbol
+  int ex_spectral = 0;   // E_x from the x-spectrum of phi instead of central differences
+  void* exs = nullptr;   // R [Ny][P] spectral E_x (ex_spectral only)
+  void* spec_dx = nullptr;  // complex R [Ny][Mp]: its half spectrum
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -221,6 +224,7 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.fb = r->fb;
   a.fd = r->fd;
   a.fdq = -r->fd * r->tau_m;
+  a.ex = r->exs;
   a.flux_part = r->flux_part;
   a.err = r->err;
   a.wp = 1.0 / r->tau_p;
@@ -273,6 +277,8 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.pdl = r->pdl;
   a.fft_cta = r->fft_cta;
   a.y_solver = r->y_solver;
+  a.ex = r->exs;
+  a.spec_dx = r->spec_dx;
   a.NE = r->NE;
   a.nfac = r->nfac;
   for (int k = 0; k < 16; ++k) a.fac[k] = r->fac[k];
@@ -306,6 +312,7 @@ FieldArgs field_args(const ehd_run* r) {
   a.rch = r->rch;
   a.fb = r->fb;
   a.fd = r->fd;
+  a.ex = r->exs;
   a.mub = r->mub;
   a.wall_mode = r->wall_mode;
   return a;
@@ -454,6 +461,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_EINVAL, "FP64 compute needs FP64 storage");
   if (o.wall_mode != 0 && o.wall_mode != 1) return fail(EHD_EINVAL, "wall_mode must be 0 or 1");
   if (o.x_symbol != 0 && o.x_symbol != 1) return fail(EHD_EINVAL, "x_symbol must be 0 or 1");
+  if (o.ex_spectral != 0 && o.ex_spectral != 1) return fail(EHD_EINVAL, "ex_spectral must be 0 or 1");
+  if (o.ex_spectral && o.step_kernel != 0) return fail(EHD_EINVAL, "spectral E_x needs the march form");
   if (o.n_modes < 0 || o.n_modes > EHD_MAX_PERT_MODES) return fail(EHD_EINVAL, "n_modes out of range");
   if (o.step_kernel != 0 && o.step_kernel != 1) return fail(EHD_EINVAL, "step_kernel must be 0 or 1");
 
@@ -551,6 +560,11 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->NE = (r->wall_mode == 0) ? 2 * Ny : 2 * Ny + 2;
   r->nfac = oddext_factors(r->NE, r->fac, 16);
   if (r->nfac > 0) r->oddt = run_alloc(r, (3 * (size_t)r->NE + r->Mh) * r->rsz);
+  r->ex_spectral = o.ex_spectral;
+  if (r->ex_spectral) {
+    r->exs = run_alloc(r, (size_t)Ny * r->P * r->rsz);
+    r->spec_dx = run_alloc(r, (size_t)Ny * r->Mp * 2 * r->rsz);
+  }
   r->rx_dn = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->rx_up = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->step_kernel = o.step_kernel;
@@ -564,7 +578,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->rx_dn && r->rx_up && r->phibar &&
             r->Ebar && r->spec && r->spec0 &&
             r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part &&
-            (r->nfac <= 0 || r->oddt);
+            (r->nfac <= 0 || r->oddt) && (!r->ex_spectral || (r->exs && r->spec_dx));
   if (!ok) {
     destroy_quiet(r);
     return fail(EHD_ENOMEM, "device allocation failed");
@@ -739,6 +753,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       break;
     case EHD_TUNE_RING_DEPTH:
       if (value != 2 && value != 3 && value != 4 && value != 6) return fail(EHD_EINVAL, "ring depth must be 2, 3, 4 or 6");
+      if (value != 2 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x runs keep ring depth 2");
       if (value == 6 && r->cols_per_lane == 2) return fail(EHD_EINVAL, "ring depth 6 needs one column per lane");
       r->ring_depth = value;
       break;
@@ -771,6 +786,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
     }
     case EHD_TUNE_COLS_PER_LANE:
       if (value != 1 && value != 2) return fail(EHD_EINVAL, "columns per lane must be 1 or 2");
+      if (value != 2 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x runs keep two columns per lane");
       if (value == 2 && r->ring_depth == 6) r->ring_depth = 3;
       r->cols_per_lane = value;
       r->nstrips = march_strips(r->Nx, value);
@@ -778,6 +794,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       break;
     case EHD_TUNE_STEP_KERNEL:
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "step kernel must be 0 or 1");
+      if (value != 0 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x needs the march form");
       r->step_kernel = value;
       r->nxb = (value == 0) ? r->nstrips : step_flux_blocks(r->Nx);
       break;
@@ -1188,6 +1205,7 @@ ehd_status ehd_batch_add(ehd_batch* b, ehd_run* r, long steps) {
   if (r->storage != EHD_STORE_F32 || r->real_f64 || r->step_kernel != 0)
     return fail(EHD_EINVAL, "batches take FP32-storage, FP32-compute runs in the march form");
   if (r->y_solver != 0) return fail(EHD_EINVAL, "batches take runs with the tridiagonal y solve");
+  if (r->ex_spectral) return fail(EHD_EINVAL, "batches take runs with central-difference E_x");
   if (r->Nx < 64 || r->Nx > b->max_nx || r->Ny > b->max_ny) return fail(EHD_EINVAL, "run size exceeds the batch limits");
   if (r->device != b->device) return fail(EHD_EINVAL, "run and batch are on different devices");
   if ((int)b->members.size() >= b->max_runs) return fail(EHD_EBUSY, "batch is full");

@@ -112,6 +112,7 @@ struct StepArgs {
   double wp, wm, gwp, gwm;   // omega+, omega-, omega_g+, omega_g-
   double mub, rho0;          // ion mobility, injected density
   double fb, fd, fdq;        // f shift r(y) = fb + fd y (fd an FP32 value), and -fd / omega- (0 when unshifted)
+  const void* ex;            // R [Ny][P]: spectral E_x, or nullptr for central differences of dphi
   int wall_mode;
   // march form only
   void* rhoc_out;            // R [Ny][P]: rho_c of the new state (slab-boundary rows: partial, see rhoc_dn)
@@ -156,6 +157,8 @@ struct PoissonArgs {
   const void* twy;           // complex R [NE]: exp(-2 pi i t / NE)
   const void* symy;          // R [NE]: 4 sin^2(pi k / NE)
   const void* kap;           // R [Mh]: kappa_m, the x symbol of wavenumber m
+  void* ex;                  // R [Ny][P]: spectral E_x written after phi, or nullptr
+  void* spec_dx;             // complex R [Ny][Mp]: -i k_m phi_m, its half spectrum
 };
 
 // Charge density of row y as the Poisson solve sees it: the step kernel's
@@ -183,6 +186,7 @@ struct FieldArgs {
   const void* phibar;        // double, or float (hi, lo) pairs when R = float
   const void* Ebar;
   const float* rch;
+  const void* ex;            // R [Ny][P]: spectral E_x, or nullptr
   double fb, fd;             // f shift r(y) = fb + fd y
   double mub;
   int wall_mode;

@@ -449,10 +449,11 @@ struct Pair<__half> {  // scaled by 2^12 like Store<__half>
   }
 };
 
-template <class S, class R, int NSTAGE>
+// SPECX: one more slot per stage holds the row's spectral E_x pair
+template <class S, class R, int NSTAGE, bool SPECX = false>
 struct March2Stages {
   static constexpr int kSlotBytes = 2 * (sizeof(S) > sizeof(R) ? sizeof(S) : sizeof(R));
-  static constexpr int kSlots = 20;
+  static constexpr int kSlots = SPECX ? 21 : 20;
   static constexpr size_t kBytesPerWarp = (size_t)NSTAGE * kSlots * 32 * kSlotBytes;
 };
 
@@ -489,9 +490,9 @@ __device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R
 
 // One warp's walk over slab `slab` of strip `strip`; warp_ring is the warp's
 // NSTAGE-row staging area.  Shared by the single-run and the batch kernels.
-template <class S, class R, int NSTAGE>
+template <class S, class R, int NSTAGE, bool SPECX = false>
 __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int slab, unsigned char* warp_ring) {
-  using St = March2Stages<S, R, NSTAGE>;
+  using St = March2Stages<S, R, NSTAGE, SPECX>;
   constexpr int NST = NSTAGE, SL = St::kSlots, SB = St::kSlotBytes;
   const int lane = threadIdx.x & 31;
   const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
@@ -556,6 +557,7 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       cp_async_elem<2 * sizeof(S)>(slot(stage, 9 + i), gin + i * pl + c);
     }
     if (row_y + 1 < Ny) cp_async_elem<2 * sizeof(R)>(slot(stage, 18), dphi + c + P);
+    if constexpr (SPECX) cp_async_elem<2 * sizeof(R)>(slot(stage, 20), static_cast<const R*>(a.ex) + c);
     if (lane == 1) {
       cp_async_elem<sizeof(R)>(slot(stage, 19), Ebar + row_y);
     } else if (rch && lane == 2) {
@@ -598,9 +600,17 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
     const R s_dn = (rch && r > 0) ? (R)__shfl_sync(0xffffffffu, ex_f, 4) : sy;
     const R sf = fb + fd * (R)r;
     // E = -grad phi at both nodes of the pair
-    const R pWl = from_left(pc[1]);   // phi(xc - 1)
-    const R pEr = from_right(pc[0]);  // phi(xc + 2)
-    const R Ex0 = R(-0.5) * (pc[1] - pWl), Ex1 = R(-0.5) * (pEr - pc[0]);
+    R Ex0, Ex1;
+    if constexpr (SPECX) {
+      const R* ex = reinterpret_cast<const R*>(slot(st, 20));
+      Ex0 = ex[0];
+      Ex1 = ex[1];
+    } else {
+      const R pWl = from_left(pc[1]);   // phi(xc - 1)
+      const R pEr = from_right(pc[0]);  // phi(xc + 2)
+      Ex0 = R(-0.5) * (pc[1] - pWl);
+      Ex1 = R(-0.5) * (pEr - pc[0]);
+    }
     const R Ey0 = Ebr - R(0.5) * (pn[0] - pm[0]), Ey1 = Ebr - R(0.5) * (pn[1] - pm[1]);
     R f0[9], g0[9], f1[9], g1[9];
 #pragma unroll
@@ -833,12 +843,13 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
   }
 }
 
-template <class S, class R, int NSTAGE>
+template <class S, class R, int NSTAGE, bool SPECX = false>
 __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
   extern __shared__ __align__(16) unsigned char march_smem[];
   const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
-  march2_body<S, R, NSTAGE>(a, gw % a.nstrips, gw / a.nstrips,
-                            march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<S, R, NSTAGE>::kBytesPerWarp);
+  march2_body<S, R, NSTAGE, SPECX>(
+      a, gw % a.nstrips, gw / a.nstrips,
+      march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<S, R, NSTAGE, SPECX>::kBytesPerWarp);
 }
 
 // Batch: every warp of a fixed grid takes march items (run, strip, slab) in
@@ -873,15 +884,20 @@ cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class S, class R, int NST>
+template <class S, class R, int NST, bool SPECX = false>
 cudaError_t march2_n(const StepArgs& a, cudaStream_t s) {
   const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
-  k_march2<S, R, NST><<<(unsigned)((warps + 3) / 4), 128, 4 * March2Stages<S, R, NST>::kBytesPerWarp, s>>>(a);
+  k_march2<S, R, NST, SPECX>
+      <<<(unsigned)((warps + 3) / 4), 128, 4 * March2Stages<S, R, NST, SPECX>::kBytesPerWarp, s>>>(a);
   return cudaGetLastError();
 }
 
 template <class S, class R>
 cudaError_t march_t(const StepArgs& a, cudaStream_t s) {
+  if (a.ex) {  // spectral E_x: march form, two columns per lane, ring depth 2
+    if (a.cols_per_lane != 2 || a.ring_depth != 2) return cudaErrorInvalidValue;
+    return march2_n<S, R, 2, true>(a, s);
+  }
   if (a.cols_per_lane == 2) {
     switch (a.ring_depth) {
       case 2: return march2_n<S, R, 2>(a, s);
@@ -914,6 +930,7 @@ cudaError_t attrs_t() {
   cudaError_t e;
   if ((e = allow_smem(k_batch_march)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 2>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march2<S, R, 2, true>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 3>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 4>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march<S, R, 2>)) != cudaSuccess) return e;

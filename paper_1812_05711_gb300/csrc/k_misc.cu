@@ -41,7 +41,8 @@ __device__ Macro macro_at(const FieldArgs& a, int x, int y) {
   const double pS = (y > 0) ? (double)dphi[c - a.P] : gw * pc;
   const double pN = (y < a.Ny - 1) ? (double)dphi[c + a.P] : gw * pc;
   Macro m;
-  m.Ex = -0.5 * ((double)dphi[c - x + xr] - (double)dphi[c - x + xl]);
+  m.Ex = a.ex ? (double)static_cast<const R*>(a.ex)[c]
+              : -0.5 * ((double)dphi[c - x + xr] - (double)dphi[c - x + xl]);
   m.Ey = (double)static_cast<const R*>(a.Ebar)[y] - 0.5 * (pN - pS);
   m.phi = load_phibar<R>(a.phibar, y) + pc;
   m.rho = rho;

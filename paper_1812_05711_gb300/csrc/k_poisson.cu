@@ -20,6 +20,8 @@
 //                 step's wall-flux partials to the run's FP64 totals.  It
 //                 runs on a second stream, beside k_modes_tile/k_rfft_inv.
 //   k_irfft_rows  inverse of k_rfft_rows -> phi minus its row mean.
+#include <algorithm>
+
 #include "ehd_dev.cuh"
 
 namespace ehd {
@@ -455,6 +457,27 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
   }
 }
 
+// Half spectrum of E_x = -d phi / dx from that of phi: -i k_m phi_m with
+// k_m = 2 pi m / Nx; m = 0 (the mean, carried apart) and the Nyquist
+// coefficient m = Nx / 2 are zero, so the inverse transform is real.
+template <class R>
+__global__ void k_spec_dx(PoissonArgs a) {
+  const Cplx<R>* __restrict__ spec = static_cast<const Cplx<R>*>(a.spec);
+  Cplx<R>* __restrict__ out = static_cast<Cplx<R>*>(a.spec_dx);
+  const long long n = (long long)a.Ny * a.Mh;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(q / a.Mh), m = (int)(q % a.Mh);
+    const long long c = (long long)y * a.Mp + m;
+    if (m == 0 || 2 * m == a.Nx) {
+      out[c] = {R(0), R(0)};
+    } else {
+      const R k = (R)(2.0 * 3.14159265358979323846 * (double)m / (double)a.Nx);
+      const Cplx<R> v = spec[c];
+      out[c] = {k * v.im, -k * v.re};
+    }
+  }
+}
+
 // threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
 constexpr int kTileThreads = 256;
 
@@ -803,6 +826,21 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
+  if (a.ex) {
+    // spectral E_x: -i k_m phi_m, then the same inverse row transform
+    PoissonArgs b = a;
+    b.spec = a.spec_dx;
+    b.dphi = a.ex;
+    k_spec_dx<R><<<(int)std::min<long long>(((long long)a.Ny * a.Mh + 255) / 256, 4096), 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (warp_fft) {
+      e = launch_irfft_warp(b, s);
+    } else {
+      k_irfft_rows<R><<<row_blocks<R>(b.Nx, b.Ny), 256, row_smem<R>(b.Nx), s>>>(b);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+  }
   if ((e = mark(2, s)) != cudaSuccess) return e;
   if (side && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   return cudaSuccess;

@@ -5,6 +5,8 @@ absolute difference divided by the field's physical scale -- rho: 1,
 u: u_ion, rho_c: rho0, phi: dphi0 = 1, E: dphi0 / H.  Bars: plain FP64
 <= 1e-12 after 1000 steps; FP32 compute on shifted FP32 storage <= 2e-5.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -191,6 +193,33 @@ def test_storage_variants_error_vs_oracle(storage, compute, bound):
     o.step(s, 200)
     e = _errors(p, run.fields(), o.fields(s))
     assert all(np.isfinite(v) for v in e.values())
+    assert max(e.values()) <= bound, e
+
+
+@functools.lru_cache(maxsize=1)
+def _oracle_1024x840(steps):
+    w = wl.precision_channel()
+    p = o.setup(*w.args())
+    s = o.init_state(p, w.amp, w.phase)
+    o.step(s, steps)
+    return p, o.fields(s)
+
+
+@gpu
+@pytest.mark.parametrize("storage,compute,bound", [("f64", "f64", 1e-11), ("f32", "f32", 1e-6),
+                                                   ("bf16", "f32", 1e-3), ("f16", "f32", 2e-4)])
+def test_storage_variants_vs_oracle_1024x840(storage, compute, bound):
+    """The 1024 x 840, T = 170 channel after 50 steps, every storage against
+    the oracle (measured: plain FP64 2.2e-12 -- the oracle's own Thomas
+    rounding at this height --, FP32 6.3e-8, BF16 2.5e-4, FP16 3.3e-5)."""
+    ehd = _ehd()
+    w = wl.precision_channel()
+    p, ora = _oracle_1024x840(50)
+    run = ehd.Run(*w.args(), storage=storage, compute=compute, amp=w.amp, phase=w.phase)
+    run.step(50)
+    e = _errors(p, run.fields(), ora)
+    run.close()
+    print(f"\n1024x840 {storage}/{compute} after 50 steps: {max(e.values()):.3g} ({max(e, key=e.get)})")
     assert max(e.values()) <= bound, e
 
 

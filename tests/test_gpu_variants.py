@@ -1,7 +1,8 @@
 """Variants of the step against the oracle (GPU, through the C ABI): the
 fluid magic parameter Lambda of Eq. 17 (1/12 as printed in Sec. IV.2, 3/16,
 1/4), the single-relaxation-time limit Lambda = (tau+ - 1/2)^2 (tau- =
-tau+), and the 3-point x symbol of the Poisson solve."""
+tau+), the 3-point x symbol of the Poisson solve, and E_x taken spectrally
+from the x-transform of phi instead of by central differences."""
 import numpy as np
 import pytest
 
@@ -24,13 +25,13 @@ def _scaled_err(p, A, B):
     return max(float(np.abs(A[k] - B[k]).max() / sc[k]) for k in A)
 
 
-def _compare(ehd, Lam, storage="f64", x_symbol=0, steps=300, T=200.0):
+def _compare(ehd, Lam, storage="f64", x_symbol=0, steps=300, T=200.0, ex_spectral=0):
     Nx, Ny = 64, 52
     amp, ph = wl.roll(41, 1e-2)
-    p = o.setup(Nx, Ny, T, 10, 10, 4000, Lam, u_ion=5e-3, x_symbol=x_symbol)
+    p = o.setup(Nx, Ny, T, 10, 10, 4000, Lam, u_ion=5e-3, x_symbol=x_symbol, ex_spectral=ex_spectral)
     s = o.init_state(p, amp, ph)
     run = ehd.Run(Nx, Ny, T, 10, 10, 4000, Lam, storage=storage, u_ion=5e-3, amp=amp, phase=ph,
-                  x_symbol=x_symbol)
+                  x_symbol=x_symbol, ex_spectral=ex_spectral)
     par = run.params()
     run.step(steps)
     o.step(s, steps)
@@ -109,3 +110,54 @@ def test_launch_shape_knobs_keep_results():
     for tune in (dict(fft_cta=0), dict(tile_modes=4), dict(tile_modes=1), dict(step_kernel=1)):
         e = _scaled_err(p, run_with(**tune), base)
         assert e <= 2e-6, (tune, e)
+
+
+@gpu
+@pytest.mark.parametrize("storage,bound", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 5e-2)])
+def test_spectral_ex_parity(storage, bound):
+    """E_x = -d phi/dx from the x-spectrum of phi (-i k_m phi_m, Nyquist
+    dropped) in the coupled step, against the oracle with the same option;
+    BF16 storage at the bar of its storage-variant test."""
+    ehd = _ehd()
+    p, _, e = _compare(ehd, 0.25, storage=storage, ex_spectral=1)
+    assert e <= bound, e
+
+
+@gpu
+def test_spectral_ex_field_and_effect():
+    """The run's E_x field is the oracle's spectral derivative of the run's
+    own phi (1e-12), and the option changes the state measurably."""
+    ehd = _ehd()
+    amp, ph = wl.roll(41, 1e-2)
+    runs = [ehd.Run(64, 52, 200.0, 10, 10, 4000, 0.25, storage="f64", u_ion=5e-3, amp=amp, phase=ph,
+                    ex_spectral=k) for k in (0, 1)]
+    for r in runs:
+        r.step(300)
+    A, B = runs[0].fields(), runs[1].fields()
+    p1 = o.setup(64, 52, 200.0, 10, 10, 4000, 0.25, u_ion=5e-3, ex_spectral=1)
+    ex, ey = o.efield(p1, B["phi"])
+    for r in runs:
+        r.close()
+    assert np.abs(B["Ex"] - ex).max() <= 1e-12 * max(1.0, np.abs(ex).max())
+    assert np.abs(B["Ey"] - ey).max() <= 1e-12 * max(1.0, np.abs(ey).max())
+    # the E_x forms differ by O(k^2) of the roll's mode: 1e-4 of u_x here,
+    # against FP64 rounding at 1e-16
+    assert np.abs(A["ux"] - B["ux"]).max() > 1e-6 * np.abs(A["ux"]).max()
+
+
+@gpu
+def test_spectral_ex_refusals():
+    """Spectral E_x runs keep the march form with two columns per lane and
+    ring depth 2 and stay out of batches."""
+    ehd = _ehd()
+    with pytest.raises(RuntimeError):
+        ehd.Run(64, 52, 200.0, 10, 10, 4000, 0.25, storage="f32", ex_spectral=1, step_kernel=1)
+    r = ehd.Run(64, 52, 200.0, 10, 10, 4000, 0.25, storage="f32", ex_spectral=1)
+    for param, value in (("cols_per_lane", 1), ("ring_depth", 3), ("step_kernel", 1)):
+        with pytest.raises(RuntimeError):
+            ehd.ehd_tune(r.handle, param, value)
+    b = ehd.Batch(2, max_nx=64, max_ny=52)
+    with pytest.raises(RuntimeError):
+        b.add(r, 10)
+    b.close()
+    r.close()

@@ -467,3 +467,46 @@ def test_threshold_sign_of_growth_eq29_roll():
     assert s150 < 0 < s180, (s150, s180)
     # the unstable side grows by well over the decaying side's rate
     assert s180 > 4 * abs(s150)
+
+
+# ------------------------------------------------- spectral E_x (variant) ---
+@pytest.mark.parametrize("Nx", [16, 24])
+def test_spectral_ex_of_fourier_modes(Nx):
+    """E_x = -d phi/dx of a row that is a sum of Fourier modes is exact with
+    the spectral derivative: phi = cos(2 pi k x / Nx + t) g(y) gives
+    E_x = (2 pi k / Nx) sin(2 pi k x / Nx + t) g(y) for k < Nx/2; the Nyquist
+    mode cos(pi x) contributes nothing; central differences give
+    sin(2 pi k / Nx) in place of 2 pi k / Nx; E_y is the same either way."""
+    Ny = 7
+    p0 = o.setup(Nx, Ny, 200.0, 10, 10, 4000, 0.25)
+    p1 = o.setup(Nx, Ny, 200.0, 10, 10, 4000, 0.25, ex_spectral=1)
+    x = np.arange(Nx)[None, :]
+    gy = 1.0 + np.arange(Ny)[:, None] / Ny
+    phi, ref, cen = 0.3 * np.cos(np.pi * x) * gy, np.zeros((Ny, Nx)), np.zeros((Ny, Nx))
+    for k, t, a in ((1, 0.4, 1.0), (3, -1.1, 0.5), (Nx // 2 - 1, 2.0, 0.25)):
+        th = 2 * np.pi * k * x / Nx + t
+        phi = phi + a * np.cos(th) * gy
+        ref = ref + a * (2 * np.pi * k / Nx) * np.sin(th) * gy
+        cen = cen + a * np.sin(2 * np.pi * k / Nx) * np.sin(th) * gy
+    ex1, ey1 = o.efield(p1, phi)
+    ex0, ey0 = o.efield(p0, phi)
+    assert np.abs(ex1 - ref).max() <= 1e-13
+    assert np.abs(ex0 - cen).max() <= 1e-13
+    assert np.array_equal(ey0, ey1)
+
+
+def test_spectral_ex_changes_the_coupled_step():
+    """The option reaches the step: 200 steps of a roll differ between the two
+    E_x forms by more than rounding, and the spectral run still conserves
+    mass to the oracle's rounding."""
+    amp, ph = [1e-2], [0.3]
+    states = []
+    for ex in (0, 1):
+        p = o.setup(32, 26, 200.0, 10, 10, 4000, 0.25, u_ion=5e-3, ex_spectral=ex)
+        s = o.init_state(p, amp, ph)
+        d = o.step(s, 200, diag=True)
+        states.append((o.fields(s), d))
+    A, B = states[0][0], states[1][0]
+    assert np.abs(A["ux"] - B["ux"]).max() > 1e-9
+    d = states[1][1]
+    assert abs(d[-1, 0] - d[0, 0]) <= 1e-11 * abs(d[0, 0])
