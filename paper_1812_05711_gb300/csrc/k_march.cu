@@ -1,21 +1,29 @@
-// k_march.cu -- the fused collide-and-stream kernel in "march" form: one warp
-// walks up a slab of rows of a 32-column strip (30 owned columns plus one halo
-// column on each side), so that every population it stores has been pulled
-// from registers (x-neighbours by warp shuffles, y-neighbours from the rows
-// already collided) and the charge of the new state, rho_c(t+1) = sum_i g_i
-// (Eq. 6), is formed from exactly the values stored -- no second pass over g.
+// k_march.cu -- the fused collide-and-stream kernel in "march" form: a warp
+// walks up a slab of rows of a strip of columns, so that every population it
+// stores has been pulled from registers (x-neighbours by warp shuffles,
+// y-neighbours from the rows already collided) and the charge of the new
+// state, rho_c(t+1) = sum_i g_i (Eq. 6), is formed from exactly the values
+// stored -- no second pass over g.
 //
-// Per row r of the walk: load the 9 f and 9 g of the lane's node (the next
-// row is prefetched), form E = -grad phi, the moments (Eqs. 5-7), collide f
-// with the electric force (TRT, Eqs. 8, 10, 12, 13, 15) and g with the drift
-// (TRT, Eqs. 9, 11, 14), then route the post-collision values:
+// Per row r of the walk: load the 9 f and 9 g of the lane's node(s) (the next
+// rows are staged ahead by cp.async), form E = -grad phi (central differences
+// of phi, or the spectral E_x plane), the moments (Eqs. 5-7), collide f with
+// the electric force (TRT, Eqs. 8, 10, 12, 13, 15) and g with the drift (TRT,
+// Eqs. 9, 11, 14), then route the post-collision values:
 //   c_y = 0   -> row r     (complete once row r+1 has been collided)
 //   c_y = +1  -> row r + 1 (kept in registers)
 //   c_y = -1  -> row r - 1 (completes row r - 1, which is stored)
 // The walls of Table I enter as row rules: halfway bounce-back of f on both
 // walls, anti-bounce-back injection of rho0 (with the wall drift mu_b E) and
-// zero-gradient outflow of g.  Halo rows (one below and one above the slab)
-// and halo columns are collided but not stored.
+// zero-gradient outflow of g.
+//
+// Two forms.  k_march2 (the default): two adjacent nodes per lane, a strip of
+// 64 columns (60 owned, one halo pair on each side, collided but not stored);
+// the slab's own rows only -- populations that leave the slab are pushed into
+// the neighbouring slab's boundary row with their share of that row's charge
+// (rhoc_dn / rhoc_up, added by the forward transform), so no row is collided
+// twice.  k_march: one node per lane, a 32-column strip (30 owned), with a
+// halo row below and above the slab collided but not stored.
 #include <type_traits>
 
 #include "ehd_dev.cuh"

@@ -89,28 +89,41 @@ __device__ void stage(const Cplx<R>* __restrict__ x, Cplx<R>* __restrict__ y, in
   }
 }
 
-template <class R, bool INV>
+// MAXP: the largest radix compiled in (7 or 13); the 11- and 13-point
+// DFTs double the kernel's registers, so lengths without those factors use
+// the MAXP = 7 instance (64 registers: four CTAs per SM instead of two)
+template <class R, bool INV, int MAXP>
 __device__ void run_stage(int P, const Cplx<R>* x, Cplx<R>* y, int N, int Ns, const Cplx<R>* tw) {
   switch (P) {
     case 2: stage<R, 2, INV>(x, y, N, Ns, tw); break;
     case 3: stage<R, 3, INV>(x, y, N, Ns, tw); break;
     case 4: stage<R, 4, INV>(x, y, N, Ns, tw); break;
     case 5: stage<R, 5, INV>(x, y, N, Ns, tw); break;
-    case 7: stage<R, 7, INV>(x, y, N, Ns, tw); break;
-    case 11: stage<R, 11, INV>(x, y, N, Ns, tw); break;
-    default: stage<R, 13, INV>(x, y, N, Ns, tw); break;
+    default:
+      if constexpr (MAXP > 7) {
+        if (P == 11) {
+          stage<R, 11, INV>(x, y, N, Ns, tw);
+          break;
+        }
+        if (P == 13) {
+          stage<R, 13, INV>(x, y, N, Ns, tw);
+          break;
+        }
+      }
+      stage<R, 7, INV>(x, y, N, Ns, tw);
+      break;
   }
 }
 
 // FFT of the NE points in buf[0] (buf[1] scratch); returns the buffer that
 // holds the result
-template <class R, bool INV>
+template <class R, bool INV, int MAXP>
 __device__ Cplx<R>* fft_column(const PoissonArgs& a, Cplx<R>* b0, Cplx<R>* b1, const Cplx<R>* tw) {
   Cplx<R>* x = b0;
   Cplx<R>* y = b1;
   int Ns = 1;
   for (int s = 0; s < a.nfac; ++s) {
-    run_stage<R, INV>(a.fac[s], x, y, a.NE, Ns, tw);
+    run_stage<R, INV, MAXP>(a.fac[s], x, y, a.NE, Ns, tw);
     Ns *= a.fac[s];
     Cplx<R>* t = x;
     x = y;
@@ -120,7 +133,7 @@ __device__ Cplx<R>* fft_column(const PoissonArgs& a, Cplx<R>* b0, Cplx<R>* b1, c
   return x;
 }
 
-template <class R>
+template <class R, int MAXP>
 __global__ void __launch_bounds__(kOddThreads) k_modes_oddext(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   grid_dep_wait();
@@ -145,7 +158,7 @@ __global__ void __launch_bounds__(kOddThreads) k_modes_oddext(PoissonArgs a) {
     b0[NE - 1 - j] = {-s.re, -s.im};
   }
   __syncthreads();
-  Cplx<R>* X = fft_column<R, false>(a, b0, b1, tw);
+  Cplx<R>* X = fft_column<R, false, MAXP>(a, b0, b1, tw);
   // divide by the symbol (Eqs. 20, 24) and by NE for the inverse
   {
     const R kap = static_cast<const R*>(a.kap)[m];
@@ -156,7 +169,7 @@ __global__ void __launch_bounds__(kOddThreads) k_modes_oddext(PoissonArgs a) {
     }
   }
   __syncthreads();
-  Cplx<R>* Y = fft_column<R, true>(a, X, X == b0 ? b1 : b0, tw);
+  Cplx<R>* Y = fft_column<R, true, MAXP>(a, X, X == b0 ? b1 : b0, tw);
   for (int j = threadIdx.x; j < Ny; j += blockDim.x) spec[(long long)j * Mp + m] = Y[off + j];
 }
 
@@ -187,8 +200,13 @@ cudaError_t launch_modes_oddext(const PoissonArgs& a, bool real_f64, cudaStream_
   if (a.Mh <= 1) return cudaSuccess;
   const dim3 grid(a.Mh - 1), block(kOddThreads);
   const bool pdl = a.pdl != 0;
-  if (real_f64) return launch_ex(pdl, k_modes_oddext<double>, grid, block, oddext_smem<double>(a.NE), s, a);
-  return launch_ex(pdl, k_modes_oddext<float>, grid, block, oddext_smem<float>(a.NE), s, a);
+  bool small = true;  // every radix <= 7
+  for (int k = 0; k < a.nfac; ++k) small = small && a.fac[k] <= 7;
+  if (real_f64)
+    return small ? launch_ex(pdl, k_modes_oddext<double, 7>, grid, block, oddext_smem<double>(a.NE), s, a)
+                 : launch_ex(pdl, k_modes_oddext<double, 13>, grid, block, oddext_smem<double>(a.NE), s, a);
+  return small ? launch_ex(pdl, k_modes_oddext<float, 7>, grid, block, oddext_smem<float>(a.NE), s, a)
+               : launch_ex(pdl, k_modes_oddext<float, 13>, grid, block, oddext_smem<float>(a.NE), s, a);
 }
 
 cudaError_t oddext_set_attributes() {
@@ -197,9 +215,13 @@ cudaError_t oddext_set_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_modes_oddext<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(k_modes_oddext<double, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_modes_oddext<double, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_modes_oddext<float, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_modes_oddext<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return cudaFuncSetAttribute(k_modes_oddext<float, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 }  // namespace ehd

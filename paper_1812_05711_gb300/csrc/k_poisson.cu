@@ -464,18 +464,20 @@ template <class R>
 __global__ void k_spec_dx(PoissonArgs a) {
   const Cplx<R>* __restrict__ spec = static_cast<const Cplx<R>*>(a.spec);
   Cplx<R>* __restrict__ out = static_cast<Cplx<R>*>(a.spec_dx);
-  const long long n = (long long)a.Ny * a.Mh;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(q / a.Mh), m = (int)(q % a.Mh);
-    const long long c = (long long)y * a.Mp + m;
-    if (m == 0 || 2 * m == a.Nx) {
-      out[c] = {R(0), R(0)};
-    } else {
-      const R k = (R)(2.0 * 3.14159265358979323846 * (double)m / (double)a.Nx);
-      const Cplx<R> v = spec[c];
-      out[c] = {k * v.im, -k * v.re};
+  // k_1 = 2 pi / Nx exactly scaled (Nx a power of two), in the compute type:
+  // no FP64 arithmetic per element on the FP32 path
+  const R k1 = R(6.283185307179586476925286766559) / (R)a.Nx;
+  for (int y = blockIdx.x; y < a.Ny; y += gridDim.x)
+    for (int m = threadIdx.x; m < a.Mh; m += blockDim.x) {
+      const long long c = (long long)y * a.Mp + m;
+      if (m == 0 || 2 * m == a.Nx) {
+        out[c] = {R(0), R(0)};
+      } else {
+        const R k = k1 * (R)m;
+        const Cplx<R> v = spec[c];
+        out[c] = {k * v.im, -k * v.re};
+      }
     }
-  }
 }
 
 // threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
@@ -831,7 +833,7 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
     PoissonArgs b = a;
     b.spec = a.spec_dx;
     b.dphi = a.ex;
-    k_spec_dx<R><<<(int)std::min<long long>(((long long)a.Ny * a.Mh + 255) / 256, 4096), 256, 0, s>>>(a);
+    k_spec_dx<R><<<std::min(a.Ny, 4096), 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (warp_fft) {
       e = launch_irfft_warp(b, s);
