@@ -37,10 +37,10 @@ __device__ __forceinline__ Cplx<R> root(const Cplx<R>* __restrict__ tw, int t) {
   return w;
 }
 
-// P-point DFT of v in registers: o_q = sum_r v_r w^(r q), w = exp(-+2 pi i / P)
+// P-point DFT of v in registers: o_q = sum_r v_r w^(r q), w = exp(-+2 pi i / P);
+// wp[t] = w^t (loaded once per stage)
 template <class R, int P, bool INV>
-__device__ __forceinline__ void dft_p(const Cplx<R> (&v)[P], Cplx<R> (&o)[P], const Cplx<R>* __restrict__ tw,
-                                      int N) {
+__device__ __forceinline__ void dft_p(const Cplx<R> (&v)[P], Cplx<R> (&o)[P], const Cplx<R> (&wp)[P]) {
   if constexpr (P == 2) {
     o[0] = {v[0].re + v[1].re, v[0].im + v[1].im};
     o[1] = {v[0].re - v[1].re, v[0].im - v[1].im};
@@ -54,16 +54,12 @@ __device__ __forceinline__ void dft_p(const Cplx<R> (&v)[P], Cplx<R> (&o)[P], co
     o[1] = {a1.re + b1.re, a1.im + b1.im};
     o[3] = {a1.re - b1.re, a1.im - b1.im};
   } else {
-    Cplx<R> w[P];
-    const int q = N / P;
-#pragma unroll
-    for (int t = 0; t < P; ++t) w[t] = root<R, INV>(tw, t * q);
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       Cplx<R> s = v[0];
 #pragma unroll
       for (int r = 1; r < P; ++r) {
-        const Cplx<R> t = cmul(v[r], w[(r * k) % P]);
+        const Cplx<R> t = cmul(v[r], wp[(r * k) % P]);
         s.re += t.re;
         s.im += t.im;
       }
@@ -72,17 +68,34 @@ __device__ __forceinline__ void dft_p(const Cplx<R> (&v)[P], Cplx<R> (&o)[P], co
   }
 }
 
+// Twiddles of butterfly kk: w1 = exp(-+2 pi i kk / (Ns P)) from the table;
+// in FP32 its powers w1^r by repeated products (one table load per butterfly
+// instead of P - 1; the powers lose at most P - 2 roundings), in FP64 from
+// the table (FP64 products cost more than the loads on this GPU).
 template <class R, int P, bool INV>
 __device__ void stage(const Cplx<R>* __restrict__ x, Cplx<R>* __restrict__ y, int N, int Ns,
                       const Cplx<R>* __restrict__ tw) {
   const int nb = N / P, tstep = N / (Ns * P);
+  Cplx<R> wp[P];
+#pragma unroll
+  for (int t = 0; t < P; ++t) wp[t] = root<R, INV>(tw, t * (N / P));
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
     const int kk = j % Ns;
     Cplx<R> v[P], o[P];
     v[0] = x[j];
+    if constexpr (sizeof(R) == 4) {
+      const Cplx<R> w1 = root<R, INV>(tw, kk * tstep);
+      Cplx<R> w = w1;
 #pragma unroll
-    for (int r = 1; r < P; ++r) v[r] = cmul(x[j + r * nb], root<R, INV>(tw, r * kk * tstep));
-    dft_p<R, P, INV>(v, o, tw, N);
+      for (int r = 1; r < P; ++r) {
+        v[r] = cmul(x[j + r * nb], w);
+        if (r + 1 < P) w = cmul(w, w1);
+      }
+    } else {
+#pragma unroll
+      for (int r = 1; r < P; ++r) v[r] = cmul(x[j + r * nb], root<R, INV>(tw, r * kk * tstep));
+    }
+    dft_p<R, P, INV>(v, o, wp);
     const int base = (j / Ns) * Ns * P + kk;
 #pragma unroll
     for (int r = 0; r < P; ++r) y[base + r * Ns] = o[r];
