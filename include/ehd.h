@@ -102,9 +102,8 @@ typedef struct {
                        (k_m = 2 pi m / Nx, Nyquist mode dropped), formed by the
                        Poisson solve into a plane that the march form reads.
                        Needs the march form with 2 columns per lane and ring
-                       depth 2; refused in batches.  The run then holds two
-                       more arrays, [Ny][P] and [Ny][Mp] complex, beyond
-                       ehd_footprint. */
+                       depth 2; refused in batches.  The run then holds one
+                       more [Ny][P] array beyond ehd_footprint. */
 } ehd_options;
 
 /* Fill *opt with the defaults above. */

@@ -105,7 +105,6 @@ struct ehd_run {
   void* oddt = nullptr;  // its tables: complex R [NE] twiddles, R [NE] y symbol, R [Mh] x symbol
   int ex_spectral = 0;   // E_x from the x-spectrum of phi instead of central differences
   void* exs = nullptr;   // R [Ny][P] spectral E_x (ex_spectral only)
-  void* spec_dx = nullptr;  // complex R [Ny][Mp]: its half spectrum
   int nstrips = 1;
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -278,7 +277,6 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.fft_cta = r->fft_cta;
   a.y_solver = r->y_solver;
   a.ex = r->exs;
-  a.spec_dx = r->spec_dx;
   a.NE = r->NE;
   a.nfac = r->nfac;
   for (int k = 0; k < 16; ++k) a.fac[k] = r->fac[k];
@@ -563,7 +561,6 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   r->ex_spectral = o.ex_spectral;
   if (r->ex_spectral) {
     r->exs = run_alloc(r, (size_t)Ny * r->P * r->rsz);
-    r->spec_dx = run_alloc(r, (size_t)Ny * r->Mp * 2 * r->rsz);
   }
   r->rx_dn = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->rx_up = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
@@ -578,7 +575,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->rx_dn && r->rx_up && r->phibar &&
             r->Ebar && r->spec && r->spec0 &&
             r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part &&
-            (r->nfac <= 0 || r->oddt) && (!r->ex_spectral || (r->exs && r->spec_dx));
+            (r->nfac <= 0 || r->oddt) && (!r->ex_spectral || r->exs);
   if (!ok) {
     destroy_quiet(r);
     return fail(EHD_ENOMEM, "device allocation failed");

@@ -158,7 +158,6 @@ struct PoissonArgs {
   const void* symy;          // R [NE]: 4 sin^2(pi k / NE)
   const void* kap;           // R [Mh]: kappa_m, the x symbol of wavenumber m
   void* ex;                  // R [Ny][P]: spectral E_x written after phi, or nullptr
-  void* spec_dx;             // complex R [Ny][Mp]: -i k_m phi_m, its half spectrum
 };
 
 // Charge density of row y as the Poisson solve sees it: the step kernel's
@@ -262,6 +261,8 @@ bool fftw_supported(int Nx);
 cudaError_t fftw_set_tables();
 cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s);
 cudaError_t launch_irfft_warp(const PoissonArgs& a, cudaStream_t s);
+// The same transform of -i k_m phi_m (spectral E_x) into a.ex.
+cudaError_t launch_irfft_warp_dx(const PoissonArgs& a, cudaStream_t s);
 cudaError_t launch_fields(const FieldArgs& a, int storage, bool real_f64, unsigned mask, double* out,
                           cudaStream_t s);
 cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, double* part, int nblk,

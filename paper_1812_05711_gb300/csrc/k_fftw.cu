@@ -198,7 +198,22 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
 }
 
 // Inverse transform of row y by one warp -> phi minus its row mean.
-template <int E>
+// Coefficient k of the half spectrum as the inverse transforms read it: phi_k,
+// or with DX that of E_x = -d phi / dx, -i k_k phi_k with k_k = 2 pi k / N
+// (N = 2L; the Nyquist coefficient k = L is dropped so that E_x is real).
+template <bool DX>
+__device__ __forceinline__ float2 spec_in(const float2* spec, int k, int L) {
+  const float2 v = spec[k];
+  if constexpr (!DX) {
+    return v;
+  } else {
+    if (k == L) return make_float2(0.0f, 0.0f);
+    const float kk = (3.14159265358979323846f / (float)L) * (float)k;
+    return make_float2(kk * v.y, -kk * v.x);
+  }
+}
+
+template <int E, bool DX = false>
 __device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, float2* sm) {
   const int lane = threadIdx.x & 31;
   constexpr int L = 32 * E;
@@ -211,8 +226,8 @@ __device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, flo
 #pragma unroll
   for (int n2 = 0; n2 < E; ++n2) {
     const int k = lane + 32 * n2;
-    const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec[k];
-    const float2 sp = spec[L - k];
+    const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec_in<DX>(spec, k, L);
+    const float2 sp = spec_in<DX>(spec, L - k, L);
     const float2 sc = make_float2(sp.x, -sp.y);
     const float2 Ev = make_float2(0.5f * (sk.x + sc.x), 0.5f * (sk.y + sc.y));
     const float2 Dv = make_float2(0.5f * (sk.x - sc.x), 0.5f * (sk.y - sc.y));
@@ -224,7 +239,7 @@ __device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, flo
   float xr[32], xi[32];
   four_step<E>(re, im, xr, xi, tw, sm, lane);
   if (lane < E) {
-    float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(a.dphi) + (long long)y * a.P);
+    float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(DX ? a.ex : a.dphi) + (long long)y * a.P);
     const float inL = 1.0f / (float)L;
 #pragma unroll
     for (int k1 = 0; k1 < 32; ++k1) dphi2[lane + E * k1] = make_float2(xr[k1] * inL, -xi[k1] * inL);
@@ -460,7 +475,8 @@ __global__ void __launch_bounds__(kCtaT) k_rfft_cta(PoissonArgs a) {
   }
 }
 
-// Inverse transform of row y (N = 2048) -> phi minus its row mean.
+// Inverse transform of row y (N = 2048) -> phi minus its row mean (DX: E_x).
+template <bool DX = false>
 __global__ void __launch_bounds__(kCtaT) k_irfft_cta(PoissonArgs a) {
   __shared__ float2 sm[kSmemCta];
   grid_dep_wait();
@@ -474,8 +490,8 @@ __global__ void __launch_bounds__(kCtaT) k_irfft_cta(PoissonArgs a) {
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1) {
     const int k = t + 64 * n1;
-    const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec[k];
-    const float2 sp = spec[kCtaL - k];
+    const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec_in<DX>(spec, k, kCtaL);
+    const float2 sp = spec_in<DX>(spec, kCtaL - k, kCtaL);
     const float2 sc = make_float2(sp.x, -sp.y);
     const float2 Ev = make_float2(0.5f * (sk.x + sc.x), 0.5f * (sk.y + sc.y));
     const float2 Dv = make_float2(0.5f * (sk.x - sc.x), 0.5f * (sk.y - sc.y));
@@ -486,7 +502,7 @@ __global__ void __launch_bounds__(kCtaT) k_irfft_cta(PoissonArgs a) {
   }
   float zr[16], zi[16];
   cta_fft1024(re, im, zr, zi, tw, sm);
-  float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(a.dphi) + (long long)y * a.P);
+  float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(DX ? a.ex : a.dphi) + (long long)y * a.P);
   const float inL = 1.0f / (float)kCtaL;
   const int k1 = t >> 2, q = t & 3;
 #pragma unroll
@@ -506,14 +522,14 @@ __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
   if (y < a.Ny) rfft_warp_body<E>(a, y, smem[warp]);
 }
 
-template <int E>
+template <int E, bool DX = false>
 __global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
   __shared__ float2 smem[4][E * 33];
   grid_dep_wait();
   grid_dep_launch();
   const int warp = threadIdx.x >> 5;
   const int y = blockIdx.x * 4 + warp;
-  if (y < a.Ny) irfft_warp_body<E>(a, y, smem[warp]);
+  if (y < a.Ny) irfft_warp_body<E, DX>(a, y, smem[warp]);
 }
 
 // Batch: warps of a fixed grid take row items (run, y); the row length picks
@@ -579,20 +595,24 @@ cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_irfft_warp(const PoissonArgs& a, cudaStream_t s) {
+template <bool DX>
+cudaError_t irfft_warp_n(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
-    case 64: return launch_ex(a.pdl != 0, k_irfft_warp<1>, dim3(g), dim3(128), 0, s, a);
-    case 128: return launch_ex(a.pdl != 0, k_irfft_warp<2>, dim3(g), dim3(128), 0, s, a);
-    case 256: return launch_ex(a.pdl != 0, k_irfft_warp<4>, dim3(g), dim3(128), 0, s, a);
-    case 512: return launch_ex(a.pdl != 0, k_irfft_warp<8>, dim3(g), dim3(128), 0, s, a);
-    case 1024: return launch_ex(a.pdl != 0, k_irfft_warp<16>, dim3(g), dim3(128), 0, s, a);
+    case 64: return launch_ex(a.pdl != 0, k_irfft_warp<1, DX>, dim3(g), dim3(128), 0, s, a);
+    case 128: return launch_ex(a.pdl != 0, k_irfft_warp<2, DX>, dim3(g), dim3(128), 0, s, a);
+    case 256: return launch_ex(a.pdl != 0, k_irfft_warp<4, DX>, dim3(g), dim3(128), 0, s, a);
+    case 512: return launch_ex(a.pdl != 0, k_irfft_warp<8, DX>, dim3(g), dim3(128), 0, s, a);
+    case 1024: return launch_ex(a.pdl != 0, k_irfft_warp<16, DX>, dim3(g), dim3(128), 0, s, a);
     case 2048:
-      if (a.fft_cta) return launch_ex(a.pdl != 0, k_irfft_cta, dim3(a.Ny), dim3(kCtaT), 0, s, a);
-      return launch_ex(a.pdl != 0, k_irfft_warp<32>, dim3(g), dim3(128), 0, s, a);
+      if (a.fft_cta) return launch_ex(a.pdl != 0, k_irfft_cta<DX>, dim3(a.Ny), dim3(kCtaT), 0, s, a);
+      return launch_ex(a.pdl != 0, k_irfft_warp<32, DX>, dim3(g), dim3(128), 0, s, a);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
+
+cudaError_t launch_irfft_warp(const PoissonArgs& a, cudaStream_t s) { return irfft_warp_n<false>(a, s); }
+
+cudaError_t launch_irfft_warp_dx(const PoissonArgs& a, cudaStream_t s) { return irfft_warp_n<true>(a, s); }
 
 }  // namespace ehd

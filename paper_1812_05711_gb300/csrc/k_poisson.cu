@@ -264,7 +264,21 @@ __global__ void __launch_bounds__(256) k_rfft_rows(PoissonArgs a) {
 }
 
 // ------------------------------------------------------------ inverse FFT ---
-template <class R>
+// DX: the transform of E_x = -d phi / dx instead, coefficient k read as
+// -i k_k phi_k (k_k = 2 pi k / N, the Nyquist coefficient dropped), into a.ex
+template <class R, bool DX>
+__device__ __forceinline__ Cplx<R> spec_coef(const Cplx<R>* spec, int k, int L) {
+  const Cplx<R> v = spec[k];
+  if constexpr (!DX) {
+    return v;
+  } else {
+    if (k == L) return {R(0), R(0)};
+    const R kk = (R(3.141592653589793238462643383279502884) / (R)L) * (R)k;
+    return {kk * v.im, -kk * v.re};
+  }
+}
+
+template <class R, bool DX = false>
 __global__ void __launch_bounds__(256) k_irfft_rows(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = a.Nx, L = N >> 1;
@@ -286,8 +300,8 @@ __global__ void __launch_bounds__(256) k_irfft_rows(PoissonArgs a) {
   for (int k = tr; k < L; k += T) {
     Cplx<R> z = {R(0), R(0)};
     if (live) {
-      const Cplx<R> sk = (k == 0) ? Cplx<R>{R(0), R(0)} : spec[k];
-      const Cplx<R> sc = cconj(spec[L - k]);
+      const Cplx<R> sk = (k == 0) ? Cplx<R>{R(0), R(0)} : spec_coef<R, DX>(spec, k, L);
+      const Cplx<R> sc = cconj(spec_coef<R, DX>(spec, L - k, L));
       const Cplx<R> E = {R(0.5) * (sk.re + sc.re), R(0.5) * (sk.im + sc.im)};
       const Cplx<R> D = {R(0.5) * (sk.re - sc.re), R(0.5) * (sk.im - sc.im)};
       const Cplx<R> O = cmul(D, cconj(stw[k]));  // D / W^k
@@ -298,7 +312,7 @@ __global__ void __launch_bounds__(256) k_irfft_rows(PoissonArgs a) {
   __syncthreads();
   const Cplx<R>* zr = fft_rows<R>(A, B, L, T, tr, stw, true);
   if (live) {
-    R* dphi = static_cast<R*>(a.dphi) + (long long)y * a.P;
+    R* dphi = static_cast<R*>(DX ? a.ex : a.dphi) + (long long)y * a.P;
     const R inL = R(1) / (R)L;
     for (int n = tr; n < L; n += T) {
       const Cplx<R> v = zr[pidx(n)];
@@ -455,29 +469,6 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
     const int m = m0 + mo2;
     if (m >= 1 && m < Mh) spec[(long long)j * Mp + m] = d[idx];
   }
-}
-
-// Half spectrum of E_x = -d phi / dx from that of phi: -i k_m phi_m with
-// k_m = 2 pi m / Nx; m = 0 (the mean, carried apart) and the Nyquist
-// coefficient m = Nx / 2 are zero, so the inverse transform is real.
-template <class R>
-__global__ void k_spec_dx(PoissonArgs a) {
-  const Cplx<R>* __restrict__ spec = static_cast<const Cplx<R>*>(a.spec);
-  Cplx<R>* __restrict__ out = static_cast<Cplx<R>*>(a.spec_dx);
-  // k_1 = 2 pi / Nx exactly scaled (Nx a power of two), in the compute type:
-  // no FP64 arithmetic per element on the FP32 path
-  const R k1 = R(6.283185307179586476925286766559) / (R)a.Nx;
-  for (int y = blockIdx.x; y < a.Ny; y += gridDim.x)
-    for (int m = threadIdx.x; m < a.Mh; m += blockDim.x) {
-      const long long c = (long long)y * a.Mp + m;
-      if (m == 0 || 2 * m == a.Nx) {
-        out[c] = {R(0), R(0)};
-      } else {
-        const R k = k1 * (R)m;
-        const Cplx<R> v = spec[c];
-        out[c] = {k * v.im, -k * v.re};
-      }
-    }
 }
 
 // threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
@@ -829,16 +820,12 @@ cudaError_t poisson_t(const PoissonArgs& a, cudaStream_t s, cudaStream_t side, c
   }
   if (e != cudaSuccess) return e;
   if (a.ex) {
-    // spectral E_x: -i k_m phi_m, then the same inverse row transform
-    PoissonArgs b = a;
-    b.spec = a.spec_dx;
-    b.dphi = a.ex;
-    k_spec_dx<R><<<std::min(a.Ny, 4096), 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // spectral E_x: the inverse row transform of -i k_m phi_m, formed as it
+    // reads the solved spectrum
     if (warp_fft) {
-      e = launch_irfft_warp(b, s);
+      e = launch_irfft_warp_dx(a, s);
     } else {
-      k_irfft_rows<R><<<row_blocks<R>(b.Nx, b.Ny), 256, row_smem<R>(b.Nx), s>>>(b);
+      k_irfft_rows<R, true><<<row_blocks<R>(a.Nx, a.Ny), 256, row_smem<R>(a.Nx), s>>>(a);
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
@@ -866,6 +853,7 @@ cudaError_t set_attrs_t() {
   cudaError_t e;
   if ((e = allow_max_dynamic_smem(k_rfft_rows<R>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_irfft_rows<R>)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_irfft_rows<R, true>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreads>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreadsSmall>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8>)) != cudaSuccess) return e;
