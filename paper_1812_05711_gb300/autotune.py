@@ -70,9 +70,9 @@ def tune(batch, steps: int = 8, ticks: int = 4, use_cache: bool = True, verbose:
     base = {k: ehd_batch_tune_get(batch.handle, k) for k in BATCH_TUNE}
     auto_rows = base["slab_rows"]
     cands = []
-    for rows in sorted({max(4, auto_rows // 2), auto_rows, auto_rows * 2, 0}):
+    for rows in sorted({max(4, auto_rows // 2), auto_rows, auto_rows * 2, 8, 12, 16, 24, 0}):
         for mf in (0.5, 1.0, 2.0):
-            for rf in (0.5, 1.0):
+            for rf in (0.5, 1.0, 1.25):
                 cands.append({"slab_rows": rows, "march_ctas": max(1, int(base["march_ctas"] * mf)),
                               "row_ctas": max(1, int(base["row_ctas"] * rf)), "tile_ctas": base["tile_ctas"]})
     best, best_ms, t0 = None, float("inf"), time.perf_counter()

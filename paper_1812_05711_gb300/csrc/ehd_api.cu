@@ -125,6 +125,7 @@ struct ehd_batch {
   int2* d_rows = nullptr;
   int2* d_tiles = nullptr;
   int* d_counts = nullptr;
+  int* d_work = nullptr;  // [4] dynamic item counters of the step's phases
   BatchRunDesc* h_runs = nullptr;
   int4* h_march = nullptr;
   int2* h_rows = nullptr;
@@ -1051,6 +1052,7 @@ void batch_free(ehd_batch* b) {
   cudaFree(b->d_rows);
   cudaFree(b->d_tiles);
   cudaFree(b->d_counts);
+  cudaFree(b->d_work);
   cudaFreeHost(b->h_runs);
   cudaFreeHost(b->h_march);
   cudaFreeHost(b->h_rows);
@@ -1071,7 +1073,9 @@ BatchTables batch_tables(const ehd_batch* b) {
   t.row_items = b->d_rows;
   t.tile_items = b->d_tiles;
   t.counts = b->d_counts;
+  t.work = b->d_work;
   t.modes_smem = b->modes_smem;
+  t.emax = std::max(1, b->max_nx / 64);
   return t;
 }
 
@@ -1082,15 +1086,36 @@ void batch_build_items(ehd_batch* b, int resident_warps) {
   for (ehd_run* r : b->members) strip_rows += (long long)march_strips(r->Nx, 2) * r->Ny;
   long long rows = (strip_rows + resident_warps - 1) / std::max(1, resident_warps);
   b->slab_rows = b->slab_rows_fixed > 0 ? b->slab_rows_fixed : (int)std::max(4LL, rows);
+  // the phases take their items from a counter in list order: largest
+  // first (full slabs, then the partial top slabs by height; rows of the
+  // widest runs first; wavenumber tiles of the tallest runs first), so the
+  // last items taken are the short ones
+  const int S = b->slab_rows;
+  const size_t nmem = b->members.size();
   size_t nm = 0, nr = 0, nt = 0;
-  for (size_t i = 0; i < b->members.size(); ++i) {
+  for (size_t i = 0; i < nmem; ++i) {
     ehd_run* r = b->members[i];
-    const int ns = march_strips(r->Nx, 2), nsl = (r->Ny + b->slab_rows - 1) / b->slab_rows;
-    for (int sl = 0; sl < nsl; ++sl)
+    const int ns = march_strips(r->Nx, 2);
+    for (int sl = 0; sl < r->Ny / S; ++sl)
       for (int s = 0; s < ns; ++s) b->h_march[nm++] = make_int4((int)i, s, sl, 0);
-    for (int y = 0; y < r->Ny; ++y) b->h_rows[nr++] = make_int2((int)i, y);
-    for (int m0 = 0; m0 < r->Mh; m0 += kBatchTileModes) b->h_tiles[nt++] = make_int2((int)i, m0);
   }
+  for (int h = S - 1; h >= 1; --h)
+    for (size_t i = 0; i < nmem; ++i) {
+      ehd_run* r = b->members[i];
+      if (r->Ny % S != h) continue;
+      const int ns = march_strips(r->Nx, 2);
+      for (int s = 0; s < ns; ++s) b->h_march[nm++] = make_int4((int)i, s, r->Ny / S, 0);
+    }
+  std::vector<size_t> by_nx(nmem), by_ny(nmem);
+  for (size_t i = 0; i < nmem; ++i) by_nx[i] = by_ny[i] = i;
+  std::stable_sort(by_nx.begin(), by_nx.end(),
+                   [&](size_t p, size_t q) { return b->members[p]->Nx > b->members[q]->Nx; });
+  std::stable_sort(by_ny.begin(), by_ny.end(),
+                   [&](size_t p, size_t q) { return b->members[p]->Ny > b->members[q]->Ny; });
+  for (size_t i : by_nx)
+    for (int y = 0; y < b->members[i]->Ny; ++y) b->h_rows[nr++] = make_int2((int)i, y);
+  for (size_t i : by_ny)
+    for (int m0 = 0; m0 < b->members[i]->Mh; m0 += kBatchTileModes) b->h_tiles[nt++] = make_int2((int)i, m0);
   b->h_counts[0] = (int)b->members.size();
   b->h_counts[1] = (int)nm;
   b->h_counts[2] = (int)nr;
@@ -1103,7 +1128,8 @@ ehd_status batch_capture(ehd_batch* b, int K, cudaGraphExec_t* out) {
   EHD_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < K && e == cudaSuccess; ++s) {
-    e = launch_batch_march(t, s, b->grid_march, b->stream);
+    e = cudaMemsetAsync(b->d_work, 0, 4 * sizeof(int), b->stream);
+    if (e == cudaSuccess) e = launch_batch_march(t, s, b->grid_march, b->stream);
     if (e == cudaSuccess) e = launch_batch_rfft(t, s, b->grid_rows, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
@@ -1173,12 +1199,13 @@ ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream, 
   b->d_rows = devmem<int2>(b->cap_rows);
   b->d_tiles = devmem<int2>(b->cap_tiles);
   b->d_counts = devmem<int>(4);
+  b->d_work = devmem<int>(4);
   b->h_runs = pinned<BatchRunDesc>(max_runs);
   b->h_march = pinned<int4>(b->cap_march);
   b->h_rows = pinned<int2>(b->cap_rows);
   b->h_tiles = pinned<int2>(b->cap_tiles);
   b->h_counts = pinned<int>(4);
-  if (!b->d_runs || !b->d_march || !b->d_rows || !b->d_tiles || !b->d_counts || !b->h_runs || !b->h_march ||
+  if (!b->d_runs || !b->d_march || !b->d_rows || !b->d_tiles || !b->d_counts || !b->d_work || !b->h_runs || !b->h_march ||
       !b->h_rows || !b->h_tiles || !b->h_counts) {
     batch_free(b);
     return fail(EHD_ENOMEM, "batch table allocation failed");

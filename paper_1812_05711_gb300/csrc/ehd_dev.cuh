@@ -222,8 +222,19 @@ struct BatchTables {
   const int2* row_items;    // (run, row)
   const int2* tile_items;   // (run, first wavenumber)
   const int* counts;        // device: [0] runs, [1] march items, [2] rows, [3] tiles
+  int* work;                // device: items taken so far in this step's march, forward FFT,
+                            // wavenumber and inverse FFT phases (zeroed before each step)
   int modes_smem;           // tile bytes for the largest admissible Ny (fixed per batch)
+  int emax;                 // largest admissible Nx / 64: the widest warp-FFT shape compiled in
 };
+
+// Dynamic scheduling of a batch phase's items (largest first in the lists):
+// one lane or thread takes the next index from the phase's counter.
+__device__ __forceinline__ int next_item_warp(int* counter) {
+  int it = 0;
+  if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
 // one launch of each phase for step t (0-based) of a tick
 cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStream_t s);

@@ -534,13 +534,16 @@ __global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
 
 // Batch: warps of a fixed grid take row items (run, y); the row length picks
 // the transform shape.
-template <bool INV>
-__global__ void __launch_bounds__(128) k_batch_fft(BatchTables t, int step) {
-  __shared__ float2 smem[4][32 * 33];
+// EMAX: the widest row shape of the batch (Nx / 64); narrower batches get an
+// instance with less shared memory (and, for the inverse up to EMAX = 8, at
+// most 102 registers: five CTAs per SM), so more row FFTs run at once.
+template <bool INV, int EMAX>
+__device__ __forceinline__ void batch_fft_body(const BatchTables& t, int step) {
+  __shared__ float2 smem[4][EMAX * 33];
   const int warp = threadIdx.x >> 5;
-  const int nw = gridDim.x * 4;
   const int n = t.counts[2];
-  for (int it = blockIdx.x * 4 + warp; it < n; it += nw) {
+  int* counter = t.work + (INV ? 3 : 1);
+  for (int it = next_item_warp(counter); it < n; it = next_item_warp(counter)) {
     const int2 w = t.row_items[it];
     const BatchRunDesc& rd = t.runs[w.x];
     if (step >= rd.remaining) continue;
@@ -548,22 +551,61 @@ __global__ void __launch_bounds__(128) k_batch_fft(BatchTables t, int step) {
     float2* sm = smem[warp];
     switch (rd.E) {
       case 1: INV ? irfft_warp_body<1>(a, w.y, sm) : rfft_warp_body<1>(a, w.y, sm); break;
-      case 2: INV ? irfft_warp_body<2>(a, w.y, sm) : rfft_warp_body<2>(a, w.y, sm); break;
-      case 4: INV ? irfft_warp_body<4>(a, w.y, sm) : rfft_warp_body<4>(a, w.y, sm); break;
-      case 8: INV ? irfft_warp_body<8>(a, w.y, sm) : rfft_warp_body<8>(a, w.y, sm); break;
-      case 16: INV ? irfft_warp_body<16>(a, w.y, sm) : rfft_warp_body<16>(a, w.y, sm); break;
-      default: INV ? irfft_warp_body<32>(a, w.y, sm) : rfft_warp_body<32>(a, w.y, sm); break;
+      case 2:
+        if constexpr (EMAX >= 2) INV ? irfft_warp_body<2>(a, w.y, sm) : rfft_warp_body<2>(a, w.y, sm);
+        break;
+      case 4:
+        if constexpr (EMAX >= 4) INV ? irfft_warp_body<4>(a, w.y, sm) : rfft_warp_body<4>(a, w.y, sm);
+        break;
+      case 8:
+        if constexpr (EMAX >= 8) INV ? irfft_warp_body<8>(a, w.y, sm) : rfft_warp_body<8>(a, w.y, sm);
+        break;
+      case 16:
+        if constexpr (EMAX >= 16) INV ? irfft_warp_body<16>(a, w.y, sm) : rfft_warp_body<16>(a, w.y, sm);
+        break;
+      default:
+        if constexpr (EMAX >= 32) INV ? irfft_warp_body<32>(a, w.y, sm) : rfft_warp_body<32>(a, w.y, sm);
+        break;
     }
   }
 }
 
+template <int EMAX>
+__global__ void __launch_bounds__(128) k_batch_rfft(BatchTables t, int step) {
+  batch_fft_body<false, EMAX>(t, step);
+}
+
+template <int EMAX>
+__global__ void __launch_bounds__(128) k_batch_irfft(BatchTables t, int step) {
+  batch_fft_body<true, EMAX>(t, step);
+}
+
+template <int EMAX>
+__global__ void __launch_bounds__(128, 5) k_batch_irfft_narrow(BatchTables t, int step) {
+  batch_fft_body<true, EMAX>(t, step);
+}
+
 cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStream_t s) {
-  k_batch_fft<false><<<grid, 128, 0, s>>>(t, step);
+  switch (t.emax) {
+    case 1: k_batch_rfft<1><<<grid, 128, 0, s>>>(t, step); break;
+    case 2: k_batch_rfft<2><<<grid, 128, 0, s>>>(t, step); break;
+    case 4: k_batch_rfft<4><<<grid, 128, 0, s>>>(t, step); break;
+    case 8: k_batch_rfft<8><<<grid, 128, 0, s>>>(t, step); break;
+    case 16: k_batch_rfft<16><<<grid, 128, 0, s>>>(t, step); break;
+    default: k_batch_rfft<32><<<grid, 128, 0, s>>>(t, step); break;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStream_t s) {
-  k_batch_fft<true><<<grid, 128, 0, s>>>(t, step);
+  switch (t.emax) {
+    case 1: k_batch_irfft_narrow<1><<<grid, 128, 0, s>>>(t, step); break;
+    case 2: k_batch_irfft_narrow<2><<<grid, 128, 0, s>>>(t, step); break;
+    case 4: k_batch_irfft_narrow<4><<<grid, 128, 0, s>>>(t, step); break;
+    case 8: k_batch_irfft_narrow<8><<<grid, 128, 0, s>>>(t, step); break;
+    case 16: k_batch_irfft<16><<<grid, 128, 0, s>>>(t, step); break;
+    default: k_batch_irfft<32><<<grid, 128, 0, s>>>(t, step); break;
+  }
   return cudaGetLastError();
 }
 

@@ -860,17 +860,17 @@ __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
       march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<S, R, NSTAGE, SPECX>::kBytesPerWarp);
 }
 
-// Batch: every warp of a fixed grid takes march items (run, strip, slab) in
-// turn; runs whose budget in the tick is used up are skipped.  Bounded to
-// three CTAs per SM (168 registers, a few bytes spilled): at 180 registers
-// only two fit and the batch step takes 320 instead of 280 us.
+// Batch: every warp of a fixed grid takes march items (run, strip, slab),
+// full slabs first, from the step's counter until none is left; runs whose
+// budget in the tick is used up are skipped.  Bounded to three CTAs per SM
+// (168 registers, a few bytes spilled): at 180 registers only two fit and
+// the batch step takes 320 instead of 280 us.
 __global__ void __launch_bounds__(128, 3) k_batch_march(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char march_smem[];
   constexpr int NST = 2;
   unsigned char* ring = march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<float, float, NST>::kBytesPerWarp;
-  const int nw = gridDim.x * 4;
   const int n = t.counts[1];
-  for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < n; it += nw) {
+  for (int it = next_item_warp(t.work); it < n; it = next_item_warp(t.work)) {
     const int4 w = t.march_items[it];
     const BatchRunDesc& rd = t.runs[w.x];
     if (step >= rd.remaining) continue;  // whole warp

@@ -711,8 +711,15 @@ __global__ void __launch_bounds__(NT) k_mean_mode(PoissonArgs a) {
 __global__ void __launch_bounds__(kTileThreads) k_batch_modes(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileScratch<float, kBatchTileModes, kTileThreads> ts;
+  __shared__ int s_it;
   const int n = t.counts[3];
-  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+  for (;;) {
+    // the CTA takes the next tile (tallest runs first) from the step's counter
+    if (threadIdx.x == 0) s_it = atomicAdd(t.work + 2, 1);
+    __syncthreads();
+    const int it = s_it;
+    __syncthreads();
+    if (it >= n) break;
     const int2 w = t.tile_items[it];
     const BatchRunDesc& rd = t.runs[w.x];
     if (step >= rd.remaining) continue;  // whole CTA
