@@ -123,9 +123,15 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
   const float2* rc2 = reinterpret_cast<const float2*>(static_cast<const float*>(a.rhoc) + (long long)y * a.P);
   const float *rdn, *rup;
   rhoc_partials<float>(a, y, rdn, rup);
-  const float ieps = (float)a.inv_eps;
+  const float nieps = -(float)a.inv_eps;
+  // A row constant c0 is taken out before the transform (the differences are
+  // exact and small, so the rounding scales with the row's variation); only
+  // the m = 0 bin depends on it, and it is restored there in float-float.
+  const float* row = reinterpret_cast<const float*>(rc2);
+  float c0 = row[0];
+  if (rdn) c0 += rdn[0];
+  if (rup) c0 += rup[0];
   float re[E], im[E];
-  float shi = 0.0f, slo = 0.0f;
 #pragma unroll
   for (int n2 = 0; n2 < E; ++n2) {
     float2 v = rc2[lane + 32 * n2];
@@ -139,36 +145,25 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
       v.x += u.x;
       v.y += u.y;
     }
-    re[n2] = -v.x * ieps;
-    im[n2] = -v.y * ieps;
-    float s, e;
-    two_sum_f(shi, re[n2], s, e);
-    slo += e;
-    two_sum_f(s, im[n2], shi, e);
-    slo += e;
-  }
-  // row sum over the warp (float-float): the m = 0 DFT coefficient
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, shi, o), l2 = __shfl_xor_sync(0xffffffffu, slo, o);
-    float s, e;
-    two_sum_f(shi, h2, s, e);
-    shi = s;
-    slo = slo + l2 + e;
-  }
-  {
-    float h, l;
-    two_sum_f(shi, slo, h, l);
-    if (lane == 0) static_cast<float2*>(a.spec0)[y] = make_float2(h, l);
-    const float mean = h / (float)N;
-#pragma unroll
-    for (int n2 = 0; n2 < E; ++n2) {
-      re[n2] -= mean;
-      im[n2] -= mean;
-    }
+    re[n2] = (v.x - c0) * nieps;
+    im[n2] = (v.y - c0) * nieps;
   }
   float xr[32], xi[32];
   four_step<E>(re, im, xr, xi, tw, sm, lane);
+  if (lane == 0) {
+    // m = 0 coefficient (Z0 sits in lane 0, k1 = 0), float-float:
+    // (Re Z0 + Im Z0) + N c0 (-1/eps), the product exact by the FMA
+    // two-product, N a power of two
+    float s, e;
+    two_sum_f(xr[0], xi[0], s, e);
+    const float p = c0 * nieps, pe = fmaf(c0, nieps, -p);
+    const float P = p * (float)N, PE = pe * (float)N;
+    float h, l;
+    two_sum_f(s, P, h, l);
+    l += e + PE;
+    two_sum_f(h, l, s, e);
+    static_cast<float2*>(a.spec0)[y] = make_float2(s, e);
+  }
   // untangle into the half spectrum: S[k] = E_k + W_N^k O_k,
   // E_k = (Z[k] + Z*[L-k]) / 2, O_k = (Z[k] - Z*[L-k]) / (2i); lane k2 holds
   // k = k2 + E k1, whose partner L - k sits in lane (E - k2) mod E at 31 - k1
@@ -197,7 +192,6 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
   if (lane == 0) spec[L] = make_float2(xr[0] - xi[0], 0.0f);  // Nyquist: Re Z0 - Im Z0
 }
 
-// Inverse transform of row y by one warp -> phi minus its row mean.
 // Coefficient k of the half spectrum as the inverse transforms read it: phi_k,
 // or with DX that of E_x = -d phi / dx, -i k_k phi_k with k_k = 2 pi k / N
 // (N = 2L; the Nyquist coefficient k = L is dropped so that E_x is real).
@@ -213,6 +207,7 @@ __device__ __forceinline__ float2 spec_in(const float2* spec, int k, int L) {
   }
 }
 
+// Inverse transform of row y by one warp -> phi minus its row mean (DX: E_x).
 template <int E, bool DX = false>
 __device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, float2* sm) {
   const int lane = threadIdx.x & 31;
