@@ -90,9 +90,14 @@ typedef struct {
                        creates and owns */
   int step_kernel;  /* 0: march form -- a warp walks a slab of rows, pulls the
                        populations through registers and writes the new
-                       charge density itself (default); 1: one thread per
-                       node, push form, charge density summed by a separate
-                       kernel.  Same results up to rounding order. */
+                       charge density itself; 1: one thread per node, push
+                       form, charge density summed by a separate kernel.
+                       Same results up to rounding order.  -1 (default):
+                       the march form, except plain FP64 runs (FP64 compute)
+                       without spectral E_x, which take the push form: there
+                       the FP64 arithmetic of a warp's row walk is latency
+                       bound and one thread per node is faster at every size
+                       (128x104: 52 vs 112 us per step). */
   int x_symbol;     /* x second derivative of the Poisson solve: 0 spectral,
                        -(2 pi m / Nx)^2 (Eq. 20, default); 1 the 3-point
                        difference -4 sin^2(pi m / Nx), so that the solve

@@ -267,7 +267,7 @@ def ehd_last_error() -> str:
 
 # ------------------------------------------------------------ convenience
 def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
-                 amp=(), phase=(), stream=None, step_kernel=0, x_symbol=0, ex_spectral=0) -> Options:
+                 amp=(), phase=(), stream=None, step_kernel=-1, x_symbol=0, ex_spectral=0) -> Options:
     o = ehd_default_options()
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if compute is None:
@@ -299,7 +299,7 @@ class Run:
     """
 
     def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
-                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=0,
+                 u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=-1,
                  x_symbol=0, ex_spectral=0):
         self.Nx, self.Ny = int(Nx), int(Ny)
         self._stream_obj = None

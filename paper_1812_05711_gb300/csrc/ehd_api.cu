@@ -392,6 +392,7 @@ extern "C" {
 void ehd_default_options(ehd_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
+  o->step_kernel = -1;
   o->storage = EHD_STORE_F32;
   o->compute = EHD_COMPUTE_F32;
   o->lambda_g = 1e-6;
@@ -461,9 +462,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   if (o.wall_mode != 0 && o.wall_mode != 1) return fail(EHD_EINVAL, "wall_mode must be 0 or 1");
   if (o.x_symbol != 0 && o.x_symbol != 1) return fail(EHD_EINVAL, "x_symbol must be 0 or 1");
   if (o.ex_spectral != 0 && o.ex_spectral != 1) return fail(EHD_EINVAL, "ex_spectral must be 0 or 1");
-  if (o.ex_spectral && o.step_kernel != 0) return fail(EHD_EINVAL, "spectral E_x needs the march form");
+  if (o.ex_spectral && o.step_kernel == 1) return fail(EHD_EINVAL, "spectral E_x needs the march form");
   if (o.n_modes < 0 || o.n_modes > EHD_MAX_PERT_MODES) return fail(EHD_EINVAL, "n_modes out of range");
-  if (o.step_kernel != 0 && o.step_kernel != 1) return fail(EHD_EINVAL, "step_kernel must be 0 or 1");
+  if (o.step_kernel < -1 || o.step_kernel > 1) return fail(EHD_EINVAL, "step_kernel must be -1, 0 or 1");
 
   ehd_run* r = new ehd_run();
   {
@@ -565,7 +566,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   }
   r->rx_dn = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->rx_up = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
-  r->step_kernel = o.step_kernel;
+  r->step_kernel = (o.step_kernel >= 0) ? o.step_kernel : (r->real_f64 && !o.ex_spectral) ? 1 : 0;
   r->cols_per_lane = 2;
   r->nstrips = march_strips(Nx, r->cols_per_lane);
   r->nxb = (r->step_kernel == 0) ? r->nstrips : step_flux_blocks(Nx);

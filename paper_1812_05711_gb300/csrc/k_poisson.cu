@@ -648,8 +648,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
     if constexpr (sizeof(R) == 8) {
       v[j] = static_cast<const double*>(a.spec0)[j];
     } else {
-      const float2 sv = static_cast<const float2*>(a.spec0)[j];
-      v[j] = {sv.x, sv.y};
+      v[j] = {static_cast<const float2*>(a.spec0)[j].x, static_cast<const float2*>(a.spec0)[j].y};
     }
   }
   sub_sync<NT>();

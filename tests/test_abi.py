@@ -71,3 +71,4 @@ def test_footprint_scales_with_storage():
 def test_default_options():
     o = ehd.ehd_default_options()
     assert o.storage == 1 and o.compute == 1 and o.lambda_g == 1e-6 and o.u_ion == 2e-3
+    assert o.step_kernel == -1  # chosen per run: push form for plain FP64, march form otherwise

@@ -274,6 +274,19 @@ def test_march_and_node_parallel_forms_agree(storage, tol):
 
 
 @gpu
+def test_default_step_form():
+    """Unless asked, plain FP64 runs take the node-parallel push form (their
+    FP64 row walk is latency bound) and every other run the march form."""
+    ehd = _ehd()
+    cases = ((dict(storage="f64"), 1), (dict(storage="f32"), 0), (dict(storage="f64", compute="f32"), 0),
+             (dict(storage="f64", ex_spectral=1), 0), (dict(storage="f64", step_kernel=0), 0))
+    for kw, form in cases:
+        r = ehd.Run(32, 26, 200.0, 10, 10, 4000, 0.25, **kw)
+        assert ehd.ehd_tune_get(r.handle, "step_kernel") == form, kw
+        r.close()
+
+
+@gpu
 @pytest.mark.parametrize("slab", [4, 5, 17, 51, 52])
 def test_slab_heights_fp64_parity(slab):
     """The march form walks slabs of rows and pushes the populations that
@@ -282,6 +295,7 @@ def test_slab_heights_fp64_parity(slab):
     the collector (51 of 52 rows), gives the oracle's state."""
     w = wl.small_channel(64, seed=29)
     ehd, p, s, run = _pair(w, u_ion=5e-3)
+    ehd.ehd_tune(run.handle, "step_kernel", 0)  # plain FP64 defaults to the push form
     ehd.ehd_tune(run.handle, "slab_rows", slab)
     run.step(120)
     o.step(s, 120)
