@@ -752,6 +752,8 @@ namespace {
 constexpr size_t kSmemCap = 200 * 1024;
 
 // wavenumbers per CTA: the spectrum and pivot tiles of all rows must fit
+// (8, as the batch's wavenumber tiles, so that a run gives the same bits
+// alone and in a batch: the tile width sets the scans' chunking)
 int tile_modes(int Ny, size_t cbytes, size_t rbytes) {
   int mb = 8;
   while (mb > 1 && (size_t)Ny * mb * (cbytes + rbytes) > kSmemCap) mb >>= 1;
