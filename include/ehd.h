@@ -272,8 +272,10 @@ void ehd_destroy(ehd_run* run);
  * are the single-run ones, applied per run). */
 
 /* Create a batch for up to max_runs runs (max_nx a power of two in
- * [64, 2048], max_ny in [2, 4096]); stream = cudaStream_t or NULL for an own
- * stream.  EHD_EINVAL / EHD_ENOMEM / EHD_ECUDA. */
+ * [64, 2048], max_ny in [2, 4096] and small enough that max_ny rows of 8
+ * wavenumbers fit one CTA's shared memory beside 16 KB: 2250 rows on a GPU
+ * with 227 KB); stream = cudaStream_t or NULL for an own stream.
+ * EHD_EINVAL / EHD_ENOMEM / EHD_ECUDA. */
 ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream,
                             ehd_batch** out);
 

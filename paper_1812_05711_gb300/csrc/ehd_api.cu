@@ -1175,6 +1175,17 @@ ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream, 
   b->max_nx = max_nx;
   b->max_ny = max_ny;
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  {
+    // the batch's wavenumber tiles hold max_ny rows of 8 wavenumbers (12 B
+    // each) in shared memory, beside about 16 KB of fixed scratch
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    const int rows_cap = (optin - 16384) / (kBatchTileModes * (int)(sizeof(float2) + sizeof(float)));
+    if (max_ny > rows_cap) {
+      delete b;
+      return fail(EHD_EINVAL, "max_ny %d exceeds the %d rows a batch's wavenumber tile holds", max_ny, rows_cap);
+    }
+  }
   if (stream) {
     b->stream = static_cast<cudaStream_t>(stream);
   } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {

@@ -88,3 +88,14 @@ def test_batch_membership_changes_between_ticks():
         assert np.array_equal(alone.save()[1], r.save()[1]), w.name
     batch.close()
     r1.step(2)                  # an ordinary run again
+
+
+@gpu
+def test_batch_row_limit_is_checked_at_creation():
+    """A batch whose wavenumber tiles (max_ny rows of 8 wavenumbers) would not
+    fit in shared memory is refused when it is created, not at its first tick."""
+    ehd = _ehd()
+    with pytest.raises(RuntimeError):
+        ehd.Batch(2, max_nx=64, max_ny=4096)
+    b = ehd.Batch(2, max_nx=64, max_ny=2048)
+    b.close()
