@@ -14,7 +14,7 @@
  *   - Work is enqueued on the run's CUDA stream and is asynchronous unless the
  *     comment says the call synchronises.  A run is not thread-safe; distinct
  *     runs may be driven from distinct host threads.
- *   - Grids: Nx columns (periodic in x, a power of two, 16..4096), Ny node rows
+ *   - Grids: Nx columns (periodic in x, a power of two, 16..2048), Ny node rows
  *     (2..8192).  Node row j sits at y = j + 1/2; the injector electrode
  *     (phi = 1, rho_c = rho0) is the wall y = 0 and the collector (phi = 0) the
  *     wall y = H = Ny.  Host field arrays are FP64, row-major, x fastest:

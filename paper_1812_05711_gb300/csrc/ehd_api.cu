@@ -415,7 +415,7 @@ ehd_status ehd_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void
 
 ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
   if (!bytes) return fail(EHD_EINVAL, "bytes is NULL");
-  if (Nx < 16 || Nx > 4096 || (Nx & (Nx - 1)) || Ny < 2 || Ny > 8192 || storage < 0 || storage > 3)
+  if (Nx < 16 || Nx > 2048 || (Nx & (Nx - 1)) || Ny < 2 || Ny > 8192 || storage < 0 || storage > 3)
     return fail(EHD_EINVAL, "unsupported size or storage");
   const size_t P = (size_t)((Nx + 31) / 32 * 32), Mp = ((size_t)Nx / 2 + 1 + 3) / 4 * 4;
   const size_t rs = (storage == 0) ? 8 : 4;  // worst case for the compute type
@@ -449,8 +449,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   ehd_options o;
   ehd_default_options(&o);
   if (opt) o = *opt;
-  if (Nx < 16 || Nx > 4096 || (Nx & (Nx - 1)))
-    return fail(EHD_EINVAL, "Nx must be a power of two in [16, 4096] (got %d)", Nx);
+  // the row transforms hold a row in one CTA (at most 2048 points)
+  if (Nx < 16 || Nx > 2048 || (Nx & (Nx - 1)))
+    return fail(EHD_EINVAL, "Nx must be a power of two in [16, 2048] (got %d)", Nx);
   if (Ny < 2 || Ny > 8192) return fail(EHD_EINVAL, "Ny must be in [2, 8192] (got %d)", Ny);
   if (!(T > 0) || !(C > 0) || !(M > 0) || !(Fe > 0) || !(Lambda > 0))
     return fail(EHD_EINVAL, "T, C, M, Fe and Lambda must be positive");

@@ -55,6 +55,9 @@ def test_create_rejects_bad_options():
     with pytest.raises(ehd.EhdError) as ei:
         ehd.ehd_create(128, 104, 200, 10, 10, 4000, 0.25, o)
     assert "x_symbol" in str(ei.value)
+    with pytest.raises(ehd.EhdError) as ei:
+        ehd.ehd_create(4096, 104, 200, 10, 10, 4000, 0.25, ehd.ehd_default_options())
+    assert "2048" in str(ei.value)
 
 
 def test_footprint_scales_with_storage():
@@ -66,6 +69,8 @@ def test_footprint_scales_with_storage():
     assert b32 >= 4 * 9 * 2048 * 1680 * 4
     with pytest.raises(ehd.EhdError):
         ehd.ehd_footprint(100, 10, 1)
+    with pytest.raises(RuntimeError):  # rows are transformed within one CTA: at most 2048 points
+        ehd.ehd_footprint(4096, 10, 1)
 
 
 def test_default_options():
