@@ -12,8 +12,7 @@
  * Everything is double precision, one thread, loops in the order the paper
  * states the method.  Each function names the passage it follows.
  *
- * Readings of the paper where it is silent or inconsistent (each also listed
- * in the design doc):
+ * Readings of the paper where it is silent or inconsistent:
  *   - walls halfway between node rows: node row j sits at y = j + 1/2, the
  *     injector (phi = phi0, rho_c = rho0) at y = 0 and the collector (phi = 0)
  *     at y = H = Ny.  The Poisson closure mirrors about the wall
@@ -28,7 +27,8 @@
  *     anti-bounce-back, collector = zero-normal-gradient outflow; f bounces
  *     back at both walls.
  *   - E = -grad phi by second-order central differences, using the same wall
- *     ghosts as the Poisson closure.
+ *     ghosts as the Poisson closure (ex_spectral = 1: E_x as the derivative
+ *     of the row's trigonometric interpolant instead).
  *   - lattice scaling of (T, C, M, Fe): rho = 1, dphi0 = 1, H = Ny and a free
  *     ion drift speed u_ion = mu_b dphi0 / H.
  *   - order inside one step: E(t) from phi(t); moments; Eq. 7 velocity with
