@@ -243,16 +243,23 @@ void* ehd_stream(ehd_run* run);
  *   stream  cudaStream_t to enqueue on (NULL = the legacy default stream).
  * Every intermediate (half spectrum, Thomas pivots, twiddles, FP64 mean
  * profile) lives in one fixed 8 MiB __device__ array inside the library;
- * every GPU that loads the library holds it until the process exits.  Sizes
- * whose intermediates do not fit (beyond about 1024 x 840 nodes; Nx a power
- * of two up to 2048, Ny up to 4096) return EHD_EINVAL with a message, as do
- * NULL pointers and eps <= 0.  The first call on a device, with that device
- * current, looks up the array's device address and builds the tables for
- * the sizes given; make that first call before any stream capture.  Later
- * calls rebuild the tables only when Nx, Ny or wall_mode change.  All calls
- * share the one array and it keeps the last call's contents (each call
- * writes everything it reads, so nothing needs clearing): calls that
- * overlap on the GPU, e.g. on two streams, race.  Asynchronous. */
+ * every GPU that loads the library holds it until the process exits.  With
+ * CUDA's default lazy module loading the array is placed on a device when
+ * the library's code is first used there, at the latest by the first call of
+ * this function: make that first call on each device before a pool reserves
+ * the rest of that device's memory.  Sizes whose intermediates do not fit
+ * (beyond about 1024 x 840 nodes; Nx a power of two up to 2048, Ny up to
+ * 4096) return EHD_EINVAL with a message, as do NULL pointers and eps <= 0.
+ * Every call looks up the array's device address with the calling device
+ * current.  The first call on a device builds the twiddle and pivot tables
+ * for the sizes given; make that first call before any stream capture.
+ * Later calls rebuild the tables only when Nx, Ny or wall_mode change,
+ * except that a call made while its stream is being captured always
+ * enqueues the rebuild, and after one such call every later call on that
+ * device rebuilds them too.  All calls share the one array and it keeps the
+ * last call's contents (each call writes everything it reads, so nothing
+ * needs clearing): calls that overlap on the GPU, e.g. on two streams, race.
+ * Asynchronous. */
 ehd_status ehd_poisson_noalloc(int Nx, int Ny, double eps, double phi0,
                                int wall_mode, const float* rhoc, float* phi,
                                void* stream);
@@ -271,20 +278,36 @@ void ehd_destroy(ehd_run* run);
  * Ny <= max_ny.  Each member's result is the one it gets alone (the kernels
  * are the single-run ones, applied per run). */
 
-/* Create a batch for up to max_runs runs (max_nx a power of two in
- * [64, 2048], max_ny in [2, 4096] and small enough that max_ny rows of 8
- * wavenumbers fit one CTA's shared memory beside 16 KB: 2250 rows on a GPU
- * with 227 KB); stream = cudaStream_t or NULL for an own stream.
+/* Create a batch for up to max_runs runs whose device state together holds
+ * at most hbm_budget bytes (the sum of the members' ehd_footprint; 0 = no
+ * limit), with max_nx a power of two in [64, 2048] and max_ny in [2, 4096]
+ * small enough that max_ny rows of 8 wavenumbers fit one CTA's shared memory
+ * beside 16 KB (2250 rows on a GPU with 227 KB); stream = cudaStream_t or
+ * NULL for an own stream.  The batch's own work lists (a few MB for
+ * thousands of runs) are not counted in hbm_budget.
  * EHD_EINVAL / EHD_ENOMEM / EHD_ECUDA. */
-ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream,
-                            ehd_batch** out);
+ehd_status ehd_batch_create(int max_runs, size_t hbm_budget, int max_nx,
+                            int max_ny, void* stream, ehd_batch** out);
 
 /* Add a run with a budget of `steps` further steps.  Synchronises the run's
- * own stream.  EHD_EBUSY if the batch is full; EHD_EINVAL for a run of the
- * wrong kind or size, or one that is already in a batch.  While a member, the
- * run is advanced only by ehd_batch_tick (ehd_step returns EHD_EBUSY); its
- * fields, diagnostics and checkpoints stay readable. */
+ * own stream.  EHD_EBUSY if the batch is full or the run's footprint does not
+ * fit what is left of the HBM budget; EHD_EINVAL for a run of the wrong kind
+ * or size, or one that is already in a batch.  While a member, the run is
+ * advanced only by ehd_batch_tick (ehd_step returns EHD_EBUSY); its fields,
+ * diagnostics and checkpoints stay readable. */
 ehd_status ehd_batch_add(ehd_batch* batch, ehd_run* run, long steps);
+
+/* Admission query for a run not yet created (a server's check before it
+ * allocates one): EHD_OK if a run of Nx x Ny nodes and this storage would be
+ * admitted now, EHD_EBUSY if it would have to wait for a slot or for memory
+ * held by members, EHD_EINVAL if it can never be admitted (outside the
+ * batch's size limits or the storage it takes, or a footprint above the
+ * whole HBM budget).  Changes nothing. */
+ehd_status ehd_batch_admits(ehd_batch* batch, int Nx, int Ny, int storage);
+
+/* Bytes the members' device state holds (sum of their ehd_footprint) and the
+ * batch's HBM budget (0 = no limit); either pointer (host) may be NULL. */
+ehd_status ehd_batch_memory(ehd_batch* batch, size_t* used, size_t* budget);
 
 /* Remove a run (synchronises the batch stream).  EHD_EINVAL if not a member. */
 ehd_status ehd_batch_remove(ehd_batch* batch, ehd_run* run);

@@ -32,8 +32,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ehd_oracle.c")
 _HDR = os.path.join(_HERE, "ehd_oracle.h")
 _LIB = os.path.join(_HERE, "libehd_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libehd_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 NDIAG = 6  # mass, charge, q_in, q_out, kinetic energy, max|u_y|
 FIELDS = ("rho", "ux", "uy", "rho_c", "phi", "Ex", "Ey")
@@ -66,17 +68,58 @@ class Params(ctypes.Structure):
                        else getattr(self, name)) for name, _ in self._fields_}
 
 
+def _compile(out: str, extra, force: bool) -> str:
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", *extra,
+             "-shared", "-o", tmp, _SRC, "-lm"], cwd=_HERE)
+        os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile ehd_oracle.c into libehd_oracle.so next to it (gcc, -O2)."""
+    """Compile ehd_oracle.c into libehd_oracle.so next to it (gcc, -O2), and
+    the same source with -fopenmp into libehd_oracle_omp.so (used only to
+    time the oracle on all host cores; if the compiler has no OpenMP, that
+    build is skipped)."""
     with _lock:
-        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
-            tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(
-                ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
-                 "-shared", "-o", tmp, _SRC, "-lm"], cwd=_HERE)
-            os.replace(tmp, _LIB)
+        _compile(_LIB, [], force)
+        try:
+            _compile(_LIB_OMP, ["-fopenmp"], force)
+        except (subprocess.CalledProcessError, OSError):
+            pass
     return _LIB
+
+
+def use_threads(n: int | None = None) -> int:
+    """Switch this process's oracle calls to the -fopenmp build with n
+    threads (all host cores when None).  Rows, wavenumbers and nodes are
+    shared among threads; the states it computes are bitwise those of the
+    one-thread build (only the diagnostic sums are reordered).  Returns the
+    thread count, or 0 if no OpenMP build is available.  For timing only."""
+    global _lib, _lib_omp
+    build()
+    if not os.path.exists(_LIB_OMP):
+        return 0
+    with _lock:
+        if _lib_omp is None:
+            _lib_omp = ctypes.CDLL(_LIB_OMP)
+        L = _lib_omp
+    _declare(L)
+    L.orc_threads.argtypes = [ctypes.c_int]
+    L.orc_threads.restype = ctypes.c_int
+    got = L.orc_threads(int(n) if n else (os.cpu_count() or 1))
+    _lib = L
+    return got
+
+
+def use_one_thread():
+    """Back to the one-thread build."""
+    global _lib
+    _lib = None
+    lib()
 
 
 def lib():
@@ -84,30 +127,35 @@ def lib():
     if _lib is None:
         build()
         L = ctypes.CDLL(_LIB)
-        dp = ctypes.POINTER(ctypes.c_double)
-        ip = ctypes.POINTER(ctypes.c_int)
-        pp = ctypes.POINTER(Params)
-        L.orc_setup.argtypes = [pp]
-        L.orc_setup.restype = ctypes.c_int
-        L.orc_lattice.argtypes = [ip, ip, dp, ip]
-        L.orc_hydrostatic_params.argtypes = [ctypes.c_double] * 4 + [dp, dp]
-        L.orc_hydrostatic_params.restype = ctypes.c_int
-        L.orc_dft.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
-        L.orc_fft.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int]
-        L.orc_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
-        L.orc_poisson_general.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_double, ctypes.c_double, dp, dp]
-        L.orc_poisson_oddext.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_double, ctypes.c_double, dp, dp]
-        L.orc_poisson.argtypes = [pp, dp, dp]
-        L.orc_efield.argtypes = [pp, dp, dp, dp]
-        L.orc_perturbation.argtypes = [pp, ctypes.c_int, dp, dp, ctypes.c_double,
-                                       ctypes.c_double, dp, dp]
-        L.orc_init.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
-        L.orc_fields.argtypes = [pp, dp, dp, dp, dp]
-        L.orc_step.argtypes = [pp, dp, dp, dp, ctypes.c_long, dp]
+        _declare(L)
         _lib = L
     return _lib
+
+
+def _declare(L):
+    """ctypes signatures of the oracle library L."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(Params)
+    L.orc_setup.argtypes = [pp]
+    L.orc_setup.restype = ctypes.c_int
+    L.orc_lattice.argtypes = [ip, ip, dp, ip]
+    L.orc_hydrostatic_params.argtypes = [ctypes.c_double] * 4 + [dp, dp]
+    L.orc_hydrostatic_params.restype = ctypes.c_int
+    L.orc_dft.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
+    L.orc_fft.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int]
+    L.orc_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
+    L.orc_poisson_general.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, dp, dp]
+    L.orc_poisson_oddext.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, dp, dp]
+    L.orc_poisson.argtypes = [pp, dp, dp]
+    L.orc_efield.argtypes = [pp, dp, dp, dp]
+    L.orc_perturbation.argtypes = [pp, ctypes.c_int, dp, dp, ctypes.c_double,
+                                   ctypes.c_double, dp, dp]
+    L.orc_init.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
+    L.orc_fields.argtypes = [pp, dp, dp, dp, dp]
+    L.orc_step.argtypes = [pp, dp, dp, dp, ctypes.c_long, dp]
 
 
 def _dp(a: np.ndarray):

@@ -52,6 +52,22 @@ static const int OOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static const double CS2 = 1.0 / 3.0;
 static const double OPI = 3.14159265358979323846264338327950288;
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the -fopenmp timing build (returns the count in use; the
+ * one-thread build ignores the request and returns 1). */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 void orc_lattice(int* cx, int* cy, double* w, int* opp) {
   for (int i = 0; i < 9; ++i) {
     cx[i] = OCX[i];
@@ -231,6 +247,14 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
   size_t nc = (size_t)Nx * Ny;
   double* sre = (double*)malloc(sizeof(double) * nc); /* [m][y] */
   double* sim = (double*)malloc(sizeof(double) * nc);
+  double wall_coef = (wall_mode == 0) ? 2.0 : 1.0;
+
+  /* Rows (and then wavenumbers) are independent.  Built with -fopenmp (the
+   * multi-thread timing build only) the loops below are shared among
+   * threads, each with its own scratch; the arithmetic of every row and
+   * every wavenumber is the same as in the one-thread build. */
+#pragma omp parallel
+  {
   double* rre = (double*)malloc(sizeof(double) * Nx);
   double* rim = (double*)malloc(sizeof(double) * Nx);
   double* tre = (double*)malloc(sizeof(double) * Nx);
@@ -242,6 +266,7 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
   double* dim = (double*)malloc(sizeof(double) * Ny);
 
   /* forward DFT of every row */
+#pragma omp for
   for (int y = 0; y < Ny; ++y) {
     for (int x = 0; x < Nx; ++x) {
       rre[x] = src[(size_t)y * Nx + x];
@@ -254,7 +279,7 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
     }
   }
   /* one tridiagonal per wavenumber */
-  double wall_coef = (wall_mode == 0) ? 2.0 : 1.0;
+#pragma omp for
   for (int m = 0; m < Nx; ++m) {
     int ms = (m <= Nx / 2) ? m : m - Nx; /* signed wavenumber */
     double kx = 2.0 * OPI * (double)ms / (double)Nx;
@@ -287,6 +312,7 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
     }
   }
   /* inverse DFT of every row, keep the real part */
+#pragma omp for
   for (int y = 0; y < Ny; ++y) {
     for (int m = 0; m < Nx; ++m) {
       rre[m] = sre[(size_t)m * Ny + y];
@@ -295,8 +321,6 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
     transform_row(Nx, rre, rim, tre, tim, +1);
     for (int x = 0; x < Nx; ++x) phi[(size_t)y * Nx + x] = rre[x] / (double)Nx;
   }
-  free(sre);
-  free(sim);
   free(rre);
   free(rim);
   free(tre);
@@ -306,6 +330,9 @@ void orc_poisson_general(int Nx, int Ny, int wall_mode, int x_symbol,
   free(c);
   free(dre);
   free(dim);
+  }
+  free(sre);
+  free(sim);
 }
 
 /* Sec. IV.3 as the paper prints it, without the tridiagonal: the source is
@@ -402,6 +429,7 @@ void orc_poisson_oddext(int Nx, int Ny, int wall_mode, int x_symbol,
 void orc_poisson(const orc_params* p, const double* rhoc, double* phi) {
   size_t nc = (size_t)p->Nx * p->Ny;
   double* s = (double*)malloc(sizeof(double) * nc);
+#pragma omp parallel for
   for (size_t k = 0; k < nc; ++k) s[k] = -rhoc[k] / p->eps; /* Eq. 4 */
   orc_poisson_general(p->Nx, p->Ny, p->wall_mode, p->x_symbol, p->phi0, 0.0, s,
                       phi);
@@ -600,7 +628,10 @@ void orc_step(const orc_params* p, double* f, double* g, double* phi,
       orc_efield(p, phi, Ex, Ey);
     }
     double mass = 0, charge = 0, ke = 0, maxuy = 0;
-    /* collision at every node */
+    /* collision at every node (nodes are independent; the -fopenmp timing
+     * build shares them among threads, which reorders only the diagnostic
+     * sums) */
+#pragma omp parallel for reduction(+ : mass, charge, ke) reduction(max : maxuy)
     for (size_t k = 0; k < nc; ++k) {
       double fl[9], gl[9], feq[9], geq[9], Fi[9];
       double rho = 0, jx = 0, jy = 0, rc = 0;
@@ -650,6 +681,9 @@ void orc_step(const orc_params* p, double* f, double* g, double* phi,
     }
     /* streaming f_i(x + c_i, t+1) = f_i*(x, t) with the wall rules */
     double q_in = 0, q_out = 0;
+    /* every (population, node) pair writes its own target, so rows are
+     * independent */
+#pragma omp parallel for reduction(+ : q_in, q_out)
     for (int y = 0; y < Ny; ++y) {
       for (int x = 0; x < Nx; ++x) {
         size_t k = (size_t)y * Nx + x;
@@ -691,6 +725,7 @@ void orc_step(const orc_params* p, double* f, double* g, double* phi,
     }
     /* rho_c(t+1) and phi(t+1) */
     if (!p->no_poisson) {
+#pragma omp parallel for
       for (size_t k = 0; k < nc; ++k) {
         double s = 0;
         for (int i = 0; i < 9; ++i) s += g[(size_t)i * nc + k];

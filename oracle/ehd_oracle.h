@@ -34,6 +34,7 @@ typedef struct {
   double rho_a, y_a;
 } orc_params;
 
+int orc_threads(int n);
 void orc_lattice(int* cx, int* cy, double* w, int* opp);
 int orc_setup(orc_params* p);
 int orc_hydrostatic_params(double rho0, double eps, double H, double dphi0,

@@ -99,12 +99,15 @@ def lib():
         L.ehd_tune.restype = ctypes.c_int
         L.ehd_tune_get.argtypes = [vp, ip]
         L.ehd_tune_get.restype = ctypes.c_int
-        L.ehd_batch_create.argtypes = [ip, ip, ip, vp, ctypes.POINTER(vp)]
+        L.ehd_batch_create.argtypes = [ip, ctypes.c_size_t, ip, ip, vp, ctypes.POINTER(vp)]
         L.ehd_batch_add.argtypes = [vp, vp, ctypes.c_long]
         L.ehd_batch_remove.argtypes = [vp, vp]
         L.ehd_batch_tick.argtypes = [vp, ip]
         L.ehd_batch_sync.argtypes = [vp]
-        for name in ("ehd_batch_create", "ehd_batch_add", "ehd_batch_remove", "ehd_batch_tick", "ehd_batch_sync"):
+        L.ehd_batch_admits.argtypes = [vp, ip, ip, ip]
+        L.ehd_batch_memory.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+        for name in ("ehd_batch_create", "ehd_batch_add", "ehd_batch_remove", "ehd_batch_tick", "ehd_batch_sync",
+                     "ehd_batch_admits", "ehd_batch_memory"):
             getattr(L, name).restype = ctypes.c_int
         L.ehd_batch_remaining.argtypes = [vp, vp]
         L.ehd_batch_remaining.restype = ctypes.c_long
@@ -371,10 +374,26 @@ class Run:
 
 
 # ------------------------------------------------------------------ batches
-def ehd_batch_create(max_runs, max_nx, max_ny, stream=None) -> int:
+def ehd_batch_create(max_runs, hbm_budget, max_nx, max_ny, stream=None) -> int:
     h = ctypes.c_void_p()
-    _check(lib().ehd_batch_create(int(max_runs), int(max_nx), int(max_ny), stream, ctypes.byref(h)))
+    _check(lib().ehd_batch_create(int(max_runs), int(hbm_budget), int(max_nx), int(max_ny), stream,
+                                  ctypes.byref(h)))
     return h.value
+
+
+def ehd_batch_admits(b, Nx, Ny, storage) -> int:
+    """Status of the admission query: 0 (EHD_OK), -6 (EHD_EBUSY) or -1
+    (EHD_EINVAL, never admissible); raises on other failures."""
+    st = int(lib().ehd_batch_admits(b, int(Nx), int(Ny), int(storage)))
+    if st not in (0, -1, -6):
+        _check(st)
+    return st
+
+
+def ehd_batch_memory(b):
+    used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().ehd_batch_memory(b, ctypes.byref(used), ctypes.byref(budget)))
+    return used.value, budget.value
 
 
 def ehd_batch_add(b, run_handle, steps):
@@ -423,14 +442,23 @@ def ehd_batch_destroy(b):
 class Batch:
     """Runs of uneven sizes advanced together (FP32 storage and compute)."""
 
-    def __init__(self, max_runs, max_nx=2048, max_ny=1680, stream=None, torch_stream=True):
+    def __init__(self, max_runs, max_nx=2048, max_ny=1680, stream=None, torch_stream=True, hbm_budget=0):
         self._stream_obj = None
         if stream is None and torch_stream:
             import torch
             self._stream_obj = torch.cuda.Stream()
             stream = self._stream_obj.cuda_stream
-        self.handle = ehd_batch_create(max_runs, max_nx, max_ny, stream)
+        self.handle = ehd_batch_create(max_runs, hbm_budget, max_nx, max_ny, stream)
         self.members = {}
+
+    def admits(self, Nx, Ny, storage="f32") -> int:
+        """0: admitted now; -6 (EHD_EBUSY): wait for a slot or memory;
+        -1 (EHD_EINVAL): never."""
+        return ehd_batch_admits(self.handle, Nx, Ny, STORAGE[storage])
+
+    def memory(self):
+        """(bytes the members hold, HBM budget)."""
+        return ehd_batch_memory(self.handle)
 
     def add(self, run: "Run", steps: int):
         ehd_batch_add(self.handle, run.handle, steps)

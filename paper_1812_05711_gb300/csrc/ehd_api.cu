@@ -113,6 +113,9 @@ struct ehd_run {
 
 struct ehd_batch {
   int device = 0, max_runs = 0, max_nx = 0, max_ny = 0, sms = 152;
+  size_t hbm_budget = 0;      // bytes the members' device state may hold (0: no limit)
+  size_t hbm_used = 0;        // sum of the members' ehd_footprint
+  std::vector<size_t> member_bytes;
   cudaStream_t stream = nullptr, side = nullptr;
   bool own_stream = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_upload = nullptr;
@@ -1160,7 +1163,8 @@ ehd_status batch_capture(ehd_batch* b, int K, cudaGraphExec_t* out) {
 
 extern "C" {
 
-ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream, ehd_batch** out) {
+ehd_status ehd_batch_create(int max_runs, size_t hbm_budget, int max_nx, int max_ny, void* stream,
+                            ehd_batch** out) {
   if (!out) return fail(EHD_EINVAL, "out is NULL");
   *out = nullptr;
   if (max_runs < 1 || max_runs > 4096) return fail(EHD_EINVAL, "max_runs must be in [1, 4096]");
@@ -1175,6 +1179,7 @@ ehd_status ehd_batch_create(int max_runs, int max_nx, int max_ny, void* stream, 
   b->max_runs = max_runs;
   b->max_nx = max_nx;
   b->max_ny = max_ny;
+  b->hbm_budget = hbm_budget;
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   {
     // the batch's wavenumber tiles hold max_ny rows of 8 wavenumbers (12 B
@@ -1250,12 +1255,44 @@ ehd_status ehd_batch_add(ehd_batch* b, ehd_run* r, long steps) {
   if (r->Nx < 64 || r->Nx > b->max_nx || r->Ny > b->max_ny) return fail(EHD_EINVAL, "run size exceeds the batch limits");
   if (r->device != b->device) return fail(EHD_EINVAL, "run and batch are on different devices");
   if ((int)b->members.size() >= b->max_runs) return fail(EHD_EBUSY, "batch is full");
+  size_t need = 0;
+  if (ehd_footprint(r->Nx, r->Ny, r->storage, &need) != EHD_OK) return EHD_EINVAL;
+  if (b->hbm_budget && b->hbm_used + need > b->hbm_budget)
+    return fail(EHD_EBUSY, "HBM budget: the members hold %zu of %zu bytes, the run needs %zu", b->hbm_used,
+                b->hbm_budget, need);
   DeviceGuard dg(b->device);
   EHD_CK(cudaStreamSynchronize(r->stream));
   r->batch = b;
   b->members.push_back(r);
   b->remaining.push_back(steps);
+  b->member_bytes.push_back(need);
+  b->hbm_used += need;
   b->dirty = true;
+  return EHD_OK;
+}
+
+ehd_status ehd_batch_admits(ehd_batch* b, int Nx, int Ny, int storage) {
+  if (!b) return fail(EHD_EINVAL, "batch is NULL");
+  if (storage != EHD_STORE_F32) return fail(EHD_EINVAL, "batches take FP32-storage runs");
+  if (Nx < 64 || Nx > b->max_nx || Ny > b->max_ny || Ny < 2)
+    return fail(EHD_EINVAL, "a %dx%d run exceeds the batch limits", Nx, Ny);
+  size_t need = 0;
+  ehd_status st = ehd_footprint(Nx, Ny, storage, &need);
+  if (st != EHD_OK) return st;
+  if (b->hbm_budget && need > b->hbm_budget)
+    return fail(EHD_EINVAL, "a %dx%d run needs %zu bytes, more than the whole HBM budget of %zu", Nx, Ny, need,
+                b->hbm_budget);
+  if ((int)b->members.size() >= b->max_runs) return fail(EHD_EBUSY, "batch is full");
+  if (b->hbm_budget && b->hbm_used + need > b->hbm_budget)
+    return fail(EHD_EBUSY, "HBM budget: the members hold %zu of %zu bytes, the run needs %zu", b->hbm_used,
+                b->hbm_budget, need);
+  return EHD_OK;
+}
+
+ehd_status ehd_batch_memory(ehd_batch* b, size_t* used, size_t* budget) {
+  if (!b) return fail(EHD_EINVAL, "batch is NULL");
+  if (used) *used = b->hbm_used;
+  if (budget) *budget = b->hbm_budget;
   return EHD_OK;
 }
 
@@ -1268,6 +1305,8 @@ ehd_status ehd_batch_remove(ehd_batch* b, ehd_run* r) {
   const size_t i = (size_t)(it - b->members.begin());
   b->members.erase(it);
   b->remaining.erase(b->remaining.begin() + i);
+  b->hbm_used -= b->member_bytes[i];
+  b->member_bytes.erase(b->member_bytes.begin() + i);
   r->batch = nullptr;
   b->dirty = true;
   return EHD_OK;

@@ -12,8 +12,15 @@
 // exits.
 //
 // In host code the array's name is only a host-side stand-in; its device
-// address is obtained once per device with cudaGetSymbolAddress (on the first
-// call made with that device current) and passed to the kernels.
+// address is looked up with cudaGetSymbolAddress on every call, with the
+// calling device current, and passed to the kernels.
+//
+// The twiddle and pivot tables for a grid are rebuilt only when the sizes
+// change, which the host tracks per device.  A call made while its stream is
+// being captured cannot rely on that record (the captured work may run any
+// number of times, interleaved with direct calls for other sizes), so it
+// always enqueues the table build, and from then on every call on that
+// device rebuilds the tables.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -57,8 +64,9 @@ Layout layout_for(int Nx, int Ny) {
 }
 
 struct DeviceSlot {
-  unsigned char* base = nullptr;  // device address of g_scratch on this device
+  unsigned char* base = nullptr;  // device address of g_scratch at the last call
   int Nx = 0, Ny = 0, wall_mode = -1;  // sizes the tables were built for
+  bool always_rebuild = false;    // set once a call was made during stream capture
 };
 std::mutex g_mu;
 DeviceSlot g_slots[kMaxDevices];
@@ -306,15 +314,24 @@ extern "C" ehd_status ehd_poisson_noalloc(int Nx, int Ny, double eps, double phi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceSlot& slot = g_slots[dev];
-  if (!slot.base) {
-    void* addr = nullptr;
-    e = cudaGetSymbolAddress(&addr, g_scratch);
-    if (e != cudaSuccess || !addr)
-      return na_fail(EHD_ECUDA, "ehd_poisson_noalloc: cudaGetSymbolAddress of the static scratch failed");
+  void* addr = nullptr;
+  e = cudaGetSymbolAddress(&addr, g_scratch);
+  if (e != cudaSuccess || !addr)
+    return na_fail(EHD_ECUDA, "ehd_poisson_noalloc: cudaGetSymbolAddress of the static scratch failed");
+  if (static_cast<unsigned char*>(addr) != slot.base) {
+    // first call on this device, or the module was loaded again (e.g. after
+    // cudaDeviceReset): nothing in the array can be trusted
+    slot = DeviceSlot{};
     slot.base = static_cast<unsigned char*>(addr);
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;  // unknown: take the safe path
+  }
+  if (cap != cudaStreamCaptureStatusNone) slot.always_rebuild = true;
   const Ptrs p = ptrs(slot.base, L);
-  if (slot.Nx != Nx || slot.Ny != Ny || slot.wall_mode != wall_mode) {
+  if (slot.always_rebuild || slot.Nx != Nx || slot.Ny != Ny || slot.wall_mode != wall_mode) {
     const int n = Nx / 2 + 1;
     k_na_tables<<<(n + 127) / 128, 128, 0, s>>>(Nx, Ny, wall_mode, p);
     if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(EHD_ECUDA, "ehd_poisson_noalloc: table kernel launch failed");

@@ -4,7 +4,9 @@ Requests (a channel size, the groups T, C, M, Fe, Lambda, an Eq. 29
 perturbation and a step budget) arrive over time.  The server keeps every
 admitted run's populations resident on the GPU, admits a waiting request as
 soon as a batch slot is free and its device footprint (``ehd_footprint``)
-fits the HBM budget, and advances all admitted runs together, tick by tick,
+fits the HBM budget -- the batch itself keeps that account behind the C ABI
+(``ehd_batch_create`` takes the budget, ``ehd_batch_admits`` answers before a
+run is allocated, ``ehd_batch_add`` refuses with EHD_EBUSY) -- and advances all admitted runs together, tick by tick,
 through one :class:`~paper_1812_05711_gb300.Batch`.  A run leaves at the end
 of the tick in which its budget is used up; its result (the final
 diagnostics and, optionally, fields) is recorded with its latency
@@ -23,6 +25,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import STORAGE, Batch, Run, ehd_footprint
+
+OK, EINVAL, EBUSY = 0, -1, -6  # ehd_status values of the batch's admission query
 
 
 @dataclass
@@ -67,14 +71,13 @@ class Server:
                  max_ny: int = 840, u_ion: float = 2e-3, keep_fields=(), clock=time.perf_counter):
         if tick_steps < 2 or tick_steps % 2:
             raise ValueError("tick_steps must be even and >= 2")
-        self.batch = Batch(max_runs, max_nx=max_nx, max_ny=max_ny)
+        self.batch = Batch(max_runs, max_nx=max_nx, max_ny=max_ny, hbm_budget=int(hbm_budget))
         self.max_runs, self.max_nx, self.max_ny = max_runs, max_nx, max_ny
         self.hbm_budget, self.tick_steps, self.u_ion = int(hbm_budget), int(tick_steps), u_ion
         self.keep_fields = tuple(keep_fields)
         self.clock = clock
         self.waiting = collections.deque()
         self.active = {}   # run handle -> (request, run, admitted time)
-        self.used = 0
         self.results = []
         self.t0 = None
         self.ticks = 0
@@ -83,10 +86,15 @@ class Server:
     def footprint(self, req: Request) -> int:
         return ehd_footprint(req.Nx, req.Ny, STORAGE["f32"])
 
+    @property
+    def used(self) -> int:
+        """Bytes the admitted runs hold, as the batch accounts them."""
+        return self.batch.memory()[0]
+
     def submit(self, req: Request):
         if req.Nx > self.max_nx or req.Ny > self.max_ny or req.Nx < 64:
             raise ValueError(f"request {req.rid}: grid {req.Nx}x{req.Ny} outside the server limits")
-        if self.footprint(req) > self.hbm_budget:
+        if self.batch.admits(req.Nx, req.Ny) == EINVAL:
             raise ValueError(f"request {req.rid}: footprint exceeds the whole HBM budget")
         self.waiting.append(req)
 
@@ -98,15 +106,13 @@ class Server:
             req = self.waiting[0]
             if req.arrival > now:
                 break
-            need = self.footprint(req)
-            if self.used + need > self.hbm_budget:
-                break  # first come, first served: wait for memory to free up
+            if self.batch.admits(req.Nx, req.Ny) != OK:
+                break  # first come, first served: wait for a slot or memory to free up
             self.waiting.popleft()
             run = Run(req.Nx, req.Ny, req.T, req.C, req.M, req.Fe, req.Lambda, storage="f32",
                       u_ion=self.u_ion, amp=req.amp, phase=req.phase)
-            self.batch.add(run, req.steps)
+            self.batch.add(run, req.steps)  # the batch accounts the run's footprint
             self.active[run.handle] = (req, run, now)
-            self.used += need
 
     def _retire(self, now: float):
         for h in [h for h, (req, run, _) in self.active.items() if self.batch.remaining(run) == 0]:
@@ -116,7 +122,6 @@ class Server:
             flds = run.fields(self.keep_fields) if self.keep_fields else None
             self.results.append(Result(req.rid, req.arrival, t_adm, now, req.steps, diag, flds))
             run.close()
-            self.used -= self.footprint(req)
 
     # --------------------------------------------------------------- loop
     def step(self) -> bool:

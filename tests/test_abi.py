@@ -77,3 +77,11 @@ def test_default_options():
     o = ehd.ehd_default_options()
     assert o.storage == 1 and o.compute == 1 and o.lambda_g == 1e-6 and o.u_ion == 2e-3
     assert o.step_kernel == -1  # chosen per run: push form for plain FP64, march form otherwise
+
+
+def test_batch_queries_reject_null():
+    """The admission query and the memory account need a batch (no GPU)."""
+    L = ehd.lib()
+    assert L.ehd_batch_admits(None, 128, 104, 1) == -1
+    assert L.ehd_batch_memory(None, None, None) == -1
+    assert "NULL" in ehd.ehd_last_error()

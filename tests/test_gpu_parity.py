@@ -206,12 +206,16 @@ def _oracle_1024x840(steps):
 
 
 @gpu
-@pytest.mark.parametrize("storage,compute,bound", [("f64", "f64", 1e-11), ("f32", "f32", 1e-6),
+@pytest.mark.parametrize("storage,compute,bound", [("f64", "f64", 5e-12), ("f32", "f32", 1e-6),
                                                    ("bf16", "f32", 1e-3), ("f16", "f32", 2e-4)])
 def test_storage_variants_vs_oracle_1024x840(storage, compute, bound):
     """The 1024 x 840, T = 170 channel after 50 steps, every storage against
-    the oracle (measured: plain FP64 2.2e-12 -- the oracle's own Thomas
-    rounding at this height --, FP32 6.3e-8, BF16 2.5e-4, FP16 3.3e-5)."""
+    the oracle (measured: plain FP64 2.2e-12, FP32 6.3e-8, BF16 2.5e-4, FP16
+    3.3e-5).  The plain FP64 bound is the 1e-12 bar plus twice the oracle's
+    own rounding at this height: its Thomas elimination of the mean mode
+    loses 2.1e-12 of the E_y scale at 840 rows against a 40-digit solve of the
+    same system (tests/test_oracle_rounding.py), against 3e-14 at the 104
+    rows of the 1e-12 parity configuration."""
     ehd = _ehd()
     w = wl.precision_channel()
     p, ora = _oracle_1024x840(50)

@@ -437,7 +437,7 @@ def test_initial_state_moments():
     assert np.abs(F["ux"] - ux).max() < 1e-3 * p.u_ion * 1e-2 + 1e-12
 
 
-# ------------------------------------------------- linear threshold ---
+# ------------------------------- linear threshold (Sec. V.2, T_c = 163.4) ---
 def _growth_rate(max_uy, steps_per_sample=1):
     """Exponential rate of max|u_y| per step: least-squares slope of its log
     over the second half of the record (the first half lets the initial

@@ -30,18 +30,37 @@ class FakeRun:
 
 
 class FakeBatch:
-    def __init__(self, max_runs, max_nx, max_ny):
+    """Slots and HBM accounting as ehd_batch_admits / ehd_batch_add keep
+    them (footprint of an Nx x Ny run: Nx * Ny bytes)."""
+
+    def __init__(self, max_runs, max_nx, max_ny, hbm_budget=0):
         self.left = {}
+        self.bytes = {}
         self.ticks = []
+        self.max_runs, self.budget = max_runs, hbm_budget
+
+    def admits(self, Nx, Ny, storage="f32"):
+        need = Nx * Ny
+        if self.budget and need > self.budget:
+            return -1
+        if len(self.left) >= self.max_runs or (self.budget and sum(self.bytes.values()) + need > self.budget):
+            return -6
+        return 0
+
+    def memory(self):
+        return sum(self.bytes.values()), self.budget
 
     def add(self, run, steps):
+        assert self.admits(run.Nx, run.Ny) == 0
         self.left[run.handle] = steps
+        self.bytes[run.handle] = run.Nx * run.Ny
 
     def remaining(self, run):
         return self.left[run.handle]
 
     def remove(self, run):
         del self.left[run.handle]
+        del self.bytes[run.handle]
 
     def tick(self, k):
         self.ticks.append(sorted(self.left))
