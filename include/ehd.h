@@ -40,7 +40,8 @@ typedef enum {
   EHD_ENOMEM = -2,     /* device or host allocation failed */
   EHD_ECUDA = -3,      /* a CUDA runtime call failed */
   EHD_EDIVERGED = -4,  /* a non-finite density or charge was produced */
-  EHD_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  EHD_ETIMEOUT = -5,   /* a bounded device wait gave up (reported by the next
+                          synchronising call, like EHD_EDIVERGED) */
   EHD_EBUSY = -6       /* reserved: capacity exhausted */
 } ehd_status;
 
@@ -176,7 +177,13 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * complex FFT of length NE, division by -(kappa_m + 4 sin^2(pi k / NE))
  * (Eqs. 20, 24), inverse FFT, first Ny points (Eq. 25); NE must have no
  * prime factor above 13 and one column must fit in shared memory, and
- * runs in a batch keep 0; the mean mode m = 0 is solved as before).
+ * runs in a batch keep 0; the mean mode m = 0 is solved as before),
+ * EHD_TUNE_MARCH_TMA (march form, FP32 storage and compute, 128 <= Nx <=
+ * 2048: 0, the default, per-lane 8-byte cp.async staging and 8-byte
+ * stores; 1, each row of a strip staged by tensor copies
+ * (cp.async.bulk.tensor, 9 planes per copy) with mbarrier completion;
+ * 2, the same and completed rows written by tensor stores from a
+ * shared-memory tile; the same results bit for bit).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -187,6 +194,7 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_PDL 6
 #define EHD_TUNE_FFT_CTA 7
 #define EHD_TUNE_Y_SOLVER 8
+#define EHD_TUNE_MARCH_TMA 9
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

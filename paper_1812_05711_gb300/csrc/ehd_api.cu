@@ -109,6 +109,11 @@ struct ehd_run {
   long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   ehd_batch* batch = nullptr;  // batch the run belongs to, if any
+  // TMA form of the march (FP32 storage and compute, 128 <= Nx): tensor maps
+  // for a step from buffer 0 and from buffer 1, and whether it is used
+  MarchTma tma[2] = {};
+  bool tma_ok = false;
+  int march_tma = 0;
 };
 
 struct ehd_batch {
@@ -320,6 +325,16 @@ FieldArgs field_args(const ehd_run* r) {
   return a;
 }
 
+// The march form's collide-and-stream kernel: its TMA form when the run
+// takes it, else the cp.async form.
+bool tma_form(const ehd_run* r) {
+  return r->march_tma && r->tma_ok && r->cols_per_lane == 2 && !r->ex_spectral && r->step_kernel == 0;
+}
+cudaError_t launch_march_run(const ehd_run* r, const StepArgs& sa, int cur) {
+  if (tma_form(r)) return launch_march_tma(sa, r->tma[cur], r->march_tma == 2, r->stream);
+  return launch_march(sa, r->storage, r->real_f64, r->stream);
+}
+
 // One coupled step from buffer `cur`: collide+stream with the wall-flux
 // partials, then the Poisson solve of the new charge (which also adds the
 // fluxes to the FP64 totals).  The march form writes the new charge itself;
@@ -327,7 +342,7 @@ FieldArgs field_args(const ehd_run* r) {
 cudaError_t enqueue_step(ehd_run* r, int cur) {
   const StepArgs sa = step_args(r, cur);
   if (r->step_kernel == 0) {
-    cudaError_t e = launch_march(sa, r->storage, r->real_f64, r->stream);
+    cudaError_t e = launch_march_run(r, sa, cur);
     if (e != cudaSuccess) return e;
     return launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
   }
@@ -361,6 +376,7 @@ ehd_status check_err(ehd_run* r) {
   int h = 0;
   EHD_CK(cudaMemcpyAsync(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost, r->stream));
   EHD_CK(cudaStreamSynchronize(r->stream));
+  if (h & 2) return fail(EHD_ETIMEOUT, "a bounded wait of the step kernel gave up (tensor copy not completed)");
   if (h) return fail(EHD_EDIVERGED, "non-finite density or charge in the state");
   return EHD_OK;
 }
@@ -591,6 +607,18 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_ENOMEM, "device allocation failed");
   }
   r->err = reinterpret_cast<int*>(r->small + 16);
+  // tensor maps of the TMA march (FP32 storage and compute): one set per
+  // buffer parity; the default form when they encode
+  if (r->storage == EHD_STORE_F32 && !r->real_f64 && march_tma_supported(Nx)) {
+    r->tma_ok = march_tma_encode(&r->tma[0], r->f[0], r->g[0], r->dphi, r->f[1], r->g[1], Nx, Ny, r->P) ==
+                    cudaSuccess &&
+                march_tma_encode(&r->tma[1], r->f[1], r->g[1], r->dphi, r->f[0], r->g[0], Nx, Ny, r->P) ==
+                    cudaSuccess;
+    // the per-lane cp.async form stays the default: at 2048 x 1680 the
+    // tensor-copy forms took 98.6 (loads) and 100.8 us (loads and stores)
+    // per launch against its 93.4 us
+    r->march_tma = 0;
+  }
   // march slabs: as many warps as the GPU holds at once (one wave), at
   // least 4 rows each
   {
@@ -799,6 +827,12 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       r->nstrips = march_strips(r->Nx, value);
       if (r->step_kernel == 0) r->nxb = r->nstrips;
       break;
+    case EHD_TUNE_MARCH_TMA:
+      if (value < 0 || value > 2) return fail(EHD_EINVAL, "TMA march must be 0, 1 or 2");
+      if (value != 0 && !r->tma_ok)
+        return fail(EHD_EINVAL, "the TMA march needs FP32 storage and compute and 128 <= Nx <= 2048");
+      r->march_tma = value;
+      break;
     case EHD_TUNE_STEP_KERNEL:
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "step kernel must be 0 or 1");
       if (value != 0 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x needs the march form");
@@ -828,6 +862,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_PDL: return r->pdl;
     case EHD_TUNE_FFT_CTA: return r->fft_cta;
     case EHD_TUNE_Y_SOLVER: return r->y_solver;
+    case EHD_TUNE_MARCH_TMA: return tma_form(r) ? r->march_tma : 0;
   }
   return -1;
 }
@@ -880,7 +915,7 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
     const int nxt = 1 - r->cur;
     e = cudaEventRecord(E[0], r->stream);
     if (e == cudaSuccess)
-      e = (r->step_kernel == 0) ? launch_march(sa, r->storage, r->real_f64, r->stream)
+      e = (r->step_kernel == 0) ? launch_march_run(r, sa, r->cur)
                                 : launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
     if (e == cudaSuccess) e = cudaEventRecord(E[1], r->stream);
     if (e == cudaSuccess && r->step_kernel == 1)
@@ -1387,6 +1422,7 @@ ehd_status ehd_batch_sync(ehd_batch* b) {
   for (ehd_run* r : b->members) {
     int h = 0;
     EHD_CK(cudaMemcpy(&h, r->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & 2) return fail(EHD_ETIMEOUT, "a bounded wait of a member's step kernel gave up");
     if (h) return fail(EHD_EDIVERGED, "a member run holds a non-finite density or charge");
   }
   return EHD_OK;

@@ -16,6 +16,7 @@
 //   rch          per-row charge shift (hydrostatic rho_c rounded to FP32), [Ny]
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is reached through the runtime)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -242,6 +243,23 @@ cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStr
 cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s);
 constexpr int kBatchTileModes = 8;
+
+// Tensor maps of the TMA form of the march kernel (FP32 storage and compute,
+// Nx >= 128): the pre-collision populations as 3-D tensors {Nx, Ny, 9}
+// loaded in boxes of {68, 1, 9} (a strip's 64 columns and the 4-column
+// alignment margin, every plane of one row), the potential fluctuation
+// {Nx, Ny} in boxes of {68, 1}, and the post-collision populations stored in
+// boxes of {60, 1, 9} (a strip's owned columns).  One set per buffer parity.
+constexpr int kTmaLoadCols = 68;
+constexpr int kTmaStoreCols = 60;
+struct MarchTma {
+  CUtensorMap f, g, dphi, fo, go;
+};
+// Encode the maps of a run (f[cur], g[cur] in, f[1-cur], g[1-cur] out).
+cudaError_t march_tma_encode(MarchTma* m, const void* fin, const void* gin, const void* dphi, void* fout, void* gout,
+                             int Nx, int Ny, int P);
+bool march_tma_supported(int Nx);
+cudaError_t launch_march_tma(const StepArgs& a, const MarchTma& m, bool tensor_stores, cudaStream_t s);
 
 // Launchers (defined in the .cu files); storage: 0 F64, 1 F32, 2 BF16, 3 F16;
 // real_f64: compute type (true = double).

@@ -884,6 +884,598 @@ cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, cudaStr
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA form of the march (FP32 storage and compute, Nx >= 128).  The same
+// walk, collision and routing as march2_body; what changes is how rows move
+// between HBM and the warp:
+//   - loads: one elected lane stages each row of the strip with three
+//     cp.async.bulk.tensor copies (the 9 f planes and the 9 g planes as one
+//     {68, 1, 9} box each, the potential fluctuation of the next row as a
+//     {68, 1} box) into a two-stage shared-memory ring; an mbarrier per stage
+//     counts the bytes in.  The box starts 4 columns left of the strip's
+//     first (halo) column so that its x coordinate is 16-byte aligned; lanes
+//     read their pair at offset 2 + 2 lane.  The two halo pairs that wrap
+//     around the periodic x boundary (strip 0's lane 0 and the last strip's
+//     right halo lane) fall outside the tensor and read the zero fill, so
+//     those lanes fetch their own pair with 8-byte cp.async copies.
+//   - stores: every row a warp completes inside its slab goes out as two
+//     {60, 1, 9} tensor stores from a shared-memory tile (all 18 planes of
+//     the strip's owned columns); the few partial rows at slab boundaries,
+//     the pushes into neighbouring slabs and the collector row keep 8-byte
+//     stores.
+// Every wait on an mbarrier is bounded; a wait that gives up sets bit 1 of
+// the run's error word (EHD_ETIMEOUT on the host), drains what the warp has
+// in flight and ends the warp.
+namespace tma {
+
+constexpr int kLC = kTmaLoadCols;   // 68 loaded columns per row and plane
+constexpr int kSC = kTmaStoreCols;  // 60 stored (owned) columns
+constexpr unsigned kPlaneBytes = 9u * kLC * 4u;  // 2448: one {68, 1, 9} box
+// per-warp shared memory (byte offsets; TMA destinations 128-byte aligned)
+constexpr int kStF = 0;                  // [9][68] f of the staged row
+constexpr int kStG = 2560;               // [9][68] g
+constexpr int kStP = 5120;               // [68] potential fluctuation of the next row
+constexpr int kStW = 5504;               // [20][2] the wrap lane's own pair (18 populations, potential)
+constexpr int kStage = 5760;             // bytes per stage
+constexpr int kOutF = 2 * kStage;        // [9][60] f of the completed row
+constexpr int kOutG = kOutF + 2176;      // [9][60] g
+constexpr int kMbar = kOutF + 2 * 2176;  // two mbarriers
+constexpr int kWarpBytes = kMbar + 128;  // 16000
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void load3d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(0), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void load2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void store3d(const CUtensorMap* map, int x, int y, unsigned src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(map), "r"(x),
+               "r"(y), "r"(0), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+}  // namespace tma
+
+template <bool TSTORE>
+__device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma& tm, int strip, int slab,
+                                               unsigned char* ws) {
+  using namespace tma;
+  using R = float;
+  const int lane = threadIdx.x & 31;
+  const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
+  const int y0 = slab * a.slab_rows;
+  if (y0 >= Ny) return;  // whole warp
+  const int y1 = min(y0 + a.slab_rows, Ny);
+  const int xs = strip * 60;
+  const int x0 = xs - 4;                 // box start (16-byte aligned; -4 for strip 0)
+  const int xcol = xs - 2 + 2 * lane;    // the lane's pair, unwrapped
+  const int xc = (xcol + 2 * Nx) % Nx;   // wrapped (even)
+  const bool owned = lane >= 1 && lane <= 30 && xs + 2 * (lane - 1) < Nx;
+  // the halo pairs across the periodic boundary, outside the tensor's x range
+  const bool wrap = (strip == 0 && lane == 0) || (strip == ns - 1 && xcol == Nx);
+  const int toff = 2 + 2 * lane;         // the pair's column in the staged box
+  const long long pl = a.plane;
+  const float* __restrict__ fin = static_cast<const float*>(a.fin);
+  const float* __restrict__ gin = static_cast<const float*>(a.gin);
+  float* __restrict__ fo = static_cast<float*>(a.fout);
+  float* __restrict__ go = static_cast<float*>(a.gout);
+  R* __restrict__ rho_out = static_cast<R*>(a.rhoc_out);
+  const R* __restrict__ dphi = static_cast<const R*>(a.dphi);
+  const R* __restrict__ Ebar = static_cast<const R*>(a.Ebar);
+  const float* __restrict__ rch = a.rch;
+  const R wp = (R)a.wp, wm = (R)a.wm, gwp = (R)a.gwp, gwm = (R)a.gwm;
+  const R cp = R(1) - R(0.5) * wp, cm = R(1) - R(0.5) * wm;
+  const R mub = (R)a.mub, rho0 = (R)a.rho0;
+  const R gwall = (a.wall_mode == 0) ? R(-1) : R(0);
+  const R W1 = (R)kW1, W2 = (R)kW2;
+  const R fb = (R)a.fb, fd = (R)a.fd, fdq = (R)a.fdq;
+  const R wd1 = W1 * fd, wd2 = W2 * fd;
+  const int rs = y0, re = y1 - 1;
+  const bool push_dn = y0 > 0, push_up = y1 < Ny;
+  R* __restrict__ rx_dn = static_cast<R*>(a.rhoc_dn);
+  R* __restrict__ rx_up = static_cast<R*>(a.rhoc_up);
+  R sy_last = R(0);
+
+  const unsigned mbar0 = smem_u32(ws + kMbar);
+  if (lane == 0) {
+    mbar_init(mbar0);
+    mbar_init(mbar0 + 8);
+    fence_mbar_init();
+  }
+  __syncwarp();
+
+  // stage one row: the elected lane's tensor copies, the wrap lane's pair
+  auto issue = [&](int row_y, int stage) {
+    unsigned char* st = ws + stage * kStage;
+    const bool next = row_y + 1 < Ny;
+    if (lane == 0) {
+      const unsigned mb = mbar0 + 8 * stage;
+      fence_async_smem();  // the stage's previous contents were read through the generic proxy
+      mbar_expect_tx(mb, 2 * kPlaneBytes + (next ? kLC * 4u : 0u));
+      load3d(smem_u32(st + kStF), &tm.f, x0, row_y, mb);
+      load3d(smem_u32(st + kStG), &tm.g, x0, row_y, mb);
+      if (next) load2d(smem_u32(st + kStP), &tm.dphi, x0, row_y + 1, mb);
+    }
+    if (wrap) {
+      const long long c = (long long)row_y * P + xc;
+      float* w = reinterpret_cast<float*>(st + kStW);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        cp_async_elem<8>(w + 2 * i, fin + i * pl + c);
+        cp_async_elem<8>(w + 2 * (9 + i), gin + i * pl + c);
+      }
+      if (next) cp_async_elem<8>(w + 36, dphi + c + P);
+    }
+    cp_async_commit();
+  };
+
+  // carried rows, [k][j]: H (c_y = 0) of row r-1, U (c_y = +1) of rows r-1, r
+  R Hm[6][2] = {}, Um[6][2] = {}, Uc[6][2] = {};
+  R pm[2], pc[2];
+  {
+    const long long c = (long long)rs * P + xc;
+    pc[0] = dphi[c];
+    pc[1] = dphi[c + 1];
+    if (rs > 0) {
+      pm[0] = dphi[c - P];
+      pm[1] = dphi[c - P + 1];
+    } else {
+      pm[0] = gwall * pc[0];
+      pm[1] = gwall * pc[1];
+    }
+  }
+  double qin = 0.0, qout = 0.0;
+  bool bad = false, timed_out = false;
+  // the row scalars (mean field, charge shifts) of row r, loaded a row ahead
+  R Eb_n = Ebar[rs], sy_n = rch[rs];
+  R sup_n = (rs + 1 < Ny) ? rch[rs + 1] : sy_n, sdn_n = (rs > 0) ? rch[rs - 1] : sy_n;
+  bool out_pending = false;  // a tensor store of the out tile may still be reading it
+  int stuck = -1;            // iteration whose wait gave up
+
+  issue(rs, 0);
+  for (int r = rs; r <= re; ++r) {
+    const long long row = (long long)r * P;
+    const int kk = r - rs;
+    const int stg = kk & 1;
+    __syncwarp();  // every lane has finished reading the stage about to be refilled
+    if (r + 1 <= re) issue(r + 1, stg ^ 1);
+    else cp_async_commit();  // keep one group per iteration
+    const R Ebr = Eb_n, sy = sy_n, s_up = sup_n, s_dn = sdn_n;
+    if (r + 1 <= re) {
+      Eb_n = Ebar[r + 1];
+      sy_n = rch[r + 1];
+      sup_n = (r + 2 < Ny) ? rch[r + 2] : sy_n;
+      sdn_n = rch[r];
+    }
+    if (!mbar_wait(mbar0 + 8 * stg, (unsigned)(kk >> 1) & 1u)) {
+      timed_out = true;
+      stuck = kk;
+      break;
+    }
+    cp_async_wait<1>();  // the wrap lane's copies of row r (row r + 1's may be pending)
+    const unsigned char* st = ws + stg * kStage;
+    R F[9][2], G[9][2];
+    R pn[2];
+    if (wrap) {
+      const float2* w = reinterpret_cast<const float2*>(st + kStW);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const float2 vf = w[i], vg = w[9 + i];
+        F[i][0] = vf.x;
+        F[i][1] = vf.y;
+        G[i][0] = vg.x;
+        G[i][1] = vg.y;
+      }
+      const float2 vp = w[18];
+      pn[0] = vp.x;
+      pn[1] = vp.y;
+    } else {
+      const float* tf = reinterpret_cast<const float*>(st + kStF) + toff;
+      const float* tg = reinterpret_cast<const float*>(st + kStG) + toff;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const float2 vf = *reinterpret_cast<const float2*>(tf + i * kLC);
+        const float2 vg = *reinterpret_cast<const float2*>(tg + i * kLC);
+        F[i][0] = vf.x;
+        F[i][1] = vf.y;
+        G[i][0] = vg.x;
+        G[i][1] = vg.y;
+      }
+      const float2 vp = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + kStP) + toff);
+      pn[0] = vp.x;
+      pn[1] = vp.y;
+    }
+    if (r + 1 >= Ny) {
+      pn[0] = gwall * pc[0];
+      pn[1] = gwall * pc[1];
+    }
+    const R sf = fb + fd * (R)r;
+    R Ex0, Ex1;
+    {
+      const R pWl = from_left(pc[1]);   // phi(xc - 1)
+      const R pEr = from_right(pc[0]);  // phi(xc + 2)
+      Ex0 = R(-0.5) * (pc[1] - pWl);
+      Ex1 = R(-0.5) * (pEr - pc[0]);
+    }
+    const R Ey0 = Ebr - R(0.5) * (pn[0] - pm[0]), Ey1 = Ebr - R(0.5) * (pn[1] - pm[1]);
+    R f0[9], g0[9], f1[9], g1[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      f0[i] = F[i][0];
+      g0[i] = G[i][0];
+      f1[i] = F[i][1];
+      g1[i] = G[i][1];
+    }
+    bool b0, b1;
+    collide_node<float, R>(f0, g0, Ex0, Ey0, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b0);
+    collide_node<float, R>(f1, g1, Ex1, Ey1, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b1);
+    if (owned && (b0 || b1)) bad = true;
+    const R P1f0 = from_left(f1[1]), P5f0 = from_left(f1[5]), P8f0 = from_left(f1[8]);
+    const R P3f1 = from_right(f0[3]), P6f1 = from_right(f0[6]), P7f1 = from_right(f0[7]);
+    const R P1g0 = from_left(g1[1]), P5g0 = from_left(g1[5]), P8g0 = from_left(g1[8]);
+    const R P3g1 = from_right(g0[3]), P6g1 = from_right(g0[6]), P7g1 = from_right(g0[7]);
+    const R Pf1[2] = {P1f0, f0[1]}, Pf5[2] = {P5f0, f0[5]}, Pf8[2] = {P8f0, f0[8]};
+    const R Pf3[2] = {f1[3], P3f1}, Pf6[2] = {f1[6], P6f1}, Pf7[2] = {f1[7], P7f1};
+    const R Pg1[2] = {P1g0, g0[1]}, Pg5[2] = {P5g0, g0[5]}, Pg8[2] = {P8g0, g0[8]};
+    const R Pg3[2] = {g1[3], P3g1}, Pg6[2] = {g1[6], P6g1}, Pg7[2] = {g1[7], P7g1};
+    const R f0c[2] = {f0[0], f1[0]}, g0c[2] = {g0[0], g1[0]};
+    const R f2c[2] = {f0[2], f1[2]}, g2c[2] = {g0[2], g1[2]};
+    const R f4c[2] = {f0[4], f1[4]}, g4c[2] = {g0[4], g1[4]};
+    const R f5c[2] = {f0[5], f1[5]}, f6c[2] = {f0[6], f1[6]}, f7c[2] = {f0[7], f1[7]}, f8c[2] = {f0[8], f1[8]};
+    const R g5c[2] = {g0[5], g1[5]}, g6c[2] = {g0[6], g1[6]}, g7c[2] = {g0[7], g1[7]}, g8c[2] = {g0[8], g1[8]};
+    R Un[6][2];
+    {
+      const R sh = sy - s_up;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        Un[0][j] = f2c[j];
+        Un[1][j] = Pf5[j];
+        Un[2][j] = Pf6[j];
+        Un[3][j] = g2c[j] + W1 * sh;
+        Un[4][j] = Pg5[j] + W2 * sh;
+        Un[5][j] = Pg6[j] + W2 * sh;
+      }
+    }
+    if (r == 0) {
+      const R Exs[2] = {Ex0, Ex1}, Eys[2] = {Ey0, Ey1};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const R wx = mub * Exs[j], wy = mub * Eys[j];
+        const R w15 = R(1.5) * (wx * wx + wy * wy);
+        const R c2 = wy, c5 = wx + wy, c6 = wy - wx;
+        const R n2 = -(g4c[j] + R(2) * W1 * sy) + R(2) * W1 * rho0 * (R(1) + R(4.5) * c2 * c2 - w15);
+        const R n5 = -(g7c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c5 * c5 - w15);
+        const R n6 = -(g8c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c6 * c6 - w15);
+        Uc[0][j] = f4c[j] - wd1;
+        Uc[1][j] = f7c[j] - wd2;
+        Uc[2][j] = f8c[j] - wd2;
+        Uc[3][j] = n2;
+        Uc[4][j] = n5;
+        Uc[5][j] = n6;
+        if (owned && y0 == 0)
+          qin += (((double)n2 - (double)g4c[j]) + ((double)n5 - (double)g7c[j])) + ((double)n6 - (double)g8c[j]);
+      }
+    }
+    R n4[2], n7[2], n8[2];
+    {
+      const R sh = sy - s_dn;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        n4[j] = g4c[j] + W1 * sh;
+        n7[j] = Pg7[j] + W2 * sh;
+        n8[j] = Pg8[j] + W2 * sh;
+      }
+    }
+    if (r > y0) {
+      // row r - 1 is complete
+      const bool ups = !(r - 1 == y0 && push_dn);
+      const long long c = row - P + xc;
+      if (ups && !TSTORE) {
+        if (owned) {
+          Pair<float>::st(fo + c, Hm[0][0], Hm[0][1]);
+          Pair<float>::st(fo + pl + c, Hm[1][0], Hm[1][1]);
+          Pair<float>::st(fo + 2 * pl + c, Um[0][0], Um[0][1]);
+          Pair<float>::st(fo + 3 * pl + c, Hm[2][0], Hm[2][1]);
+          Pair<float>::st(fo + 4 * pl + c, f4c[0], f4c[1]);
+          Pair<float>::st(fo + 5 * pl + c, Um[1][0], Um[1][1]);
+          Pair<float>::st(fo + 6 * pl + c, Um[2][0], Um[2][1]);
+          Pair<float>::st(fo + 7 * pl + c, Pf7[0], Pf7[1]);
+          Pair<float>::st(fo + 8 * pl + c, Pf8[0], Pf8[1]);
+          Pair<float>::st(go + c, Hm[3][0], Hm[3][1]);
+          Pair<float>::st(go + pl + c, Hm[4][0], Hm[4][1]);
+          Pair<float>::st(go + 2 * pl + c, Um[3][0], Um[3][1]);
+          Pair<float>::st(go + 3 * pl + c, Hm[5][0], Hm[5][1]);
+          Pair<float>::st(go + 4 * pl + c, n4[0], n4[1]);
+          Pair<float>::st(go + 5 * pl + c, Um[4][0], Um[4][1]);
+          Pair<float>::st(go + 6 * pl + c, Um[5][0], Um[5][1]);
+          Pair<float>::st(go + 7 * pl + c, n7[0], n7[1]);
+          Pair<float>::st(go + 8 * pl + c, n8[0], n8[1]);
+        }
+      } else if (ups) {
+        // a whole row of the slab: through the out tile and two tensor stores
+        if (out_pending) {
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
+        }
+        if (owned) {
+          float* of = reinterpret_cast<float*>(ws + kOutF) + 2 * (lane - 1);
+          float* og = reinterpret_cast<float*>(ws + kOutG) + 2 * (lane - 1);
+          const R vf[9][2] = {{Hm[0][0], Hm[0][1]}, {Hm[1][0], Hm[1][1]}, {Um[0][0], Um[0][1]},
+                              {Hm[2][0], Hm[2][1]}, {f4c[0], f4c[1]},     {Um[1][0], Um[1][1]},
+                              {Um[2][0], Um[2][1]}, {Pf7[0], Pf7[1]},     {Pf8[0], Pf8[1]}};
+          const R vg[9][2] = {{Hm[3][0], Hm[3][1]}, {Hm[4][0], Hm[4][1]}, {Um[3][0], Um[3][1]},
+                              {Hm[5][0], Hm[5][1]}, {n4[0], n4[1]},       {Um[4][0], Um[4][1]},
+                              {Um[5][0], Um[5][1]}, {n7[0], n7[1]},       {n8[0], n8[1]}};
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            *reinterpret_cast<float2*>(of + i * kSC) = make_float2(vf[i][0], vf[i][1]);
+            *reinterpret_cast<float2*>(og + i * kSC) = make_float2(vg[i][0], vg[i][1]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          fence_async_smem();
+          store3d(&tm.fo, xs, r - 1, smem_u32(ws + kOutF));
+          store3d(&tm.go, xs, r - 1, smem_u32(ws + kOutG));
+          bulk_commit();
+        }
+        out_pending = true;
+      } else if (owned) {
+        Pair<float>::st(fo + c, Hm[0][0], Hm[0][1]);
+        Pair<float>::st(fo + pl + c, Hm[1][0], Hm[1][1]);
+        Pair<float>::st(fo + 3 * pl + c, Hm[2][0], Hm[2][1]);
+        Pair<float>::st(fo + 4 * pl + c, f4c[0], f4c[1]);
+        Pair<float>::st(fo + 7 * pl + c, Pf7[0], Pf7[1]);
+        Pair<float>::st(fo + 8 * pl + c, Pf8[0], Pf8[1]);
+        Pair<float>::st(go + c, Hm[3][0], Hm[3][1]);
+        Pair<float>::st(go + pl + c, Hm[4][0], Hm[4][1]);
+        Pair<float>::st(go + 3 * pl + c, Hm[5][0], Hm[5][1]);
+        Pair<float>::st(go + 4 * pl + c, n4[0], n4[1]);
+        Pair<float>::st(go + 7 * pl + c, n7[0], n7[1]);
+        Pair<float>::st(go + 8 * pl + c, n8[0], n8[1]);
+      }
+      if (owned) {
+        R q[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const R h = (Hm[3][j] + Hm[4][j]) + Hm[5][j];
+          const R d = (n4[j] + n7[j]) + n8[j];
+          const R u = ups ? (Um[3][j] + Um[4][j]) + Um[5][j] : R(0);
+          q[j] = s_dn + ((h + u) + d);
+        }
+        Pair<R>::st(rho_out + c, q[0], q[1]);
+      }
+    }
+    if (r == y0 && push_dn && owned) {
+      const long long c = row - P + xc;
+      Pair<float>::st(fo + 4 * pl + c, f4c[0], f4c[1]);
+      Pair<float>::st(fo + 7 * pl + c, Pf7[0], Pf7[1]);
+      Pair<float>::st(fo + 8 * pl + c, Pf8[0], Pf8[1]);
+      Pair<float>::st(go + 4 * pl + c, n4[0], n4[1]);
+      Pair<float>::st(go + 7 * pl + c, n7[0], n7[1]);
+      Pair<float>::st(go + 8 * pl + c, n8[0], n8[1]);
+      R q[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) q[j] = (n4[j] + n7[j]) + n8[j];
+      Pair<R>::st(rx_dn + (long long)slab * P + xc, q[0], q[1]);
+    }
+    if (r == Ny - 1 && owned) {
+      const bool ups = !(r == y0 && push_dn);
+      const long long c = row + xc;
+      Pair<float>::st(fo + c, f0c[0], f0c[1]);
+      Pair<float>::st(fo + pl + c, Pf1[0], Pf1[1]);
+      Pair<float>::st(fo + 3 * pl + c, Pf3[0], Pf3[1]);
+      Pair<float>::st(fo + 4 * pl + c, f2c[0] + wd1, f2c[1] + wd1);
+      Pair<float>::st(fo + 7 * pl + c, f5c[0] + wd2, f5c[1] + wd2);
+      Pair<float>::st(fo + 8 * pl + c, f6c[0] + wd2, f6c[1] + wd2);
+      Pair<float>::st(go + c, g0c[0], g0c[1]);
+      Pair<float>::st(go + pl + c, Pg1[0], Pg1[1]);
+      Pair<float>::st(go + 3 * pl + c, Pg3[0], Pg3[1]);
+      Pair<float>::st(go + 4 * pl + c, g4c[0], g4c[1]);
+      Pair<float>::st(go + 7 * pl + c, Pg7[0], Pg7[1]);
+      Pair<float>::st(go + 8 * pl + c, Pg8[0], Pg8[1]);
+      if (ups) {
+        Pair<float>::st(fo + 2 * pl + c, Uc[0][0], Uc[0][1]);
+        Pair<float>::st(fo + 5 * pl + c, Uc[1][0], Uc[1][1]);
+        Pair<float>::st(fo + 6 * pl + c, Uc[2][0], Uc[2][1]);
+        Pair<float>::st(go + 2 * pl + c, Uc[3][0], Uc[3][1]);
+        Pair<float>::st(go + 5 * pl + c, Uc[4][0], Uc[4][1]);
+        Pair<float>::st(go + 6 * pl + c, Uc[5][0], Uc[5][1]);
+      }
+      R q[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const R h = (g0c[j] + Pg1[j]) + Pg3[j];
+        const R d = (g4c[j] + Pg7[j]) + Pg8[j];
+        const R u = ups ? (Uc[3][j] + Uc[4][j]) + Uc[5][j] : R(0);
+        q[j] = sy + ((h + u) + d);
+        qout += ((double)g2c[j] + (double)g5c[j]) + (double)g6c[j];
+        qout -= ((double)g4c[j] + (double)g7c[j]) + (double)g8c[j];
+      }
+      Pair<R>::st(rho_out + c, q[0], q[1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      Hm[0][j] = f0c[j];
+      Hm[1][j] = Pf1[j];
+      Hm[2][j] = Pf3[j];
+      Hm[3][j] = g0c[j];
+      Hm[4][j] = Pg1[j];
+      Hm[5][j] = Pg3[j];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        Um[q][j] = Uc[q][j];
+        Uc[q][j] = Un[q][j];
+      }
+      pm[j] = pc[j];
+      pc[j] = pn[j];
+    }
+    sy_last = sy;
+  }
+  cp_async_wait<0>();
+  if (timed_out) {
+    // drain the warp's tensor copies in flight (again bounded): the row it
+    // waited for and the next row, if that was issued; report; end the warp
+    if (lane == 0) {
+      atomicOr(a.err, 2);
+      mbar_wait(mbar0 + 8 * (stuck & 1), (unsigned)(stuck >> 1) & 1u);
+      if (rs + stuck + 1 <= re) mbar_wait(mbar0 + 8 * ((stuck + 1) & 1), (unsigned)((stuck + 1) >> 1) & 1u);
+      bulk_wait0();
+    }
+    __syncwarp();
+    return;
+  }
+  if (push_up && owned) {
+    const bool ups = !(re == y0 && push_dn);
+    const long long c = (long long)re * P + xc;
+    Pair<float>::st(fo + c, Hm[0][0], Hm[0][1]);
+    Pair<float>::st(fo + pl + c, Hm[1][0], Hm[1][1]);
+    Pair<float>::st(fo + 3 * pl + c, Hm[2][0], Hm[2][1]);
+    Pair<float>::st(go + c, Hm[3][0], Hm[3][1]);
+    Pair<float>::st(go + pl + c, Hm[4][0], Hm[4][1]);
+    Pair<float>::st(go + 3 * pl + c, Hm[5][0], Hm[5][1]);
+    if (ups) {
+      Pair<float>::st(fo + 2 * pl + c, Um[0][0], Um[0][1]);
+      Pair<float>::st(fo + 5 * pl + c, Um[1][0], Um[1][1]);
+      Pair<float>::st(fo + 6 * pl + c, Um[2][0], Um[2][1]);
+      Pair<float>::st(go + 2 * pl + c, Um[3][0], Um[3][1]);
+      Pair<float>::st(go + 5 * pl + c, Um[4][0], Um[4][1]);
+      Pair<float>::st(go + 6 * pl + c, Um[5][0], Um[5][1]);
+    }
+    R q[2], e[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const R h = (Hm[3][j] + Hm[4][j]) + Hm[5][j];
+      const R u = ups ? (Um[3][j] + Um[4][j]) + Um[5][j] : R(0);
+      q[j] = sy_last + (h + u);
+      e[j] = (Uc[3][j] + Uc[4][j]) + Uc[5][j];
+    }
+    Pair<R>::st(rho_out + c, q[0], q[1]);
+    const long long cu = c + P;
+    Pair<float>::st(fo + 2 * pl + cu, Uc[0][0], Uc[0][1]);
+    Pair<float>::st(fo + 5 * pl + cu, Uc[1][0], Uc[1][1]);
+    Pair<float>::st(fo + 6 * pl + cu, Uc[2][0], Uc[2][1]);
+    Pair<float>::st(go + 2 * pl + cu, Uc[3][0], Uc[3][1]);
+    Pair<float>::st(go + 5 * pl + cu, Uc[4][0], Uc[4][1]);
+    Pair<float>::st(go + 6 * pl + cu, Uc[5][0], Uc[5][1]);
+    Pair<R>::st(rx_up + (long long)(slab + 1) * P + xc, e[0], e[1]);
+  }
+  if (lane == 0) bulk_wait0();  // the out tile is read and the stores are done before the warp ends
+  __syncwarp();
+  if (bad) atomicOr(a.err, 1);
+  if (y0 == 0) {
+    double v = qin;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.flux_part[strip] = v;
+  }
+  if (y1 == Ny) {
+    double v = qout;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) a.flux_part[ns + strip] = v;
+  }
+}
+
+template <bool TSTORE>
+__global__ void __launch_bounds__(128, 3) k_march_tma(StepArgs a, const __grid_constant__ MarchTma tm) {
+  extern __shared__ __align__(128) unsigned char march_smem[];
+  // tensor-copy destinations want 128-byte aligned shared memory: round the
+  // dynamic allocation's start up (it is requested 128 bytes larger)
+  const unsigned base = tma::smem_u32(march_smem);
+  unsigned char* ws0 = march_smem + (((base + 127u) & ~127u) - base);
+  const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
+  march_tma_body<TSTORE>(a, tm, gw % a.nstrips, gw / a.nstrips, ws0 + (size_t)(threadIdx.x >> 5) * tma::kWarpBytes);
+}
+
+bool march_tma_supported(int Nx) { return Nx >= 128 && Nx <= 2048; }
+
+cudaError_t launch_march_tma(const StepArgs& a, const MarchTma& m, bool tensor_stores, cudaStream_t s) {
+  if (!march_tma_supported(a.Nx) || a.cols_per_lane != 2 || a.ex || !a.rch) return cudaErrorInvalidValue;
+  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
+  const unsigned grid = (unsigned)((warps + 3) / 4);
+  const size_t smem = 4 * tma::kWarpBytes + 128;
+  if (tensor_stores)
+    k_march_tma<true><<<grid, 128, smem, s>>>(a, m);
+  else
+    k_march_tma<false><<<grid, 128, smem, s>>>(a, m);
+  return cudaGetLastError();
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+cudaError_t encode(CUtensorMap* m, const void* base, int rank, int Nx, int Ny, int P, int box_x) {
+  EncodeTiled fn = encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)Nx, (cuuint64_t)Ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * 4 * (cuuint64_t)Ny};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, 1, 9};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t march_tma_encode(MarchTma* m, const void* fin, const void* gin, const void* dphi, void* fout, void* gout,
+                             int Nx, int Ny, int P) {
+  cudaError_t e;
+  if ((e = encode(&m->f, fin, 3, Nx, Ny, P, tma::kLC)) != cudaSuccess) return e;
+  if ((e = encode(&m->g, gin, 3, Nx, Ny, P, tma::kLC)) != cudaSuccess) return e;
+  if ((e = encode(&m->dphi, dphi, 2, Nx, Ny, P, tma::kLC)) != cudaSuccess) return e;
+  if ((e = encode(&m->fo, fout, 3, Nx, Ny, P, tma::kSC)) != cudaSuccess) return e;
+  return encode(&m->go, gout, 3, Nx, Ny, P, tma::kSC);
+}
+
 namespace {
 template <class S, class R, int NST>
 cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
@@ -979,6 +1571,8 @@ int march_strips(int Nx, int cols_per_lane) { return cols_per_lane == 2 ? (Nx + 
 
 cudaError_t march_set_attributes() {
   cudaError_t e;
+  if ((e = allow_smem(k_march_tma<true>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march_tma<false>)) != cudaSuccess) return e;
   if ((e = attrs_t<double, double>()) != cudaSuccess) return e;
   if ((e = attrs_t<double, float>()) != cudaSuccess) return e;
   if ((e = attrs_t<float, float>()) != cudaSuccess) return e;

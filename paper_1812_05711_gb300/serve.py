@@ -43,6 +43,14 @@ class Request:
     amp: list = field(default_factory=list)
     phase: list = field(default_factory=list)
     arrival: float = 0.0  # seconds after the start of the stream
+    # the last `window` steps of the budget are a measurement window: the
+    # collected charge over them (FP64 wall fluxes) is reported per step
+    window: int = 0
+    # start from the final populations of request `after` (which must keep
+    # its state); the request waits until that one has finished
+    after: int | None = None
+    keep_state: bool = False  # report the final populations (f, g)
+    u_ion: float | None = None  # lattice ion drift speed (None: the server's)
 
 
 @dataclass
@@ -54,6 +62,8 @@ class Result:
     steps: int
     diagnostics: dict
     fields: dict | None = None
+    current: float | None = None  # collected charge per step over the window
+    state: tuple | None = None    # (f, g) when keep_state
 
     @property
     def latency(self) -> float:
@@ -78,6 +88,9 @@ class Server:
         self.clock = clock
         self.waiting = collections.deque()
         self.active = {}   # run handle -> (request, run, admitted time)
+        self.windows = {}  # run handle -> q_out at the start of its measurement window
+        self.states = {}   # rid -> final (f, g) of finished requests that others continue from
+        self.done_ids = set()
         self.results = []
         self.t0 = None
         self.ticks = 0
@@ -96,31 +109,73 @@ class Server:
             raise ValueError(f"request {req.rid}: grid {req.Nx}x{req.Ny} outside the server limits")
         if self.batch.admits(req.Nx, req.Ny) == EINVAL:
             raise ValueError(f"request {req.rid}: footprint exceeds the whole HBM budget")
+        if not 0 <= req.window <= req.steps:
+            raise ValueError(f"request {req.rid}: window outside the step budget")
+        if req.after is not None:
+            pred = next((q for q in self.waiting if q.rid == req.after), None)
+            if pred is None and req.after not in self.done_ids:
+                raise ValueError(f"request {req.rid}: continues from unknown request {req.after}")
+            if pred is not None:
+                if (pred.Nx, pred.Ny) != (req.Nx, req.Ny):
+                    raise ValueError(f"request {req.rid}: grid differs from request {req.after}")
+                pred.keep_state = True
         self.waiting.append(req)
 
     def _now(self) -> float:
         return self.clock() - self.t0
 
+    def _ready(self, req: Request, now: float) -> bool:
+        return req.arrival <= now and (req.after is None or req.after in self.done_ids)
+
     def _admit(self, now: float):
-        while self.waiting and len(self.active) < self.max_runs:
-            req = self.waiting[0]
-            if req.arrival > now:
+        # first come, first served among the requests that may start (arrived,
+        # and the request they continue from has finished): the first of those
+        # that does not fit makes the rest wait for a slot or memory
+        for req in list(self.waiting):
+            if len(self.active) >= self.max_runs:
                 break
+            if not self._ready(req, now):
+                if req.arrival > now:
+                    break
+                continue  # waits for its predecessor; later requests may go ahead
             if self.batch.admits(req.Nx, req.Ny) != OK:
-                break  # first come, first served: wait for a slot or memory to free up
-            self.waiting.popleft()
+                break
+            self.waiting.remove(req)
+            u_ion = self.u_ion if req.u_ion is None else req.u_ion
+            cont = req.after is not None
             run = Run(req.Nx, req.Ny, req.T, req.C, req.M, req.Fe, req.Lambda, storage="f32",
-                      u_ion=self.u_ion, amp=req.amp, phase=req.phase)
-            self.batch.add(run, req.steps)  # the batch accounts the run's footprint
+                      u_ion=u_ion, amp=[] if cont else req.amp, phase=[] if cont else req.phase)
+            if cont:
+                run.load(*self.states.pop(req.after))
+            first = req.steps - req.window if req.window else req.steps
+            self.batch.add(run, first)  # the batch accounts the run's footprint
             self.active[run.handle] = (req, run, now)
+            if req.window and first == 0:
+                self.windows[run.handle] = run.diagnostics()["q_out"]
+                self.batch.remove(run)
+                self.batch.add(run, req.window)
 
     def _retire(self, now: float):
         for h in [h for h, (req, run, _) in self.active.items() if self.batch.remaining(run) == 0]:
-            req, run, t_adm = self.active.pop(h)
+            req, run, t_adm = self.active[h]
+            if req.window and h not in self.windows:
+                # the budget before the measurement window is used up: note the
+                # collected charge so far and give the run its window (it stays
+                # resident in its slot)
+                self.windows[h] = run.diagnostics()["q_out"]
+                self.batch.remove(run)
+                self.batch.add(run, req.window)
+                continue
+            del self.active[h]
             self.batch.remove(run)
             diag = run.diagnostics()
             flds = run.fields(self.keep_fields) if self.keep_fields else None
-            self.results.append(Result(req.rid, req.arrival, t_adm, now, req.steps, diag, flds))
+            cur = (diag["q_out"] - self.windows.pop(h)) / req.window if req.window else None
+            st = run.save() if req.keep_state else None
+            if st is not None:
+                self.states[req.rid] = st
+            self.results.append(Result(req.rid, req.arrival, t_adm, now, req.steps, diag, flds, cur, st))
+            self.done_ids.add(req.rid)
             run.close()
 
     # --------------------------------------------------------------- loop

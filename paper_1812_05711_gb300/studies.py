@@ -89,3 +89,39 @@ def nusselt_sweep(T_values, Nx=64, Ny=52, u_ion=5e-3, steps=200000, window=40000
         state = r.save()
         r.close()
     return {"I_h": I_h, "lower": lower, "upper": upper}
+
+
+def nusselt_sweep_served(T_values, Nx=64, Ny=52, u_ion=5e-3, steps=200000, window=40000, amp_small=1e-3,
+                         amp_large=0.3, C=10.0, M=10.0, Fe=4000.0, Lambda=0.25, tick_steps=2000,
+                         hbm_budget=8 << 30):
+    """The Ne(T) sweep of :func:`nusselt_sweep` (Sec. V.2, FIG. 3) driven
+    through the continuous-batching server: every point is a request whose
+    last `window` steps measure the collected current.  The reference
+    (hydrostatic) run and the lower branch are independent requests, so they
+    advance together in the batch; the upper branch is a chain in which each
+    request starts from the previous (higher) T's final populations and is
+    admitted as soon as that one finishes, beside the runs still in flight.
+    FP32 storage and compute (the batch's kind of run).  Returns
+    {"I_h", "lower", "upper", "results"} as nusselt_sweep does."""
+    from .serve import Request, Server
+
+    Ts = sorted(T_values)
+    reqs = [Request(0, Nx, Ny, Ts[-1], C, M, Fe, Lambda, steps, window=window, u_ion=u_ion)]
+    for k, T in enumerate(Ts):
+        reqs.append(Request(1 + k, Nx, Ny, T, C, M, Fe, Lambda, steps, [amp_small], [0.0], window=window,
+                            u_ion=u_ion))
+    base = 1 + len(Ts)
+    for k, T in enumerate(reversed(Ts)):
+        first = k == 0
+        reqs.append(Request(base + k, Nx, Ny, T, C, M, Fe, Lambda, steps, [amp_large] if first else [],
+                            [0.0] if first else [], window=window, after=None if first else base + k - 1,
+                            u_ion=u_ion))
+    srv = Server(hbm_budget, max_runs=len(reqs), tick_steps=tick_steps, max_nx=Nx, max_ny=Ny, u_ion=u_ion)
+    try:
+        res = {r.rid: r for r in srv.serve(reqs, realtime=False)}
+    finally:
+        srv.close()
+    I_h = res[0].current
+    lower = [(T, res[1 + k].current / I_h) for k, T in enumerate(Ts)]
+    upper = [(T, res[base + k].current / I_h) for k, T in enumerate(reversed(Ts))]
+    return {"I_h": I_h, "lower": lower, "upper": upper, "results": res}

@@ -307,3 +307,82 @@ def test_slab_heights_fp64_parity(slab):
     assert max(e.values()) <= 1e-12, (slab, e)
     F = o.fields(s)
     assert run.diagnostics()["charge"] == pytest.approx(F["rho_c"].sum(), rel=1e-13)
+
+
+@gpu
+def test_c1_plain_fp64_10000_steps_vs_oracle():
+    """The plain FP64 configuration run to its full length: 128 x 104,
+    T = 200, 10,000 coupled steps on the GPU and in the oracle.  Every field
+    within 1e-12 (scaled max norm) at the end, and the exponential rate of
+    max|u_y| over the run (least-squares slope of its log over the second
+    half, sampled every 100 steps) within 1 % of the oracle's (measured
+    3.4e-13 and 5e-10 relative)."""
+    w = wl.plain_fp64_channel()
+    ehd, p, s, run = _pair(w)
+    d = o.step(s, 10000, diag=True)  # row t: the state at step t
+    t = np.arange(100, 10000, 100)
+    a = []
+    for _ in range(t.size):
+        run.step(100)
+        a.append(run.diagnostics()["max_uy"])
+    run.step(100)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, e
+
+    def rate(amp):
+        h = amp.size // 2
+        return float(np.polyfit(t[h:], np.log(amp[h:]), 1)[0])
+
+    so, sg = rate(d[t, 5]), rate(np.array(a))
+    assert abs(sg - so) <= 0.01 * abs(so), (so, sg)
+
+
+@gpu
+def test_c2_fp32_vs_gpu_fp64_2000_steps_2048x1680():
+    """The large configuration at full length: 2048 x 1680, FP32 compute on
+    shifted FP32 storage against the plain FP64 GPU path (itself pinned to
+    the oracle above) after 2,000 steps, every field within 2e-5 of its scale
+    (measured 2.1e-7, rho_c)."""
+    ehd = _ehd()
+    w = wl.large_channel()
+    F = {}
+    par = None
+    for st in ("f64", "f32"):
+        run = ehd.Run(*w.args(), storage=st, amp=w.amp, phase=w.phase)
+        run.step(2000)
+        F[st] = run.fields()
+        par = run.params()
+        run.close()
+    p = o.setup(*w.args())
+    assert par["rho0"] == pytest.approx(p.rho0, rel=1e-14)
+    e = _errors(p, F["f32"], F["f64"])
+    assert max(e.values()) <= 2e-5, e
+
+
+@gpu
+@pytest.mark.parametrize("Nx,Ny,slab", [(128, 104, 0), (256, 37, 5), (512, 416, 0), (2048, 64, 17), (1024, 9, 4)])
+def test_tma_march_equals_cp_async_march(Nx, Ny, slab):
+    """The march form's TMA staging (tensor copies of whole row segments,
+    tensor stores of completed rows, wrap-around halo pairs fetched by their
+    own lanes) computes bit for bit what the per-lane cp.async form does,
+    including ragged last strips, slab boundaries and one-wave slab sizes."""
+    ehd = _ehd()
+    a, ph = wl.roll(31, 1e-2)
+    runs = []
+    for tma in (0, 1, 2):
+        r = ehd.Run(Nx, Ny, 190.0, 10, 10, 4000, 0.25, storage="f32", u_ion=5e-3, amp=a, phase=ph)
+        ehd.ehd_tune(r.handle, "march_tma", tma)
+        if slab:
+            ehd.ehd_tune(r.handle, "slab_rows", slab)
+        assert ehd.ehd_tune_get(r.handle, "march_tma") == tma
+        r.step(33)
+        runs.append(r)
+    fa, ga = runs[0].save()
+    da = runs[0].diagnostics()
+    for r in runs[1:]:
+        fb, gb = r.save()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+        db = r.diagnostics()
+        assert da["q_in"] == db["q_in"] and da["q_out"] == db["q_out"]
+    for r in runs:
+        r.close()

@@ -84,3 +84,48 @@ def test_subcritical_hysteresis_64x52():
     assert I_upper / I_h > 1.1
     I_dead, _ = ne(95.0, state=conv)
     assert abs(I_dead / I_h - 1.0) < 1e-3
+
+
+@gpu
+def test_served_nusselt_points_vs_oracle_64x52():
+    """Sec. V.2 sweep points driven through the continuous-batching server
+    (FP32, one batch): the hydrostatic reference, a lower-branch point (a
+    small roll) and two upper-branch points (a finite-amplitude roll at
+    T = 180, then T = 170 continued from its final populations).  Each
+    request's collected current over its measurement window (FP64 wall
+    fluxes) matches the oracle's over the same steps, and so does the
+    electric Nusselt number Ne = I / I_h."""
+    _ehd()
+    from paper_1812_05711_gb300.serve import Request, Server
+    Nx, Ny, u_ion, steps, window = 64, 52, 5e-3, 12000, 4000
+    reqs = [Request(0, Nx, Ny, 180.0, 10, 10, 4000, 0.25, steps, window=window, u_ion=u_ion),
+            Request(1, Nx, Ny, 180.0, 10, 10, 4000, 0.25, steps, [1e-3], [0.0], window=window, u_ion=u_ion),
+            Request(2, Nx, Ny, 180.0, 10, 10, 4000, 0.25, steps, [0.3], [0.0], window=window, u_ion=u_ion),
+            Request(3, Nx, Ny, 170.0, 10, 10, 4000, 0.25, 2 * window, window=window, after=2, u_ion=u_ion)]
+    srv = Server(1 << 30, max_runs=4, tick_steps=1000, max_nx=Nx, max_ny=Ny, u_ion=u_ion)
+    try:
+        res = {r.rid: r for r in srv.serve(reqs, realtime=False)}
+    finally:
+        srv.close()
+
+    def oracle_current(T, amp, n, state=None):
+        p = o.setup(Nx, Ny, T, 10, 10, 4000, 0.25, u_ion=u_ion)
+        s = o.init_state(p, amp, [0.0] * len(amp)) if state is None else o.state_from(p, *state)
+        d = o.step(s, n, diag=True)
+        return d[n - window:, 3].sum() / window, (s.f, s.g)
+
+    n_threads = o.use_threads()
+    try:
+        I_h, _ = oracle_current(180.0, [], steps)
+        I_1, _ = oracle_current(180.0, [1e-3], steps)
+        I_2, st = oracle_current(180.0, [0.3], steps)
+        I_3, _ = oracle_current(170.0, [], 2 * window, state=st)
+    finally:
+        o.use_one_thread()
+    assert n_threads >= 0
+    for rid, ref in ((0, I_h), (1, I_1), (2, I_2), (3, I_3)):
+        assert res[rid].current == pytest.approx(ref, rel=1e-4), (rid, res[rid].current, ref)
+        assert res[rid].current / res[0].current == pytest.approx(ref / I_h, rel=2e-4), rid
+    # the finite-amplitude roll already carries more charge than the
+    # hydrostatic state, and the continuation keeps convecting
+    assert res[2].current / res[0].current > 1.001 and res[3].current / res[0].current > 1.001

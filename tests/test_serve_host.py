@@ -18,9 +18,18 @@ class FakeRun:
         self.handle = FakeRun._next
         self.Nx, self.Ny = Nx, Ny
         self.closed = False
+        self.steps_done = 0
+        self.loaded = None
 
     def diagnostics(self):
-        return {"mass": float(self.Nx * self.Ny)}
+        # collected charge grows by 2 per step: the window's current is 2
+        return {"mass": float(self.Nx * self.Ny), "q_out": 2.0 * self.steps_done}
+
+    def save(self):
+        return ("f", self.handle), ("g", self.handle)
+
+    def load(self, f, g):
+        self.loaded = (f, g)
 
     def fields(self, names):
         return {}
@@ -54,6 +63,8 @@ class FakeBatch:
         assert self.admits(run.Nx, run.Ny) == 0
         self.left[run.handle] = steps
         self.bytes[run.handle] = run.Nx * run.Ny
+        self.runs = getattr(self, "runs", {})
+        self.runs[run.handle] = run
 
     def remaining(self, run):
         return self.left[run.handle]
@@ -65,7 +76,9 @@ class FakeBatch:
     def tick(self, k):
         self.ticks.append(sorted(self.left))
         for h in self.left:
-            self.left[h] = max(0, self.left[h] - k)
+            n = min(k, self.left[h])
+            self.runs[h].steps_done += n
+            self.left[h] -= n
 
     def sync(self):
         pass
@@ -138,3 +151,24 @@ def test_summary_percentiles():
     assert s["runs"] == 100 and s["makespan_s"] == 100.0
     assert s["p50_s"] == pytest.approx(50.5) and s["p99_s"] == pytest.approx(99.01)
     assert s["glups"] == pytest.approx(100 * 1000 * 10 / 100.0 / 1e9)
+
+
+def test_measurement_window_and_continuation(fakes):
+    """A request's last `window` steps measure the collected current (the run
+    stays in its slot between the two parts), and a request that continues
+    from another starts from that one's final populations once it is done,
+    while independent requests go ahead of it."""
+    srv = fakes.Server(hbm_budget=10 ** 9, max_runs=8, tick_steps=4, max_nx=128, max_ny=128, clock=Clock())
+    a = fakes.Request(0, 64, 64, 200.0, 10.0, 10.0, 4000.0, 0.25, 12, window=4)
+    b = fakes.Request(1, 64, 64, 190.0, 10.0, 10.0, 4000.0, 0.25, 8, window=8, after=0)
+    c = fakes.Request(2, 64, 64, 180.0, 10.0, 10.0, 4000.0, 0.25, 4)
+    res = {r.rid: r for r in srv.serve([a, b, c], realtime=False)}
+    assert res[0].current == pytest.approx(2.0) and res[1].current == pytest.approx(2.0)
+    assert res[2].current is None
+    assert res[1].admitted >= res[0].done      # waited for its predecessor
+    assert res[2].admitted < res[0].done       # independent: went ahead
+    assert res[0].state is not None            # kept for the continuation
+    first_tick = srv.batch.ticks[0]
+    assert len(first_tick) == 2                # a and c together, b waiting
+    with pytest.raises(ValueError):
+        srv.submit(fakes.Request(9, 64, 64, 1.0, 1.0, 1.0, 1.0, 0.25, 4, after=77))
