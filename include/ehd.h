@@ -183,7 +183,8 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * stores; 1, each row of a strip staged by tensor copies
  * (cp.async.bulk.tensor, 9 planes per copy) with mbarrier completion;
  * 2, the same and completed rows written by tensor stores from a
- * shared-memory tile; the same results bit for bit).
+ * shared-memory tile; 3, tensor copies two rows ahead (three stages); the
+ * same results bit for bit).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1

@@ -331,7 +331,7 @@ bool tma_form(const ehd_run* r) {
   return r->march_tma && r->tma_ok && r->cols_per_lane == 2 && !r->ex_spectral && r->step_kernel == 0;
 }
 cudaError_t launch_march_run(const ehd_run* r, const StepArgs& sa, int cur) {
-  if (tma_form(r)) return launch_march_tma(sa, r->tma[cur], r->march_tma == 2, r->stream);
+  if (tma_form(r)) return launch_march_tma(sa, r->tma[cur], r->march_tma, r->stream);
   return launch_march(sa, r->storage, r->real_f64, r->stream);
 }
 
@@ -828,7 +828,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       if (r->step_kernel == 0) r->nxb = r->nstrips;
       break;
     case EHD_TUNE_MARCH_TMA:
-      if (value < 0 || value > 2) return fail(EHD_EINVAL, "TMA march must be 0, 1 or 2");
+      if (value < 0 || value > 3) return fail(EHD_EINVAL, "TMA march must be 0, 1, 2 or 3");
       if (value != 0 && !r->tma_ok)
         return fail(EHD_EINVAL, "the TMA march needs FP32 storage and compute and 128 <= Nx <= 2048");
       r->march_tma = value;

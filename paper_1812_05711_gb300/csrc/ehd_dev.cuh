@@ -259,7 +259,7 @@ struct MarchTma {
 cudaError_t march_tma_encode(MarchTma* m, const void* fin, const void* gin, const void* dphi, void* fout, void* gout,
                              int Nx, int Ny, int P);
 bool march_tma_supported(int Nx);
-cudaError_t launch_march_tma(const StepArgs& a, const MarchTma& m, bool tensor_stores, cudaStream_t s);
+cudaError_t launch_march_tma(const StepArgs& a, const MarchTma& m, int form, cudaStream_t s);
 
 // Launchers (defined in the .cu files); storage: 0 F64, 1 F32, 2 BF16, 3 F16;
 // real_f64: compute type (true = double).

@@ -918,10 +918,15 @@ constexpr int kStG = 2560;               // [9][68] g
 constexpr int kStP = 5120;               // [68] potential fluctuation of the next row
 constexpr int kStW = 5504;               // [20][2] the wrap lane's own pair (18 populations, potential)
 constexpr int kStage = 5760;             // bytes per stage
-constexpr int kOutF = 2 * kStage;        // [9][60] f of the completed row
-constexpr int kOutG = kOutF + 2176;      // [9][60] g
-constexpr int kMbar = kOutF + 2 * 2176;  // two mbarriers
-constexpr int kWarpBytes = kMbar + 128;  // 16000
+// layout for NST stages, with (TSTORE) or without the out tile: stages, out
+// tile [9][60] f then g, the stages' mbarriers
+template <int NST, bool TSTORE>
+struct Layout {
+  static constexpr int kOutF = NST * kStage;
+  static constexpr int kOutG = kOutF + 2176;
+  static constexpr int kMbar = kOutF + (TSTORE ? 2 * 2176 : 0);
+  static constexpr int kWarpBytes = kMbar + 128;
+};
 constexpr unsigned kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -970,10 +975,12 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 }  // namespace tma
 
-template <bool TSTORE>
+template <int NST, bool TSTORE>
 __device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma& tm, int strip, int slab,
                                                unsigned char* ws) {
   using namespace tma;
+  using L = Layout<NST, TSTORE>;
+  constexpr int kOutF = L::kOutF, kOutG = L::kOutG, kMbar = L::kMbar;
   using R = float;
   const int lane = threadIdx.x & 31;
   const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
@@ -1012,8 +1019,8 @@ __device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma
 
   const unsigned mbar0 = smem_u32(ws + kMbar);
   if (lane == 0) {
-    mbar_init(mbar0);
-    mbar_init(mbar0 + 8);
+#pragma unroll
+    for (int k = 0; k < NST; ++k) mbar_init(mbar0 + 8 * k);
     fence_mbar_init();
   }
   __syncwarp();
@@ -1066,13 +1073,17 @@ __device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma
   bool out_pending = false;  // a tensor store of the out tile may still be reading it
   int stuck = -1;            // iteration whose wait gave up
 
-  issue(rs, 0);
+#pragma unroll
+  for (int k = 0; k < NST - 1; ++k) {
+    if (rs + k <= re) issue(rs + k, k);
+    else cp_async_commit();
+  }
   for (int r = rs; r <= re; ++r) {
     const long long row = (long long)r * P;
     const int kk = r - rs;
-    const int stg = kk & 1;
+    const int stg = kk % NST;
     __syncwarp();  // every lane has finished reading the stage about to be refilled
-    if (r + 1 <= re) issue(r + 1, stg ^ 1);
+    if (r + NST - 1 <= re) issue(r + NST - 1, (kk + NST - 1) % NST);
     else cp_async_commit();  // keep one group per iteration
     const R Ebr = Eb_n, sy = sy_n, s_up = sup_n, s_dn = sdn_n;
     if (r + 1 <= re) {
@@ -1081,12 +1092,12 @@ __device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma
       sup_n = (r + 2 < Ny) ? rch[r + 2] : sy_n;
       sdn_n = rch[r];
     }
-    if (!mbar_wait(mbar0 + 8 * stg, (unsigned)(kk >> 1) & 1u)) {
+    if (!mbar_wait(mbar0 + 8 * stg, (unsigned)(kk / NST) & 1u)) {
       timed_out = true;
       stuck = kk;
       break;
     }
-    cp_async_wait<1>();  // the wrap lane's copies of row r (row r + 1's may be pending)
+    cp_async_wait<NST - 1>();  // the wrap lane's copies of row r (later rows' may be pending)
     const unsigned char* st = ws + stg * kStage;
     R F[9][2], G[9][2];
     R pn[2];
@@ -1352,8 +1363,7 @@ __device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma
     // waited for and the next row, if that was issued; report; end the warp
     if (lane == 0) {
       atomicOr(a.err, 2);
-      mbar_wait(mbar0 + 8 * (stuck & 1), (unsigned)(stuck >> 1) & 1u);
-      if (rs + stuck + 1 <= re) mbar_wait(mbar0 + 8 * ((stuck + 1) & 1), (unsigned)((stuck + 1) >> 1) & 1u);
+      for (int k = stuck; k < stuck + NST && rs + k <= re; ++k) mbar_wait(mbar0 + 8 * (k % NST), (unsigned)(k / NST) & 1u);
       bulk_wait0();
     }
     __syncwarp();
@@ -1409,7 +1419,7 @@ __device__ __forceinline__ void march_tma_body(const StepArgs& a, const MarchTma
   }
 }
 
-template <bool TSTORE>
+template <int NST, bool TSTORE>
 __global__ void __launch_bounds__(128, 3) k_march_tma(StepArgs a, const __grid_constant__ MarchTma tm) {
   extern __shared__ __align__(128) unsigned char march_smem[];
   // tensor-copy destinations want 128-byte aligned shared memory: round the
@@ -1417,20 +1427,22 @@ __global__ void __launch_bounds__(128, 3) k_march_tma(StepArgs a, const __grid_c
   const unsigned base = tma::smem_u32(march_smem);
   unsigned char* ws0 = march_smem + (((base + 127u) & ~127u) - base);
   const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
-  march_tma_body<TSTORE>(a, tm, gw % a.nstrips, gw / a.nstrips, ws0 + (size_t)(threadIdx.x >> 5) * tma::kWarpBytes);
+  march_tma_body<NST, TSTORE>(a, tm, gw % a.nstrips, gw / a.nstrips,
+                              ws0 + (size_t)(threadIdx.x >> 5) * tma::Layout<NST, TSTORE>::kWarpBytes);
 }
 
 bool march_tma_supported(int Nx) { return Nx >= 128 && Nx <= 2048; }
 
-cudaError_t launch_march_tma(const StepArgs& a, const MarchTma& m, bool tensor_stores, cudaStream_t s) {
+cudaError_t launch_march_tma(const StepArgs& a, const MarchTma& m, int form, cudaStream_t s) {
   if (!march_tma_supported(a.Nx) || a.cols_per_lane != 2 || a.ex || !a.rch) return cudaErrorInvalidValue;
   const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
   const unsigned grid = (unsigned)((warps + 3) / 4);
-  const size_t smem = 4 * tma::kWarpBytes + 128;
-  if (tensor_stores)
-    k_march_tma<true><<<grid, 128, smem, s>>>(a, m);
-  else
-    k_march_tma<false><<<grid, 128, smem, s>>>(a, m);
+  switch (form) {
+    case 1: k_march_tma<2, false><<<grid, 128, 4 * tma::Layout<2, false>::kWarpBytes + 128, s>>>(a, m); break;
+    case 2: k_march_tma<2, true><<<grid, 128, 4 * tma::Layout<2, true>::kWarpBytes + 128, s>>>(a, m); break;
+    case 3: k_march_tma<3, false><<<grid, 128, 4 * tma::Layout<3, false>::kWarpBytes + 128, s>>>(a, m); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -1571,8 +1583,9 @@ int march_strips(int Nx, int cols_per_lane) { return cols_per_lane == 2 ? (Nx + 
 
 cudaError_t march_set_attributes() {
   cudaError_t e;
-  if ((e = allow_smem(k_march_tma<true>)) != cudaSuccess) return e;
-  if ((e = allow_smem(k_march_tma<false>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march_tma<2, true>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march_tma<2, false>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_march_tma<3, false>)) != cudaSuccess) return e;
   if ((e = attrs_t<double, double>()) != cudaSuccess) return e;
   if ((e = attrs_t<double, float>()) != cudaSuccess) return e;
   if ((e = attrs_t<float, float>()) != cudaSuccess) return e;

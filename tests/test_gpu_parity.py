@@ -369,7 +369,7 @@ def test_tma_march_equals_cp_async_march(Nx, Ny, slab):
     ehd = _ehd()
     a, ph = wl.roll(31, 1e-2)
     runs = []
-    for tma in (0, 1, 2):
+    for tma in (0, 1, 2, 3):
         r = ehd.Run(Nx, Ny, 190.0, 10, 10, 4000, 0.25, storage="f32", u_ion=5e-3, amp=a, phase=ph)
         ehd.ehd_tune(r.handle, "march_tma", tma)
         if slab:

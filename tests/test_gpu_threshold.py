@@ -57,11 +57,12 @@ def test_growth_rate_matches_oracle_32x26(storage):
     """32 x 26 (aspect 1.23), C = 10, M = 10, Fe = 4000, 40,000 steps:
     sigma(T = 180) > 0 and sigma(T = 150) < 0, each within 1 % of the
     oracle's.  FP64 runs the configuration's roll amplitude A = 1e-3 (times
-    the ion drift speed).  FP32 storage rounds populations to about 1e-10,
-    which is 1e-4 of a roll of A = 1e-3 per step and shifts its measured
-    rate by 1 % (T = 180) to 12 % (T = 150, decaying); FP32 is therefore
-    compared at A = 5e-2, where the roll is well above that rounding and the
-    rate difference measured 0.02 % (A = 1e-2, T = 180)."""
+    the ion drift speed).  FP32 is compared at A = 5e-2: at A = 1e-3 its
+    rate is off by 10-15 % at T = 150 (1 % at T = 180), because FP32 does not
+    resolve the charge populations' odd non-equilibrium part, which at
+    Fe = 4000 flips sign every step (omega_g- close to 2) with an amplitude
+    far above the diffusive flux it carries; a larger roll perturbs that
+    flux by more than the rounding does."""
     ehd = _ehd()
     steps, every = 40000, 200
     A = 1e-3 if storage == "f64" else 5e-2
