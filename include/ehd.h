@@ -110,6 +110,22 @@ typedef struct {
                        Needs the march form with 2 columns per lane and ring
                        depth 2; refused in batches.  The run then holds one
                        more [Ny][P] array beyond ehd_footprint. */
+  int perturbation; /* FP32 compute only: 0 (default) stores the charge
+                       populations shifted by w_i rho_c,hydrostatic(y); 1
+                       advances an x-uniform base state of both population
+                       sets exactly, in FP64 (its collision, streaming in y,
+                       wall rules and mean-mode potential, on a second
+                       stream), and stores and collides only the charge
+                       populations' departure from it in FP32, with the
+                       departure of the equilibrium written out term by term.
+                       FP32 then resolves the charge populations' odd
+                       non-equilibrium part, which it otherwise does not at
+                       Fe of order 10^3 (omega_g- close to 2), so that growth
+                       rates of small rolls match the FP64 oracle.  Needs the
+                       march form (two columns per lane, cp.async staging) and
+                       central-difference E_x.  Batches take such runs
+                       beside plain ones (their base states advance on the
+                       batch's second stream). */
 } ehd_options;
 
 /* Fill *opt with the defaults above. */

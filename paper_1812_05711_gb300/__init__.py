@@ -55,6 +55,7 @@ class Options(ctypes.Structure):
         ("step_kernel", ctypes.c_int),
         ("x_symbol", ctypes.c_int),
         ("ex_spectral", ctypes.c_int),
+        ("perturbation", ctypes.c_int),
     ]
 
 
@@ -271,7 +272,8 @@ def ehd_last_error() -> str:
 
 # ------------------------------------------------------------ convenience
 def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
-                 amp=(), phase=(), stream=None, step_kernel=-1, x_symbol=0, ex_spectral=0) -> Options:
+                 amp=(), phase=(), stream=None, step_kernel=-1, x_symbol=0, ex_spectral=0,
+                 perturbation=0) -> Options:
     o = ehd_default_options()
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if compute is None:
@@ -291,6 +293,7 @@ def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mo
     o.step_kernel = int(step_kernel)
     o.x_symbol = int(x_symbol)
     o.ex_spectral = int(ex_spectral)
+    o.perturbation = int(perturbation)
     return o
 
 
@@ -300,11 +303,13 @@ class Run:
     ``storage``: "f64" (with FP64 compute: the plain double-precision path),
     "f32", "bf16", "f16" (FP32 compute on shifted populations); ``compute``
     may force "f32" on FP64 storage.  ``amp``/``phase``: Eq. 29 x-modes.
+    ``perturbation=1`` (FP32 compute): the charge populations are stored and
+    collided as departures from an x-uniform base state advanced in FP64.
     """
 
     def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
                  u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=-1,
-                 x_symbol=0, ex_spectral=0):
+                 x_symbol=0, ex_spectral=0, perturbation=0):
         self.Nx, self.Ny = int(Nx), int(Ny)
         self._stream_obj = None
         if stream is None and torch_stream:
@@ -312,7 +317,7 @@ class Run:
             self._stream_obj = torch.cuda.Stream()
             stream = self._stream_obj.cuda_stream
         opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel, x_symbol,
-                           ex_spectral)
+                           ex_spectral, perturbation)
         self.handle = ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt)
 
     # lifecycle

@@ -114,6 +114,16 @@ struct ehd_run {
   MarchTma tma[2] = {};
   bool tma_ok = false;
   int march_tma = 0;
+  // perturbation form: FP64 x-uniform base state ([9][Ny] per set, one per
+  // buffer parity), its potential, field and the march table per parity
+  int pert = 0;
+  double* bf[2] = {nullptr, nullptr};
+  double* bg[2] = {nullptr, nullptr};
+  double* EBd = nullptr;
+  double* phiB = nullptr;
+  double* brhs = nullptr;
+  float* btab[2] = {nullptr, nullptr};
+  cudaEvent_t ev_step = nullptr;
 };
 
 struct ehd_batch {
@@ -123,8 +133,9 @@ struct ehd_batch {
   std::vector<size_t> member_bytes;
   cudaStream_t stream = nullptr, side = nullptr;
   bool own_stream = false;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_upload = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_upload = nullptr, ev_step = nullptr;
   std::vector<ehd_run*> members;
+  int npert = 0;              // members in the perturbation form
   std::vector<long> remaining;
   int slab_rows = 4;
   // device tables and their pinned host staging copies
@@ -143,7 +154,7 @@ struct ehd_batch {
   bool dirty = true;
   int grid_march = 0, grid_rows = 0, grid_tiles = 0, grid_mean = 0, modes_smem = 0;
   int slab_rows_fixed = 0;  // 0: choose from the membership
-  std::map<int, cudaGraphExec_t> graphs;  // by tick length
+  std::map<int, cudaGraphExec_t> graphs;  // by 2 x tick length + (any member in the perturbation form)
 };
 
 namespace {
@@ -250,6 +261,7 @@ StepArgs step_args(const ehd_run* r, int cur) {
   a.ring_depth = r->ring_depth;
   a.cols_per_lane = r->cols_per_lane;
   a.pdl = r->pdl;
+  a.base_tab = r->pert ? r->btab[cur] : nullptr;
   return a;
 }
 
@@ -276,7 +288,7 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.dphi = r->dphi;
   a.phibar = r->phibar;
   a.Ebar = r->Ebar;
-  a.phi0 = r->phi0;
+  a.phi0 = r->pert ? 0.0 : r->phi0;  // perturbation form: the base carries the wall potentials
   a.wall_mode = r->wall_mode;
   a.flux_part = with_flux ? r->flux_part : nullptr;
   a.nflux = r->nxb;
@@ -297,11 +309,58 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   return a;
 }
 
-// Charge plane of buffer `cur`, then phi (the Poisson solve).
+// Perturbation form: the potential, field and march table of the base state
+// of buffer `cur`, and one FP64 step of the base from buffer `cur`.
+BasePoissonArgs base_poisson_args(const ehd_run* r, int cur) {
+  BasePoissonArgs b{};
+  b.Nx = r->Nx;
+  b.Ny = r->Ny;
+  b.wall_mode = r->wall_mode;
+  b.f = r->bf[cur];
+  b.g = r->bg[cur];
+  b.eps = r->eps;
+  b.phi0 = r->phi0;
+  b.rhs = r->brhs;
+  b.phiB = r->phiB;
+  b.EB = r->EBd;
+  b.table = r->btab[cur];
+  return b;
+}
+BaseArgs base_step_args(const ehd_run* r, int cur) {
+  BaseArgs b{};
+  b.Nx = r->Nx;
+  b.Ny = r->Ny;
+  b.fin = r->bf[cur];
+  b.gin = r->bg[cur];
+  b.fout = r->bf[1 - cur];
+  b.gout = r->bg[1 - cur];
+  b.EB = r->EBd;
+  b.wp = 1.0 / r->tau_p;
+  b.wm = 1.0 / r->tau_m;
+  b.gwp = 1.0 / r->taug_p;
+  b.gwm = 1.0 / r->taug_m;
+  b.mub = r->mub;
+  b.rho0 = r->rho0;
+  b.flux_acc = r->small;
+  return b;
+}
+// the base step from buffer `cur` and the potential of the result, on the
+// side stream after the point the main stream has reached
+cudaError_t enqueue_base(ehd_run* r, int cur) {
+  cudaError_t e = cudaEventRecord(r->ev_step, r->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(r->side, r->ev_step, 0);
+  if (e == cudaSuccess) e = launch_base_step(base_step_args(r, cur), r->side);
+  if (e == cudaSuccess) e = launch_base_poisson(base_poisson_args(r, 1 - cur), r->side);
+  return e;
+}
+
+// Charge plane of buffer `cur`, then phi (the Poisson solve).  Perturbation
+// form: the departure's charge and potential, and the base's potential.
 cudaError_t enqueue_poisson(ehd_run* r, int cur, bool with_flux) {
   cudaError_t e = launch_rhoc(r->g[cur], (long long)r->Ny * r->P, r->storage, r->real_f64, r->Nx, r->Ny, r->P,
-                              r->rch, r->rhoc, r->stream);
+                              r->pert ? nullptr : r->rch, r->rhoc, r->stream);
   if (e != cudaSuccess) return e;
+  if (r->pert && (e = launch_base_poisson(base_poisson_args(r, cur), r->stream)) != cudaSuccess) return e;
   return launch_poisson(poisson_args(r, with_flux), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
 }
 
@@ -322,6 +381,9 @@ FieldArgs field_args(const ehd_run* r) {
   a.ex = r->exs;
   a.mub = r->mub;
   a.wall_mode = r->wall_mode;
+  a.base_g = r->pert ? r->bg[r->cur] : nullptr;
+  a.phiB = r->pert ? r->phiB : nullptr;
+  a.EB = r->pert ? r->EBd : nullptr;
   return a;
 }
 
@@ -341,6 +403,10 @@ cudaError_t launch_march_run(const ehd_run* r, const StepArgs& sa, int cur) {
 // the node-parallel form needs the separate charge-moment kernel.
 cudaError_t enqueue_step(ehd_run* r, int cur) {
   const StepArgs sa = step_args(r, cur);
+  if (r->pert) {
+    cudaError_t e = enqueue_base(r, cur);
+    if (e != cudaSuccess) return e;
+  }
   if (r->step_kernel == 0) {
     cudaError_t e = launch_march_run(r, sa, cur);
     if (e != cudaSuccess) return e;
@@ -390,6 +456,7 @@ ehd_status destroy_quiet(ehd_run* r) {
   if (r->side) cudaStreamSynchronize(r->side);
   if (r->ev_fork) cudaEventDestroy(r->ev_fork);
   if (r->ev_join) cudaEventDestroy(r->ev_join);
+  if (r->ev_step) cudaEventDestroy(r->ev_step);
   if (r->side) cudaStreamDestroy(r->side);
   std::vector<void*> bl = r->blocks;
   for (void* p : bl) run_free(r, p);
@@ -419,6 +486,7 @@ void ehd_default_options(ehd_options* o) {
   o->wall_mode = 0;
   o->n_modes = 0;
   o->stream = nullptr;
+  o->perturbation = 0;
 }
 
 const char* ehd_last_error(void) { return g_err.c_str(); }
@@ -451,7 +519,9 @@ ehd_status ehd_footprint(int Nx, int Ny, int storage, size_t* bytes) {
       (ny / 4 + 2) * P * rs, (ny / 4 + 2) * P * rs,                            // slab-boundary shares
       2 * (size_t)std::max(march_strips(Nx, 1), step_flux_blocks(Nx)) * 8,    // flux partials
       16 * 8 + 64, (size_t)reduce_state_blocks() * 6 * 8,
-      (3 * (2 * ny + 2) + (size_t)Nx / 2 + 1) * rs};                         // odd-extension tables
+      (3 * (2 * ny + 2) + (size_t)Nx / 2 + 1) * rs,                          // odd-extension tables
+      9 * ny * 8, 9 * ny * 8, 9 * ny * 8, 9 * ny * 8, ny * 8, ny * 8, ny * 8,  // perturbation-form base
+      ny * 16, ny * 16};
   size_t b = 0;
   for (size_t v : bufs) {
     const size_t g = (v > (1u << 20)) ? (2u << 20) : 512;
@@ -485,6 +555,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   if (o.ex_spectral && o.step_kernel == 1) return fail(EHD_EINVAL, "spectral E_x needs the march form");
   if (o.n_modes < 0 || o.n_modes > EHD_MAX_PERT_MODES) return fail(EHD_EINVAL, "n_modes out of range");
   if (o.step_kernel < -1 || o.step_kernel > 1) return fail(EHD_EINVAL, "step_kernel must be -1, 0 or 1");
+  if (o.perturbation != 0 && o.perturbation != 1) return fail(EHD_EINVAL, "perturbation must be 0 or 1");
+  if (o.perturbation && (o.compute != EHD_COMPUTE_F32 || o.ex_spectral || o.step_kernel == 1))
+    return fail(EHD_EINVAL, "the perturbation form needs FP32 compute, the march form and central-difference E_x");
 
   ehd_run* r = new ehd_run();
   {
@@ -545,7 +618,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   }
   if (cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev_step, cudaEventDisableTiming) != cudaSuccess) {
     destroy_quiet(r);
     return fail(EHD_ECUDA, "stream/event creation failed");
   }
@@ -586,6 +660,17 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   }
   r->rx_dn = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
   r->rx_up = run_alloc(r, (size_t)(Ny / 4 + 2) * r->P * r->rsz);
+  r->pert = o.perturbation;
+  if (r->pert) {
+    for (int k = 0; k < 2; ++k) {
+      r->bf[k] = static_cast<double*>(run_alloc(r, 9 * (size_t)Ny * sizeof(double)));
+      r->bg[k] = static_cast<double*>(run_alloc(r, 9 * (size_t)Ny * sizeof(double)));
+      r->btab[k] = static_cast<float*>(run_alloc(r, 4 * (size_t)Ny * sizeof(float)));
+    }
+    r->EBd = static_cast<double*>(run_alloc(r, (size_t)Ny * sizeof(double)));
+    r->phiB = static_cast<double*>(run_alloc(r, (size_t)Ny * sizeof(double)));
+    r->brhs = static_cast<double*>(run_alloc(r, (size_t)Ny * sizeof(double)));
+  }
   r->step_kernel = (o.step_kernel >= 0) ? o.step_kernel : (r->real_f64 && !o.ex_spectral) ? 1 : 0;
   // programmatic dependent launch of the Poisson kernels: on for grids of
   // up to 2^18 nodes, whose steps are launch-latency bound (256 x 208: 17.4
@@ -601,7 +686,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   bool ok = r->f[0] && r->f[1] && r->g[0] && r->g[1] && r->dphi && r->rhoc && r->rx_dn && r->rx_up && r->phibar &&
             r->Ebar && r->spec && r->spec0 &&
             r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part &&
-            (r->nfac <= 0 || r->oddt) && (!r->ex_spectral || r->exs);
+            (r->nfac <= 0 || r->oddt) && (!r->ex_spectral || r->exs) &&
+            (!r->pert || (r->bf[0] && r->bf[1] && r->bg[0] && r->bg[1] && r->btab[0] && r->btab[1] && r->EBd &&
+                          r->phiB && r->brhs));
   if (!ok) {
     destroy_quiet(r);
     return fail(EHD_ENOMEM, "device allocation failed");
@@ -759,12 +846,30 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     }
     st = upload(r, dpack, pack.data(), pack.size() * sizeof(double));
     if (st == EHD_OK && shifted) st = upload(r, r->rch, rchf.data(), Ny * sizeof(float));
+    if (st == EHD_OK && r->pert) {
+      // base state: the x-uniform part of the initial state (no roll):
+      // f^eq(rho_h, -F_h / (2 rho_h) e_y), g^eq(rho_c,h, mu_b E_h e_y)
+      static const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+      static const double w[9] = {kW0, kW1, kW1, kW1, kW1, kW2, kW2, kW2, kW2};
+      std::vector<double> bfh(9 * (size_t)Ny), bgh(9 * (size_t)Ny);
+      for (int j = 0; j < Ny; ++j) {
+        const double fy = -0.5 * Fh / rho_h[j], gy = r->mub * Eh[j];
+        for (int i = 0; i < 9; ++i) {
+          const double fc = cy[i] * fy, gc = cy[i] * gy;
+          bfh[i * (size_t)Ny + j] = w[i] * rho_h[j] * (1.0 + 3.0 * fc + 4.5 * fc * fc - 1.5 * fy * fy);
+          bgh[i * (size_t)Ny + j] = w[i] * rc_h[j] * (1.0 + 3.0 * gc + 4.5 * gc * gc - 1.5 * gy * gy);
+        }
+      }
+      st = upload(r, r->bf[0], bfh.data(), bfh.size() * sizeof(double));
+      if (st == EHD_OK) st = upload(r, r->bg[0], bgh.data(), bgh.size() * sizeof(double));
+    }
     if (st == EHD_OK) {
       const double* p = dpack;
       cudaError_t e = cudaMemsetAsync(r->small, 0, 16 * sizeof(double) + 64, r->stream);
       if (e == cudaSuccess)
         e = launch_init(p, p + Ny, p + 2 * Ny, p + 3 * Ny, p + 4 * Ny, p + 5 * Ny, p + 5 * Ny + nx, Fh, r->mub,
-                        r->f[0], r->g[0], r->storage, Nx, Ny, r->P, r->rch, r->fb, r->fd, r->stream);
+                        r->f[0], r->g[0], r->storage, Nx, Ny, r->P, r->rch, r->fb, r->fd,
+                        r->pert ? r->bg[0] : nullptr, r->stream);
       if (e == cudaSuccess) e = enqueue_poisson(r, 0, false);
       if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
       if (e != cudaSuccess) st = fail(EHD_ECUDA, "initialisation: %s", cudaGetErrorString(e));
@@ -821,6 +926,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
     }
     case EHD_TUNE_COLS_PER_LANE:
       if (value != 1 && value != 2) return fail(EHD_EINVAL, "columns per lane must be 1 or 2");
+      if (value != 2 && r->pert) return fail(EHD_EINVAL, "perturbation-form runs keep two columns per lane");
       if (value != 2 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x runs keep two columns per lane");
       if (value == 2 && r->ring_depth == 6) r->ring_depth = 3;
       r->cols_per_lane = value;
@@ -829,12 +935,14 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       break;
     case EHD_TUNE_MARCH_TMA:
       if (value < 0 || value > 3) return fail(EHD_EINVAL, "TMA march must be 0, 1, 2 or 3");
+      if (value != 0 && r->pert) return fail(EHD_EINVAL, "perturbation-form runs use the cp.async march");
       if (value != 0 && !r->tma_ok)
         return fail(EHD_EINVAL, "the TMA march needs FP32 storage and compute and 128 <= Nx <= 2048");
       r->march_tma = value;
       break;
     case EHD_TUNE_STEP_KERNEL:
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "step kernel must be 0 or 1");
+      if (value != 0 && r->pert) return fail(EHD_EINVAL, "perturbation-form runs need the march form");
       if (value != 0 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x needs the march form");
       r->step_kernel = value;
       r->nxb = (value == 0) ? r->nstrips : step_flux_blocks(r->Nx);
@@ -913,7 +1021,8 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
     cudaEvent_t* E = &ev[(size_t)NE * t];
     const StepArgs sa = step_args(r, r->cur);
     const int nxt = 1 - r->cur;
-    e = cudaEventRecord(E[0], r->stream);
+    if (r->pert) e = enqueue_base(r, r->cur);  // on the side stream, joined by the Poisson solve
+    if (e == cudaSuccess) e = cudaEventRecord(E[0], r->stream);
     if (e == cudaSuccess)
       e = (r->step_kernel == 0) ? launch_march_run(r, sa, r->cur)
                                 : launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
@@ -1001,13 +1110,34 @@ ehd_status ehd_load(ehd_run* r, const double* f_host, const double* g_host) {
     e = cudaMemcpyAsync(stage, f_host + i * n, n * sizeof(double), cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess)
       e = launch_load_plane(stage, static_cast<char*>(r->f[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
-                            r->P, w[i], nullptr, r->fb, r->fd, r->stream);
+                            r->P, w[i], nullptr, r->fb, r->fd, nullptr, r->stream);
+  }
+  if (r->pert) {
+    // perturbation form: the new base state is the row means of the loaded
+    // populations, and g is stored as the departure from it
+    std::vector<double> bfh(9 * (size_t)r->Ny, 0.0), bgh(9 * (size_t)r->Ny, 0.0);
+    for (int i = 0; i < 9; ++i)
+      for (int j = 0; j < r->Ny; ++j) {
+        double sf = 0, sg = 0;
+        for (int x = 0; x < r->Nx; ++x) {
+          sf += f_host[i * n + (size_t)j * r->Nx + x];
+          sg += g_host[i * n + (size_t)j * r->Nx + x];
+        }
+        bfh[i * (size_t)r->Ny + j] = sf / r->Nx;
+        bgh[i * (size_t)r->Ny + j] = sg / r->Nx;
+      }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->bf[r->cur], bfh.data(), bfh.size() * sizeof(double), cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->bg[r->cur], bgh.data(), bgh.size() * sizeof(double), cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);  // the host vectors end here
   }
   for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
     e = cudaMemcpyAsync(stage, g_host + i * n, n * sizeof(double), cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess)
       e = launch_load_plane(stage, static_cast<char*>(r->g[r->cur]) + i * plane * sb, r->storage, r->Nx, r->Ny,
-                            r->P, w[i], r->rch, 0.0, 0.0, r->stream);
+                            r->P, r->pert ? 0.0 : w[i], r->pert ? nullptr : r->rch, 0.0, 0.0,
+                            r->pert ? r->bg[r->cur] + i * (size_t)r->Ny : nullptr, r->stream);
   }
   if (e == cudaSuccess) e = enqueue_poisson(r, r->cur, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
@@ -1031,9 +1161,10 @@ ehd_status ehd_save(ehd_run* r, double* f_host, double* g_host) {
     if (!host) continue;
     const void* base = set == 0 ? r->f[r->cur] : r->g[r->cur];
     for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
+      const bool dep = set == 1 && r->pert;  // g as departures from the base state
       e = launch_save_plane(static_cast<const char*>(base) + i * plane * sb, stage, r->storage, r->Nx, r->Ny, r->P,
-                            w[i], set == 0 ? nullptr : r->rch, set == 0 ? r->fb : 0.0,
-                            set == 0 ? r->fd : 0.0, r->stream);
+                            dep ? 0.0 : w[i], set == 0 || dep ? nullptr : r->rch, set == 0 ? r->fb : 0.0,
+                            set == 0 ? r->fd : 0.0, dep ? r->bg[r->cur] + i * (size_t)r->Ny : nullptr, r->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(host + i * n, stage, n * sizeof(double), cudaMemcpyDeviceToHost, r->stream);
     }
@@ -1105,6 +1236,7 @@ void batch_free(ehd_batch* b) {
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->ev_upload) cudaEventDestroy(b->ev_upload);
+  if (b->ev_step) cudaEventDestroy(b->ev_step);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -1166,14 +1298,23 @@ void batch_build_items(ehd_batch* b, int resident_warps) {
   b->h_counts[3] = (int)nt;
 }
 
-ehd_status batch_capture(ehd_batch* b, int K, cudaGraphExec_t* out) {
+// One tick of K steps.  With perturbation-form members (pert) each step
+// also advances their FP64 base states and base potentials on the side
+// stream, from the point where the previous step ended, ahead of the mean
+// modes there.
+ehd_status batch_capture(ehd_batch* b, int K, bool pert, cudaGraphExec_t* out) {
   const BatchTables t = batch_tables(b);
   cudaGraph_t g = nullptr;
   EHD_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < K && e == cudaSuccess; ++s) {
     e = cudaMemsetAsync(b->d_work, 0, 4 * sizeof(int), b->stream);
-    if (e == cudaSuccess) e = launch_batch_march(t, s, b->grid_march, b->stream);
+    if (pert) {
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_step, b->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_step, 0);
+      if (e == cudaSuccess) e = launch_batch_base(t, s, b->max_runs, b->max_ny, b->side);
+    }
+    if (e == cudaSuccess) e = launch_batch_march(t, s, b->grid_march, pert, b->stream);
     if (e == cudaSuccess) e = launch_batch_rfft(t, s, b->grid_rows, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
@@ -1235,7 +1376,8 @@ ehd_status ehd_batch_create(int max_runs, size_t hbm_budget, int max_nx, int max
   if (!b->stream || cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_step, cudaEventDisableTiming) != cudaSuccess) {
     batch_free(b);
     return fail(EHD_ECUDA, "stream/event creation failed");
   }
@@ -1302,6 +1444,7 @@ ehd_status ehd_batch_add(ehd_batch* b, ehd_run* r, long steps) {
   b->remaining.push_back(steps);
   b->member_bytes.push_back(need);
   b->hbm_used += need;
+  if (r->pert) ++b->npert;
   b->dirty = true;
   return EHD_OK;
 }
@@ -1342,6 +1485,7 @@ ehd_status ehd_batch_remove(ehd_batch* b, ehd_run* r) {
   b->remaining.erase(b->remaining.begin() + i);
   b->hbm_used -= b->member_bytes[i];
   b->member_bytes.erase(b->member_bytes.begin() + i);
+  if (r->pert) --b->npert;
   r->batch = nullptr;
   b->dirty = true;
   return EHD_OK;
@@ -1367,6 +1511,10 @@ ehd_status ehd_batch_tick(ehd_batch* b, int steps) {
       d.sa[p].nstrips = march_strips(r->Nx, 2);
       d.sa[p].slab_rows = b->slab_rows;
     }
+    for (int p = 0; p < 2; ++p) {
+      d.ba[p] = r->pert ? base_step_args(r, p) : BaseArgs{};
+      d.bp[p] = r->pert ? base_poisson_args(r, 1 - p) : BasePoissonArgs{};
+    }
     d.pa = poisson_args(r, true);
     d.pa.nflux = d.sa[0].nstrips;
     d.pa.xslab = b->slab_rows;
@@ -1388,12 +1536,13 @@ ehd_status ehd_batch_tick(ehd_batch* b, int steps) {
   }
   EHD_CK(cudaEventRecord(b->ev_upload, b->stream));
   if (nrun == 0) return EHD_OK;
-  auto it = b->graphs.find(steps);
+  const int key = 2 * steps + (b->npert > 0);
+  auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     cudaGraphExec_t ge = nullptr;
-    ehd_status st = batch_capture(b, steps, &ge);
+    ehd_status st = batch_capture(b, steps, b->npert > 0, &ge);
     if (st != EHD_OK) return st;
-    it = b->graphs.emplace(steps, ge).first;
+    it = b->graphs.emplace(key, ge).first;
   }
   EHD_CK(cudaGraphLaunch(it->second, b->stream));
   for (size_t i = 0; i < nrun; ++i) {

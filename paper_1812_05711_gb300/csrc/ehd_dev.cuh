@@ -124,6 +124,7 @@ struct StepArgs {
   int ring_depth;            // rows staged ahead by cp.async (2, 3, 4 or 6)
   int cols_per_lane;         // 1: 32-column strips (30 owned); 2: 64-column strips (60 owned)
   int pdl;                   // launch with programmatic dependent launch (see launch_ex)
+  const float* base_tab;     // perturbation form: the march table of time t ([Ny][4]); nullptr otherwise
 };
 
 struct PoissonArgs {
@@ -190,6 +191,9 @@ struct FieldArgs {
   double fb, fd;             // f shift r(y) = fb + fd y
   double mub;
   int wall_mode;
+  const double* base_g;      // perturbation form: [9][Ny] base g added to the stored departures (else nullptr)
+  const double* phiB;        // [Ny] base potential and field added to the departure's
+  const double* EB;
 };
 
 // Row-mean potential as stored: a double, or a float-float (hi, lo) pair on
@@ -204,6 +208,39 @@ __device__ __forceinline__ double load_phibar(const void* p, int j) {
   }
 }
 
+// ------------------------------------------------ perturbation form ---
+// FP32-compute runs may advance the charge populations as departures from an
+// x-uniform base state that is advanced exactly, in FP64: g = B_g(y, t) + d.
+// The base (both population sets, [9][Ny] FP64 each) follows the method's
+// own dynamics restricted to x-uniform fields -- collision, streaming in y,
+// the wall rules and the mean mode of the Poisson equation -- so the
+// departure d carries only what varies in x (a roll and its consequences)
+// and its FP32 arithmetic is relative to that.  The step kernel needs, per
+// row, the base charge, the base fluid velocity u_y and the base field E_y:
+// the march table, FP32 [Ny][4] = {rho_c, u_y, E_y, 0}.
+struct BaseArgs {
+  int Nx, Ny;
+  const double* fin;   // [9][Ny] base f at time t
+  const double* gin;   // [9][Ny] base g at time t
+  double* fout;        // [9][Ny] at t + 1
+  double* gout;
+  const double* EB;    // [Ny] base E_y at time t
+  double wp, wm, gwp, gwm, mub, rho0;
+  double* flux_acc;    // [2] FP64 totals of injected / collected charge (base part added)
+};
+struct BasePoissonArgs {
+  int Nx, Ny, wall_mode;
+  const double* f;     // [9][Ny] base state whose potential is solved
+  const double* g;
+  double eps, phi0;
+  double* rhs;         // [Ny] scratch: the mean-mode right-hand side
+  double* phiB;        // [Ny] base potential (out)
+  double* EB;          // [Ny] base E_y (out)
+  float* table;        // [Ny][4] march table (out)
+};
+cudaError_t launch_base_step(const BaseArgs& a, cudaStream_t s);
+cudaError_t launch_base_poisson(const BasePoissonArgs& a, cudaStream_t s);
+
 // ------------------------------------------------------------- batches ---
 // A batch advances many runs (FP32 storage and compute, march form) together:
 // each phase of the step is one persistent kernel over a work list that
@@ -212,6 +249,8 @@ __device__ __forceinline__ double load_phibar(const void* p, int j) {
 struct BatchRunDesc {
   StepArgs sa[2];    // [p]: step from buffer p to 1 - p
   PoissonArgs pa;    // Poisson solve of the run (with its wall fluxes)
+  BaseArgs ba[2];    // perturbation form: the base step from buffer p (ba[p].fin == nullptr otherwise)
+  BasePoissonArgs bp[2];  // and the potential of its result (buffer 1 - p)
   int cur0;          // buffer holding the state at the start of the tick
   int remaining;     // steps the run still takes in this tick
   int E;             // Nx / 64: warp-FFT shape
@@ -237,12 +276,17 @@ __device__ __forceinline__ int next_item_warp(int* counter) {
   return __shfl_sync(0xffffffffu, it, 0);
 }
 // one launch of each phase for step t (0-based) of a tick
-cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, cudaStream_t s);
+// pert: the graph has perturbation-form members (the march branches per run)
+cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, bool pert, cudaStream_t s);
 cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s);
+// perturbation-form members: the FP64 base step and its potential
+cudaError_t launch_batch_base(const BatchTables& t, int step, int max_runs, int max_ny, cudaStream_t s);
 constexpr int kBatchTileModes = 8;
+
+
 
 // Tensor maps of the TMA form of the march kernel (FP32 storage and compute,
 // Nx >= 128): the pre-collision populations as 3-D tensors {Nx, Ny, 9}
@@ -297,13 +341,15 @@ cudaError_t launch_fields(const FieldArgs& a, int storage, bool real_f64, unsign
 cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, double* part, int nblk,
                                 double* out, int* err, cudaStream_t s);
 int reduce_state_blocks();
+// shift per row: shift_w (rch[y] + c0 + c1 y) + (brow ? brow[y] : 0)
 cudaError_t launch_load_plane(const double* src, void* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double c0, double c1, cudaStream_t s);
+                              const float* rch, double c0, double c1, const double* brow, cudaStream_t s);
 cudaError_t launch_save_plane(const void* src, double* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double c0, double c1, cudaStream_t s);
+                              const float* rch, double c0, double c1, const double* brow, cudaStream_t s);
+// base_g (perturbation form): [9][Ny] subtracted from g instead of w_i rch[y]
 cudaError_t launch_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY,
                         const double* cY, const double* Sx, const double* Cy, double Fh, double mub,
                         void* f, void* g, int storage, int Nx, int Ny, int P, const float* rch, double fb,
-                        double fd, cudaStream_t s);
+                        double fd, const double* base_g, cudaStream_t s);
 
 }  // namespace ehd

@@ -496,9 +496,63 @@ __device__ __forceinline__ void collide_node(R (&f)[9], R (&g)[9], R Ex, R Ey, R
   trt_g2<R>(g[6], g[8], W2, drc, rc, vy - vx, vsq15, gwp, gwm);
 }
 
+// Perturbation form (FP32 compute): the fluid part as collide_node, with the
+// full field E = E_B + E' in the force; the charge populations g are the
+// departures d = g - B_g(y) from the x-uniform base state, and their TRT
+// collision relaxes d towards the departure of the equilibrium,
+// g^eq(rho_c, v) - g^eq(rho_c,B, v_B) (Eq. 11), written out so that every
+// term is a product with a departure (drc = sum d, v' = v - v_B): with
+// v_B = (0, vby) the base drift, cvb = c . v_B, cvp = c . v',
+//   even: w [drc (1 + 4.5 cvb^2 - 1.5 vby^2)
+//            + rho_c (9 cvb cvp - 3 vby v'_y + 4.5 cvp^2 - 1.5 |v'|^2)]
+//   odd:  w [3 drc cvb + 3 rho_c cvp]
+// (the base's own collision is advanced exactly, in FP64, elsewhere).
+template <class R>
+__device__ __forceinline__ void trt_g2p(R& gi, R& go, R w, R drc, R rc, R cvb, R cvp, R qb, R qp, R wp, R wm) {
+  const R ep = w * (drc * (R(1) + R(4.5) * cvb * cvb - qb) + rc * (R(9) * cvb * cvp + R(4.5) * cvp * cvp - qp));
+  const R em = w * R(3) * (drc * cvb + rc * cvp);
+  const R sp = R(0.5) * (gi + go), sm = R(0.5) * (gi - go);
+  const R A = -wp * (sp - ep);
+  const R B = -wm * (sm - em);
+  gi = gi + A + B;
+  go = go + A - B;
+}
+
+template <class R>
+__device__ __forceinline__ void collide_node_pert(R (&f)[9], R (&g)[9], R Ex, R EyF, R EyD, R rcB, R uBy, R vby, R sf,
+                                                  R dq, R mub, R wp, R wm, R cp, R cm, R gwp, R gwm, bool& bad) {
+  const R W0 = (R)kW0, W1 = (R)kW1, W2 = (R)kW2;
+  const R drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const R rho = sf + drho;
+  const R jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+  const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  const R drc = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  const R rc = rcB + drc;
+  bad = !isfinite(drho) || !isfinite(drc);
+  const R Fx = rc * Ex, Fy = rc * EyF;
+  const R irho = R(1) / rho;
+  const R ux = (jx + R(0.5) * Fx) * irho;
+  const R uy = (jy + R(0.5) * Fy) * irho;
+  const R usq15 = R(1.5) * (ux * ux + uy * uy);
+  const R uF3 = R(3) * (ux * Fx + uy * Fy);
+  f[0] = f[0] - wp * (f[0] - W0 * (drho - rho * usq15)) - cp * W0 * uF3;
+  trt_f2<R>(f[1], f[3], W1, drho, rho, ux, usq15, Fx, uF3, wp, wm, cp, cm);
+  trt_f2y<R>(f[2], f[4], W1, drho, rho, uy, usq15, Fy, uF3, wp, wm, cp, cm, dq);
+  trt_f2y<R>(f[5], f[7], W2, drho, rho, ux + uy, usq15, Fx + Fy, uF3, wp, wm, cp, cm, dq);
+  trt_f2y<R>(f[6], f[8], W2, drho, rho, uy - ux, usq15, Fy - Fx, uF3, wp, wm, cp, cm, dq);
+  const R vpx = ux + mub * Ex, vpy = (uy - uBy) + mub * EyD;
+  const R qb = R(1.5) * vby * vby;
+  const R qp = R(3) * vby * vpy + R(1.5) * (vpx * vpx + vpy * vpy);
+  g[0] = g[0] - gwp * (g[0] - W0 * (drc * (R(1) - qb) - rc * qp));
+  trt_g2p<R>(g[1], g[3], W1, drc, rc, R(0), vpx, qb, qp, gwp, gwm);
+  trt_g2p<R>(g[2], g[4], W1, drc, rc, vby, vpy, qb, qp, gwp, gwm);
+  trt_g2p<R>(g[5], g[7], W2, drc, rc, vby, vpx + vpy, qb, qp, gwp, gwm);
+  trt_g2p<R>(g[6], g[8], W2, drc, rc, vby, vpy - vpx, qb, qp, gwp, gwm);
+}
+
 // One warp's walk over slab `slab` of strip `strip`; warp_ring is the warp's
 // NSTAGE-row staging area.  Shared by the single-run and the batch kernels.
-template <class S, class R, int NSTAGE, bool SPECX = false>
+template <class S, class R, int NSTAGE, bool SPECX = false, bool PERT = false>
 __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int slab, unsigned char* warp_ring) {
   using St = March2Stages<S, R, NSTAGE, SPECX>;
   constexpr int NST = NSTAGE, SL = St::kSlots, SB = St::kSlotBytes;
@@ -568,6 +622,9 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
     if constexpr (SPECX) cp_async_elem<2 * sizeof(R)>(slot(stage, 20), static_cast<const R*>(a.ex) + c);
     if (lane == 1) {
       cp_async_elem<sizeof(R)>(slot(stage, 19), Ebar + row_y);
+    } else if constexpr (PERT) {
+      // the march table of the base state: rho_c,B, u_y,B, E_y,B of the row
+      if (lane >= 2 && lane <= 4) cp_async_elem<4>(slot(stage, 19), a.base_tab + 4 * row_y + (lane - 2));
     } else if (rch && lane == 2) {
       cp_async_elem<4>(slot(stage, 19), rch + row_y);
     } else if (rch && lane == 3 && row_y + 1 < Ny) {
@@ -603,9 +660,20 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
     const R ex_r = *reinterpret_cast<const R*>(slot(st, 19));
     const float ex_f = *reinterpret_cast<const float*>(slot(st, 19));
     const R Ebr = __shfl_sync(0xffffffffu, ex_r, 1);
-    const R sy = rch ? (R)__shfl_sync(0xffffffffu, ex_f, 2) : R(0);
-    const R s_up = (rch && r + 1 < Ny) ? (R)__shfl_sync(0xffffffffu, ex_f, 3) : sy;
-    const R s_dn = (rch && r > 0) ? (R)__shfl_sync(0xffffffffu, ex_f, 4) : sy;
+    R sy, s_up, s_dn, uBy = R(0), EB = R(0);
+    if constexpr (PERT) {
+      // g holds departures from the base state: no shift changes between
+      // rows (the base streams exactly); sy is the base charge of the row
+      sy = (R)__shfl_sync(0xffffffffu, ex_f, 2);
+      uBy = (R)__shfl_sync(0xffffffffu, ex_f, 3);
+      EB = (R)__shfl_sync(0xffffffffu, ex_f, 4);
+      s_up = sy;
+      s_dn = sy;
+    } else {
+      sy = rch ? (R)__shfl_sync(0xffffffffu, ex_f, 2) : R(0);
+      s_up = (rch && r + 1 < Ny) ? (R)__shfl_sync(0xffffffffu, ex_f, 3) : sy;
+      s_dn = (rch && r > 0) ? (R)__shfl_sync(0xffffffffu, ex_f, 4) : sy;
+    }
     const R sf = fb + fd * (R)r;
     // E = -grad phi at both nodes of the pair
     R Ex0, Ex1;
@@ -629,8 +697,16 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       g1[i] = G[i][1];
     }
     bool b0, b1;
-    collide_node<S, R>(f0, g0, Ex0, Ey0, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b0);
-    collide_node<S, R>(f1, g1, Ex1, Ey1, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b1);
+    if constexpr (PERT) {
+      // Ey0, Ey1 are the departure's field (its mean-mode part is the
+      // departure's); the full field adds the base's
+      const R vby = uBy + mub * EB;
+      collide_node_pert<R>(f0, g0, Ex0, EB + Ey0, Ey0, sy, uBy, vby, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b0);
+      collide_node_pert<R>(f1, g1, Ex1, EB + Ey1, Ey1, sy, uBy, vby, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b1);
+    } else {
+      collide_node<S, R>(f0, g0, Ex0, Ey0, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b0);
+      collide_node<S, R>(f1, g1, Ex1, Ey1, sy, sf, fdq, mub, wp, wm, cp, cm, gwp, gwm, b1);
+    }
     if (owned && (b0 || b1)) bad = true;
     // pulled values at (xc, xc + 1): x-shift by c_x
     // c_x = +1 (1, 5, 8): [0] from the left lane's second node, [1] own first
@@ -668,12 +744,24 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       const R Exs[2] = {Ex0, Ex1}, Eys[2] = {Ey0, Ey1};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const R wx = mub * Exs[j], wy = mub * Eys[j];
-        const R w15 = R(1.5) * (wx * wx + wy * wy);
-        const R c2 = wy, c5 = wx + wy, c6 = wy - wx;
-        const R n2 = -(g4c[j] + R(2) * W1 * sy) + R(2) * W1 * rho0 * (R(1) + R(4.5) * c2 * c2 - w15);
-        const R n5 = -(g7c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c5 * c5 - w15);
-        const R n6 = -(g8c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c6 * c6 - w15);
+        R n2, n5, n6;
+        if constexpr (PERT) {
+          // departure of the injected populations: the wall drift v_w =
+          // mu_b E against the base's (0, mu_b E_B); with d = v_w - v_wB and
+          // s = v_w + v_wB, (c.v_w)^2 - (c.v_wB)^2 = (c.d)(c.s)
+          const R dx = mub * Exs[j], dy = mub * Eys[j], sx = dx, sy2 = dy + R(2) * mub * EB;
+          const R w15 = R(1.5) * (dx * sx + dy * sy2);
+          n2 = -g4c[j] + R(2) * W1 * rho0 * (R(4.5) * dy * sy2 - w15);
+          n5 = -g7c[j] + R(2) * W2 * rho0 * (R(4.5) * (dx + dy) * (sx + sy2) - w15);
+          n6 = -g8c[j] + R(2) * W2 * rho0 * (R(4.5) * (dy - dx) * (sy2 - sx) - w15);
+        } else {
+          const R wx = mub * Exs[j], wy = mub * Eys[j];
+          const R w15 = R(1.5) * (wx * wx + wy * wy);
+          const R c2 = wy, c5 = wx + wy, c6 = wy - wx;
+          n2 = -(g4c[j] + R(2) * W1 * sy) + R(2) * W1 * rho0 * (R(1) + R(4.5) * c2 * c2 - w15);
+          n5 = -(g7c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c5 * c5 - w15);
+          n6 = -(g8c[j] + R(2) * W2 * sy) + R(2) * W2 * rho0 * (R(1) + R(4.5) * c6 * c6 - w15);
+        }
         Uc[0][j] = f4c[j] - wd1;
         Uc[1][j] = f7c[j] - wd2;
         Uc[2][j] = f8c[j] - wd2;
@@ -728,7 +816,7 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
         const R h = (Store<S>::rt(Hm[3][j]) + Store<S>::rt(Hm[4][j])) + Store<S>::rt(Hm[5][j]);
         const R d = (Store<S>::rt(n4[j]) + Store<S>::rt(n7[j])) + Store<S>::rt(n8[j]);
         const R u = ups ? (Store<S>::rt(Um[3][j]) + Store<S>::rt(Um[4][j])) + Store<S>::rt(Um[5][j]) : R(0);
-        q[j] = s_dn + ((h + u) + d);
+        q[j] = PERT ? (h + u) + d : s_dn + ((h + u) + d);  // PERT: the departure's charge
       }
       Pair<R>::st(rho_out + c, q[0], q[1]);
     }
@@ -776,7 +864,7 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
         const R h = (Store<S>::rt(g0c[j]) + Store<S>::rt(Pg1[j])) + Store<S>::rt(Pg3[j]);
         const R d = (Store<S>::rt(g4c[j]) + Store<S>::rt(Pg7[j])) + Store<S>::rt(Pg8[j]);
         const R u = ups ? (Store<S>::rt(Uc[3][j]) + Store<S>::rt(Uc[4][j])) + Store<S>::rt(Uc[5][j]) : R(0);
-        q[j] = sy + ((h + u) + d);
+        q[j] = PERT ? (h + u) + d : sy + ((h + u) + d);
         qout += ((double)Store<S>::rt(g2c[j]) + (double)Store<S>::rt(g5c[j])) + (double)Store<S>::rt(g6c[j]);
         qout -= ((double)Store<S>::rt(g4c[j]) + (double)Store<S>::rt(g7c[j])) + (double)Store<S>::rt(g8c[j]);
       }
@@ -825,7 +913,7 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
     for (int j = 0; j < 2; ++j) {
       const R h = (Store<S>::rt(Hm[3][j]) + Store<S>::rt(Hm[4][j])) + Store<S>::rt(Hm[5][j]);
       const R u = ups ? (Store<S>::rt(Um[3][j]) + Store<S>::rt(Um[4][j])) + Store<S>::rt(Um[5][j]) : R(0);
-      q[j] = sy_last + (h + u);
+      q[j] = PERT ? h + u : sy_last + (h + u);
       e[j] = (Store<S>::rt(Uc[3][j]) + Store<S>::rt(Uc[4][j])) + Store<S>::rt(Uc[5][j]);
     }
     Pair<R>::st(rho_out + c, q[0], q[1]);
@@ -851,11 +939,11 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
   }
 }
 
-template <class S, class R, int NSTAGE, bool SPECX = false>
+template <class S, class R, int NSTAGE, bool SPECX = false, bool PERT = false>
 __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
   extern __shared__ __align__(16) unsigned char march_smem[];
   const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
-  march2_body<S, R, NSTAGE, SPECX>(
+  march2_body<S, R, NSTAGE, SPECX, PERT>(
       a, gw % a.nstrips, gw / a.nstrips,
       march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<S, R, NSTAGE, SPECX>::kBytesPerWarp);
 }
@@ -865,6 +953,8 @@ __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
 // budget in the tick is used up are skipped.  Bounded to three CTAs per SM
 // (168 registers, a few bytes spilled): at 180 registers only two fit and
 // the batch step takes 320 instead of 280 us.
+// With perturbation-form members (PERT) each item takes the form of its run.
+template <bool PERT>
 __global__ void __launch_bounds__(128, 3) k_batch_march(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char march_smem[];
   constexpr int NST = 2;
@@ -875,12 +965,19 @@ __global__ void __launch_bounds__(128, 3) k_batch_march(BatchTables t, int step)
     const BatchRunDesc& rd = t.runs[w.x];
     if (step >= rd.remaining) continue;  // whole warp
     const StepArgs a = rd.sa[rd.cur0 ^ (step & 1)];
-    march2_body<float, float, NST>(a, w.y, w.z, ring);
+    if (PERT && a.base_tab)
+      march2_body<float, float, NST, false, true>(a, w.y, w.z, ring);
+    else
+      march2_body<float, float, NST>(a, w.y, w.z, ring);
   }
 }
 
-cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, cudaStream_t s) {
-  k_batch_march<<<grid, 128, 4 * March2Stages<float, float, 2>::kBytesPerWarp, s>>>(t, step);
+cudaError_t launch_batch_march(const BatchTables& t, int step, int grid, bool pert, cudaStream_t s) {
+  const size_t sm = 4 * March2Stages<float, float, 2>::kBytesPerWarp;
+  if (pert)
+    k_batch_march<true><<<grid, 128, sm, s>>>(t, step);
+  else
+    k_batch_march<false><<<grid, 128, sm, s>>>(t, step);
   return cudaGetLastError();
 }
 
@@ -1499,8 +1596,15 @@ cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
 template <class S, class R, int NST, bool SPECX = false>
 cudaError_t march2_n(const StepArgs& a, cudaStream_t s) {
   const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
-  k_march2<S, R, NST, SPECX>
-      <<<(unsigned)((warps + 3) / 4), 128, 4 * March2Stages<S, R, NST, SPECX>::kBytesPerWarp, s>>>(a);
+  const unsigned grid = (unsigned)((warps + 3) / 4);
+  const size_t smem = 4 * March2Stages<S, R, NST, SPECX>::kBytesPerWarp;
+  if constexpr (sizeof(R) == 4 && !SPECX) {
+    if (a.base_tab) {
+      k_march2<S, R, NST, false, true><<<grid, 128, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  k_march2<S, R, NST, SPECX><<<grid, 128, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1540,7 +1644,13 @@ cudaError_t allow_smem(K kernel) {
 template <class S, class R>
 cudaError_t attrs_t() {
   cudaError_t e;
-  if ((e = allow_smem(k_batch_march)) != cudaSuccess) return e;
+  if constexpr (sizeof(R) == 4) {
+    if ((e = allow_smem(k_march2<S, R, 2, false, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_march2<S, R, 3, false, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_march2<S, R, 4, false, true>)) != cudaSuccess) return e;
+  }
+  if ((e = allow_smem(k_batch_march<false>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_batch_march<true>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 2>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 2, true>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_march2<S, R, 3>)) != cudaSuccess) return e;

@@ -28,7 +28,8 @@ __device__ Macro macro_at(const FieldArgs& a, int x, int y) {
   double rho = 0, jx = 0, jy = 0, rc = 0;
   for (int i = 0; i < 9; ++i) {
     const double fi = (double)Store<S>::template ld<R>(f + i * a.plane + c) + wgt(i) * sfy;
-    const double gi = (double)Store<S>::template ld<R>(g + i * a.plane + c) + wgt(i) * sy;
+    const double gi = (double)Store<S>::template ld<R>(g + i * a.plane + c) +
+                      (a.base_g ? a.base_g[i * a.Ny + y] : wgt(i) * sy);
     rho += fi;
     jx += cxi(i) * fi;
     jy += cyi(i) * fi;
@@ -43,8 +44,8 @@ __device__ Macro macro_at(const FieldArgs& a, int x, int y) {
   Macro m;
   m.Ex = a.ex ? (double)static_cast<const R*>(a.ex)[c]
               : -0.5 * ((double)dphi[c - x + xr] - (double)dphi[c - x + xl]);
-  m.Ey = (double)static_cast<const R*>(a.Ebar)[y] - 0.5 * (pN - pS);
-  m.phi = load_phibar<R>(a.phibar, y) + pc;
+  m.Ey = (double)static_cast<const R*>(a.Ebar)[y] - 0.5 * (pN - pS) + (a.EB ? a.EB[y] : 0.0);
+  m.phi = load_phibar<R>(a.phibar, y) + pc + (a.phiB ? a.phiB[y] : 0.0);
   m.rho = rho;
   m.rc = rc;
   m.ux = (jx + 0.5 * rc * m.Ex) / rho;
@@ -119,25 +120,25 @@ __global__ void k_reduce_final(const double* part, int nblk, double* out, int* e
   if (t[5] > 0) atomicOr(err, 1);
 }
 
-// value_stored = value - shift_w (rch[y] + c0 + c1 y)   (rch may be null)
+// value_stored = value - shift_w (rch[y] + c0 + c1 y) - brow[y]   (rch, brow may be null)
 template <class S>
 __global__ void k_load_plane(const double* src, S* dst, int Nx, int Ny, int P, double shift_w, const float* rch,
-                             double c0, double c1) {
+                             double c0, double c1, const double* brow) {
   const long long n = (long long)Nx * Ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % Nx), y = (int)(k / Nx);
-    const double sh = shift_w * ((rch ? (double)rch[y] : 0.0) + c0 + c1 * y);
+    const double sh = shift_w * ((rch ? (double)rch[y] : 0.0) + c0 + c1 * y) + (brow ? brow[y] : 0.0);
     Store<S>::st(dst + (long long)y * P + x, src[k] - sh);
   }
 }
 
 template <class S>
 __global__ void k_save_plane(const S* src, double* dst, int Nx, int Ny, int P, double shift_w, const float* rch,
-                             double c0, double c1) {
+                             double c0, double c1, const double* brow) {
   const long long n = (long long)Nx * Ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % Nx), y = (int)(k / Nx);
-    const double sh = shift_w * ((rch ? (double)rch[y] : 0.0) + c0 + c1 * y);
+    const double sh = shift_w * ((rch ? (double)rch[y] : 0.0) + c0 + c1 * y) + (brow ? brow[y] : 0.0);
     dst[k] = Store<S>::template ld<double>(src + (long long)y * P + x) + sh;
   }
 }
@@ -149,7 +150,7 @@ __global__ void k_save_plane(const S* src, double* dst, int Nx, int Ny, int P, d
 template <class S>
 __global__ void k_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY, const double* cY,
                        const double* Sx, const double* Cy, double Fh, double mub, S* f, S* g, int Nx, int Ny, int P,
-                       const float* rch, double fb, double fd) {
+                       const float* rch, double fb, double fd, const double* base_g) {
   const long long n = (long long)Nx * Ny;
   const long long pl = (long long)Ny * P;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -169,7 +170,7 @@ __global__ void k_init(const double* rho_h, const double* rc_h, const double* Eh
       const double feq = w * rho * (1.0 + 3.0 * fc + 4.5 * fc * fc - 1.5 * fu2);
       const double geq = w * rc * (1.0 + 3.0 * gc + 4.5 * gc * gc - 1.5 * gu2);
       Store<S>::st(f + i * pl + c, feq - w * sfy);
-      Store<S>::st(g + i * pl + c, geq - w * sy);
+      Store<S>::st(g + i * pl + c, geq - (base_g ? base_g[i * Ny + y] : w * sy));
     }
   }
 }
@@ -218,19 +219,20 @@ cudaError_t launch_reduce_state(const FieldArgs& a, int storage, bool real_f64, 
 }
 
 cudaError_t launch_load_plane(const double* src, void* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double c0, double c1, cudaStream_t s) {
+                              const float* rch, double c0, double c1, const double* brow, cudaStream_t s) {
   return by_storage(storage, false, [&](auto* sp, auto*) {
     using S = std::remove_pointer_t<decltype(sp)>;
-    k_load_plane<S><<<kGrid, kBlock, 0, s>>>(src, static_cast<S*>(dst), Nx, Ny, P, shift_w, rch, c0, c1);
+    k_load_plane<S><<<kGrid, kBlock, 0, s>>>(src, static_cast<S*>(dst), Nx, Ny, P, shift_w, rch, c0, c1, brow);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_save_plane(const void* src, double* dst, int storage, int Nx, int Ny, int P, double shift_w,
-                              const float* rch, double c0, double c1, cudaStream_t s) {
+                              const float* rch, double c0, double c1, const double* brow, cudaStream_t s) {
   return by_storage(storage, false, [&](auto* sp, auto*) {
     using S = std::remove_pointer_t<decltype(sp)>;
-    k_save_plane<S><<<kGrid, kBlock, 0, s>>>(static_cast<const S*>(src), dst, Nx, Ny, P, shift_w, rch, c0, c1);
+    k_save_plane<S><<<kGrid, kBlock, 0, s>>>(static_cast<const S*>(src), dst, Nx, Ny, P, shift_w, rch, c0, c1,
+                                             brow);
     return cudaGetLastError();
   });
 }
@@ -238,11 +240,11 @@ cudaError_t launch_save_plane(const void* src, double* dst, int storage, int Nx,
 cudaError_t launch_init(const double* rho_h, const double* rc_h, const double* Eh, const double* sY,
                         const double* cY, const double* Sx, const double* Cy, double Fh, double mub, void* f,
                         void* g, int storage, int Nx, int Ny, int P, const float* rch, double fb, double fd,
-                        cudaStream_t s) {
+                        const double* base_g, cudaStream_t s) {
   return by_storage(storage, false, [&](auto* sp, auto*) {
     using S = std::remove_pointer_t<decltype(sp)>;
     k_init<S><<<kGrid, kBlock, 0, s>>>(rho_h, rc_h, Eh, sY, cY, Sx, Cy, Fh, mub, static_cast<S*>(f),
-                                       static_cast<S*>(g), Nx, Ny, P, rch, fb, fd);
+                                       static_cast<S*>(g), Nx, Ny, P, rch, fb, fd, base_g);
     return cudaGetLastError();
   });
 }

@@ -746,6 +746,191 @@ __global__ void __launch_bounds__(kMeanThreads) k_batch_mean(BatchTables t, int 
   }
 }
 
+
+// --------------------------------------------------- perturbation form ---
+// One step of the x-uniform base state in FP64, one thread per row: the
+// moments (Eqs. 5-7, E_x = 0), the fluid TRT collision with the force
+// rho_c E_y (Eqs. 8, 10, 12, 13, 15) and the charge TRT collision with the
+// drift u + mu_b E (Eqs. 9, 11, 14), then streaming in y (an x-uniform state
+// does not change under the x shifts) with the wall rules: halfway
+// bounce-back of f, anti-bounce-back injection of rho0 with the wall-node
+// drift, zero-gradient outflow of g (Table I).  Each (population, row) of
+// t + 1 has one writer.  The two wall rows add their charge fluxes, times Nx,
+// to the run's FP64 totals.
+namespace {
+__device__ __forceinline__ double bw(int i) { return i == 0 ? kW0 : (i < 5 ? kW1 : kW2); }
+__device__ __forceinline__ int bcx(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__device__ __forceinline__ int bcy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__device__ __forceinline__ int bopp(int i) { return i == 0 ? 0 : (i < 5 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+__device__ __forceinline__ double beq(int i, double dens, double vx, double vy) {
+  const double cu = bcx(i) * vx + bcy(i) * vy;
+  return bw(i) * dens * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy));
+}
+}  // namespace
+
+// One compiled body serves the single-run and the batch kernels (not
+// inlined: the two kernels then share its rounding bit for bit).
+__device__ __noinline__ void base_step_row(const BaseArgs& a, int y) {
+  const int Ny = a.Ny;
+  double f[9], g[9];
+  double rho = 0, jx = 0, jy = 0, rc = 0;
+  for (int i = 0; i < 9; ++i) {
+    f[i] = a.fin[i * Ny + y];
+    g[i] = a.gin[i * Ny + y];
+    rho += f[i];
+    jx += bcx(i) * f[i];
+    jy += bcy(i) * f[i];
+    rc += g[i];
+  }
+  const double Ey = a.EB[y];
+  const double Fx = 0.0, Fy = rc * Ey;
+  const double ux = (jx + 0.5 * Fx) / rho, uy = (jy + 0.5 * Fy) / rho;
+  const double vx = ux, vy = uy + a.mub * Ey;
+  double fp[9], gp[9], feq[9], geq[9], Fi[9];
+  for (int i = 0; i < 9; ++i) {
+    feq[i] = beq(i, rho, ux, uy);
+    geq[i] = beq(i, rc, vx, vy);
+    const double cu = bcx(i) * ux + bcy(i) * uy;
+    const double ax = (bcx(i) - ux) * 3.0 + cu * bcx(i) * 9.0;
+    const double ay = (bcy(i) - uy) * 3.0 + cu * bcy(i) * 9.0;
+    Fi[i] = bw(i) * (ax * Fx + ay * Fy);
+  }
+  for (int i = 0; i < 9; ++i) {
+    const int o = bopp(i);
+    const double fpl = 0.5 * (f[i] + f[o]), fmi = 0.5 * (f[i] - f[o]);
+    const double epl = 0.5 * (feq[i] + feq[o]), emi = 0.5 * (feq[i] - feq[o]);
+    const double Fpl = 0.5 * (Fi[i] + Fi[o]), Fmi = 0.5 * (Fi[i] - Fi[o]);
+    fp[i] = f[i] - a.wp * (fpl - epl) - a.wm * (fmi - emi) + (1.0 - 0.5 * a.wp) * Fpl + (1.0 - 0.5 * a.wm) * Fmi;
+    const double gpl = 0.5 * (g[i] + g[o]), gmi = 0.5 * (g[i] - g[o]);
+    const double hpl = 0.5 * (geq[i] + geq[o]), hmi = 0.5 * (geq[i] - geq[o]);
+    gp[i] = g[i] - a.gwp * (gpl - hpl) - a.gwm * (gmi - hmi);
+  }
+  double qin = 0.0, qout = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    const int yt = y + bcy(i), o = bopp(i);
+    if (yt >= 0 && yt < Ny) {
+      a.fout[i * Ny + yt] = fp[i];
+      a.gout[i * Ny + yt] = gp[i];
+    } else if (yt < 0) {
+      // injector: bounce-back of f; anti-bounce-back of g with the wall drift
+      a.fout[o * Ny + y] = fp[i];
+      const double wvx = 0.0, wvy = a.mub * Ey;
+      const double cv = bcx(o) * wvx + bcy(o) * wvy;
+      const double even = bw(o) * a.rho0 * (1.0 + 4.5 * cv * cv - 1.5 * (wvx * wvx + wvy * wvy));
+      const double gn = -gp[i] + 2.0 * even;
+      a.gout[o * Ny + y] = gn;
+      qin += gn - gp[i];
+    } else {
+      // collector: bounce-back of f; the charge leaves
+      a.fout[o * Ny + y] = fp[i];
+      qout += gp[i];
+    }
+    if (y == Ny - 1 && bcy(i) < 0) {
+      // outflow: the down-movers entering the top row are the row's own
+      a.gout[i * Ny + y] = gp[i];
+      qout -= gp[i];
+    }
+  }
+  if (y == 0) a.flux_acc[0] += (double)a.Nx * qin;
+  if (y == Ny - 1) a.flux_acc[1] += (double)a.Nx * qout;
+}
+
+__global__ void __launch_bounds__(32) k_base_step(BaseArgs a) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y < a.Ny) base_step_row(a, y);
+}
+
+// Potential of the base state (the mean mode of Eqs. 18-20 with the wall
+// potentials: the FP64 double prefix sum of k_mean_mode on the base's row
+// sums), and the march table of the state: per row the base charge, the
+// base fluid velocity u_y (Eq. 7) and the base field E_y, in FP32.
+__device__ __noinline__ void base_poisson_body(const BasePoissonArgs& b, unsigned char* smem_raw,
+                                               MeanScratch<double, 512>& ms) {
+  const int Ny = b.Ny;
+  for (int j = threadIdx.x; j < Ny; j += 512) {
+    double rc = 0;
+    for (int i = 0; i < 9; ++i) rc += b.g[i * Ny + j];
+    b.rhs[j] = -(double)b.Nx * rc / b.eps;
+  }
+  __syncthreads();
+  PoissonArgs a{};
+  a.Nx = b.Nx;
+  a.Ny = Ny;
+  a.spec0 = b.rhs;
+  a.phibar = b.phiB;
+  a.Ebar = b.EB;
+  a.phi0 = b.phi0;
+  a.wall_mode = b.wall_mode;
+  a.flux_part = nullptr;
+  mean_mode_body<double, 512>(a, smem_raw, ms);
+  __syncthreads();
+  for (int j = threadIdx.x; j < Ny; j += 512) {
+    double rho = 0, jy = 0, rc = 0;
+    for (int i = 0; i < 9; ++i) {
+      const double fi = b.f[i * Ny + j];
+      rho += fi;
+      jy += bcy(i) * fi;
+      rc += b.g[i * Ny + j];
+    }
+    const double Ey = b.EB[j];
+    b.table[4 * j + 0] = (float)rc;
+    b.table[4 * j + 1] = (float)((jy + 0.5 * rc * Ey) / rho);
+    b.table[4 * j + 2] = (float)Ey;
+    b.table[4 * j + 3] = 0.0f;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_base_poisson(BasePoissonArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MeanScratch<double, 512> ms;
+  base_poisson_body(b, smem_raw, ms);
+}
+
+// Batch: the base step of every perturbation-form member (CTA (x, r): rows
+// 32 x .. of member r), then one CTA per member for its potential.
+__global__ void __launch_bounds__(32) k_batch_base_step(BatchTables t, int step) {
+  const int r = blockIdx.y;
+  if (r >= t.counts[0]) return;
+  const BatchRunDesc& rd = t.runs[r];
+  if (step >= rd.remaining) return;
+  const BaseArgs& a = rd.ba[rd.cur0 ^ (step & 1)];
+  if (!a.fin) return;
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y < a.Ny) base_step_row(a, y);
+}
+
+__global__ void __launch_bounds__(512) k_batch_base_poisson(BatchTables t, int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ MeanScratch<double, 512> ms;
+  const int n = t.counts[0];
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const BatchRunDesc& rd = t.runs[r];
+    if (step >= rd.remaining) continue;
+    const BasePoissonArgs& b = rd.bp[rd.cur0 ^ (step & 1)];
+    if (!b.f) continue;
+    base_poisson_body(b, smem_raw, ms);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_batch_base(const BatchTables& t, int step, int maxr, int max_ny, cudaStream_t s) {
+  k_batch_base_step<<<dim3((max_ny + 31) / 32, maxr), 32, 0, s>>>(t, step);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_batch_base_poisson<<<std::min(maxr, 152), 512, 2 * (size_t)max_ny * sizeof(double), s>>>(t, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_base_step(const BaseArgs& a, cudaStream_t s) {
+  k_base_step<<<(a.Ny + 31) / 32, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_base_poisson(const BasePoissonArgs& a, cudaStream_t s) {
+  k_base_poisson<<<1, 512, 2 * (size_t)a.Ny * sizeof(double), s>>>(a);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launch ---
 namespace {
 
@@ -894,6 +1079,8 @@ cudaError_t poisson_set_attributes() {
   if (e != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_modes)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_mean)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_base_poisson)) != cudaSuccess) return e;
+  if ((e = allow_max_dynamic_smem(k_batch_base_poisson)) != cudaSuccess) return e;
   e = set_attrs_t<double>();
   if (e != cudaSuccess) return e;
   return set_attrs_t<float>();
