@@ -89,7 +89,7 @@ struct ehd_run {
   double fb = 0, fd = 0; // f shift fb + fd y: the hydrostatic density ramp, fd rounded to FP32
   double* flux_part = nullptr;
   int nxb = 0;
-  double* small = nullptr;  // [0] q_in sum, [1] q_out sum, [2..7] last reduction
+  double* small = nullptr;  // [0] q_in sum, [1] q_out sum, [2..7] last reduction, [8..9] base q_in, q_out
   int* err = nullptr;
   double* red_part = nullptr;
   int rows = 1;        // rows per CTA of the node-parallel step kernel
@@ -122,8 +122,11 @@ struct ehd_run {
   double* EBd = nullptr;
   double* phiB = nullptr;
   double* brhs = nullptr;
+  double* bsum = nullptr;  // [4][Ny] rho_c, rho, j_y, j_x of the newest base state, [2][Ny] + [2][chunks] its prefix sums
+  double* bmom = nullptr;  // [5][Ny] its moments for the next base step
   float* btab[2] = {nullptr, nullptr};
-  cudaEvent_t ev_step = nullptr;
+  cudaStream_t side2 = nullptr;  // the base chain: forked after the march, joined at the end of the step
+  cudaEvent_t ev_base = nullptr;
 };
 
 struct ehd_batch {
@@ -133,7 +136,8 @@ struct ehd_batch {
   std::vector<size_t> member_bytes;
   cudaStream_t stream = nullptr, side = nullptr;
   bool own_stream = false;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_upload = nullptr, ev_step = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_upload = nullptr, ev_base = nullptr;
+  cudaStream_t side2 = nullptr;  // base chains of perturbation-form members
   std::vector<ehd_run*> members;
   int npert = 0;              // members in the perturbation form
   std::vector<long> remaining;
@@ -316,11 +320,13 @@ BasePoissonArgs base_poisson_args(const ehd_run* r, int cur) {
   b.Nx = r->Nx;
   b.Ny = r->Ny;
   b.wall_mode = r->wall_mode;
-  b.f = r->bf[cur];
-  b.g = r->bg[cur];
-  b.eps = r->eps;
   b.phi0 = r->phi0;
+  b.mub = r->mub;
   b.rhs = r->brhs;
+  b.sums = r->bsum;
+  b.loc = r->bsum + 4 * (size_t)r->Ny;
+  b.chunk = r->bsum + 6 * (size_t)r->Ny;
+  b.mom = r->bmom;
   b.phiB = r->phiB;
   b.EB = r->EBd;
   b.table = r->btab[cur];
@@ -341,16 +347,29 @@ BaseArgs base_step_args(const ehd_run* r, int cur) {
   b.gwm = 1.0 / r->taug_m;
   b.mub = r->mub;
   b.rho0 = r->rho0;
-  b.flux_acc = r->small;
+  b.eps = r->eps;
+  b.flux_acc = r->small + 8;
+  b.cp = 1.0 - 0.5 * b.wp;
+  b.cm = 1.0 - 0.5 * b.wm;
+  b.mom = r->bmom;
+  b.sums = r->bsum;
+  b.rhs = r->brhs;
+  b.loc = r->bsum + 4 * (size_t)r->Ny;
+  b.chunk = r->bsum + 6 * (size_t)r->Ny;
   return b;
 }
-// the base step from buffer `cur` and the potential of the result, on the
-// side stream after the point the main stream has reached
+// The base step from buffer `cur` and the potential and march table of the
+// result, on the third stream from the point where the departure's forward
+// row transform has ended (ev_fork: the base kernels then run beside the
+// wavenumber solves and the inverse transform rather than holding SM slots
+// the march or the forward transform need: 125.3 us per 2048 x 1680 step
+// against 127.7 when forked right after the march, and 122.4 for the shifted
+// FP32 form); the main stream waits for them at the end of the step.
 cudaError_t enqueue_base(ehd_run* r, int cur) {
-  cudaError_t e = cudaEventRecord(r->ev_step, r->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(r->side, r->ev_step, 0);
-  if (e == cudaSuccess) e = launch_base_step(base_step_args(r, cur), r->side);
-  if (e == cudaSuccess) e = launch_base_poisson(base_poisson_args(r, 1 - cur), r->side);
+  cudaError_t e = cudaStreamWaitEvent(r->side2, r->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_base_step(base_step_args(r, cur), r->side2);
+  if (e == cudaSuccess) e = launch_base_poisson(base_poisson_args(r, 1 - cur), r->side2);
+  if (e == cudaSuccess) e = cudaEventRecord(r->ev_base, r->side2);
   return e;
 }
 
@@ -360,7 +379,10 @@ cudaError_t enqueue_poisson(ehd_run* r, int cur, bool with_flux) {
   cudaError_t e = launch_rhoc(r->g[cur], (long long)r->Ny * r->P, r->storage, r->real_f64, r->Nx, r->Ny, r->P,
                               r->pert ? nullptr : r->rch, r->rhoc, r->stream);
   if (e != cudaSuccess) return e;
-  if (r->pert && (e = launch_base_poisson(base_poisson_args(r, cur), r->stream)) != cudaSuccess) return e;
+  if (r->pert) {
+    if ((e = launch_base_sums(base_step_args(r, cur), r->stream)) != cudaSuccess) return e;
+    if ((e = launch_base_poisson(base_poisson_args(r, cur), r->stream)) != cudaSuccess) return e;
+  }
   return launch_poisson(poisson_args(r, with_flux), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
 }
 
@@ -403,14 +425,12 @@ cudaError_t launch_march_run(const ehd_run* r, const StepArgs& sa, int cur) {
 // the node-parallel form needs the separate charge-moment kernel.
 cudaError_t enqueue_step(ehd_run* r, int cur) {
   const StepArgs sa = step_args(r, cur);
-  if (r->pert) {
-    cudaError_t e = enqueue_base(r, cur);
-    if (e != cudaSuccess) return e;
-  }
   if (r->step_kernel == 0) {
     cudaError_t e = launch_march_run(r, sa, cur);
-    if (e != cudaSuccess) return e;
-    return launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
+    if (e == cudaSuccess) e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
+    if (e == cudaSuccess && r->pert) e = enqueue_base(r, cur);
+    if (e == cudaSuccess && r->pert) e = cudaStreamWaitEvent(r->stream, r->ev_base, 0);
+    return e;
   }
   cudaError_t e = launch_step(sa, r->storage, r->real_f64, r->rows, r->stream);
   if (e != cudaSuccess) return e;
@@ -454,10 +474,12 @@ ehd_status destroy_quiet(ehd_run* r) {
   for (int k = 0; k < 2; ++k)
     if (r->graph[k]) cudaGraphExecDestroy(r->graph[k]);
   if (r->side) cudaStreamSynchronize(r->side);
+  if (r->side2) cudaStreamSynchronize(r->side2);
   if (r->ev_fork) cudaEventDestroy(r->ev_fork);
   if (r->ev_join) cudaEventDestroy(r->ev_join);
-  if (r->ev_step) cudaEventDestroy(r->ev_step);
+  if (r->ev_base) cudaEventDestroy(r->ev_base);
   if (r->side) cudaStreamDestroy(r->side);
+  if (r->side2) cudaStreamDestroy(r->side2);
   std::vector<void*> bl = r->blocks;
   for (void* p : bl) run_free(r, p);
   if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
@@ -619,7 +641,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   if (cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->ev_step, cudaEventDisableTiming) != cudaSuccess) {
+      (o.perturbation && (cudaStreamCreateWithFlags(&r->side2, cudaStreamNonBlocking) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&r->ev_base, cudaEventDisableTiming) != cudaSuccess))) {
     destroy_quiet(r);
     return fail(EHD_ECUDA, "stream/event creation failed");
   }
@@ -670,6 +693,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     r->EBd = static_cast<double*>(run_alloc(r, (size_t)Ny * sizeof(double)));
     r->phiB = static_cast<double*>(run_alloc(r, (size_t)Ny * sizeof(double)));
     r->brhs = static_cast<double*>(run_alloc(r, (size_t)Ny * sizeof(double)));
+    r->bsum = static_cast<double*>(run_alloc(r, (6 * (size_t)Ny + 2 * (size_t)base_chunks(Ny)) * sizeof(double)));
+    r->bmom = static_cast<double*>(run_alloc(r, 5 * (size_t)Ny * sizeof(double)));
   }
   r->step_kernel = (o.step_kernel >= 0) ? o.step_kernel : (r->real_f64 && !o.ex_spectral) ? 1 : 0;
   // programmatic dependent launch of the Poisson kernels: on for grids of
@@ -688,7 +713,7 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
             r->rfac && r->rfac0 && r->tw && (!shifted || r->rch) && r->flux_part && r->small && r->red_part &&
             (r->nfac <= 0 || r->oddt) && (!r->ex_spectral || r->exs) &&
             (!r->pert || (r->bf[0] && r->bf[1] && r->bg[0] && r->bg[1] && r->btab[0] && r->btab[1] && r->EBd &&
-                          r->phiB && r->brhs));
+                          r->phiB && r->brhs && r->bsum && r->bmom));
   if (!ok) {
     destroy_quiet(r);
     return fail(EHD_ENOMEM, "device allocation failed");
@@ -1021,7 +1046,6 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
     cudaEvent_t* E = &ev[(size_t)NE * t];
     const StepArgs sa = step_args(r, r->cur);
     const int nxt = 1 - r->cur;
-    if (r->pert) e = enqueue_base(r, r->cur);  // on the side stream, joined by the Poisson solve
     if (e == cudaSuccess) e = cudaEventRecord(E[0], r->stream);
     if (e == cudaSuccess)
       e = (r->step_kernel == 0) ? launch_march_run(r, sa, r->cur)
@@ -1033,6 +1057,8 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
     if (e == cudaSuccess) e = cudaEventRecord(E[2], r->stream);
     if (e == cudaSuccess)
       e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join, E + 4);
+    if (e == cudaSuccess && r->pert) e = enqueue_base(r, r->cur);  // third stream, joined at the step's end
+    if (e == cudaSuccess && r->pert) e = cudaStreamWaitEvent(r->stream, r->ev_base, 0);
     if (e == cudaSuccess) e = cudaEventRecord(E[3], r->stream);
     if (e == cudaSuccess) {
       r->cur = nxt;
@@ -1083,13 +1109,13 @@ ehd_status ehd_diagnostics(ehd_run* r, double* out) {
   DeviceGuard dg(r->device);
   EHD_CK(launch_reduce_state(field_args(r), r->storage, r->real_f64, r->red_part, reduce_state_blocks(),
                              r->small + 2, r->err, r->stream));
-  double h[8];
-  EHD_CK(cudaMemcpyAsync(h, r->small, 8 * sizeof(double), cudaMemcpyDeviceToHost, r->stream));
+  double h[10];
+  EHD_CK(cudaMemcpyAsync(h, r->small, 10 * sizeof(double), cudaMemcpyDeviceToHost, r->stream));
   EHD_CK(cudaStreamSynchronize(r->stream));
-  out[0] = h[2];  // mass
-  out[1] = h[3];  // charge
-  out[2] = h[0];  // injected since creation
-  out[3] = h[1];  // collected since creation
+  out[0] = h[2];         // mass
+  out[1] = h[3];         // charge
+  out[2] = h[0] + h[8];  // injected since creation (departure and base parts)
+  out[3] = h[1] + h[9];  // collected since creation
   out[4] = h[4];  // kinetic energy
   out[5] = h[5];  // max |u_y|
   out[6] = h[6];  // max |u|
@@ -1236,7 +1262,8 @@ void batch_free(ehd_batch* b) {
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->ev_upload) cudaEventDestroy(b->ev_upload);
-  if (b->ev_step) cudaEventDestroy(b->ev_step);
+  if (b->ev_base) cudaEventDestroy(b->ev_base);
+  if (b->side2) cudaStreamDestroy(b->side2);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -1299,9 +1326,9 @@ void batch_build_items(ehd_batch* b, int resident_warps) {
 }
 
 // One tick of K steps.  With perturbation-form members (pert) each step
-// also advances their FP64 base states and base potentials on the side
-// stream, from the point where the previous step ended, ahead of the mean
-// modes there.
+// also advances their FP64 base states and base potentials on a third
+// stream, forked after the forward row transforms and joined at the end of
+// the step.
 ehd_status batch_capture(ehd_batch* b, int K, bool pert, cudaGraphExec_t* out) {
   const BatchTables t = batch_tables(b);
   cudaGraph_t g = nullptr;
@@ -1309,20 +1336,21 @@ ehd_status batch_capture(ehd_batch* b, int K, bool pert, cudaGraphExec_t* out) {
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < K && e == cudaSuccess; ++s) {
     e = cudaMemsetAsync(b->d_work, 0, 4 * sizeof(int), b->stream);
-    if (pert) {
-      if (e == cudaSuccess) e = cudaEventRecord(b->ev_step, b->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_step, 0);
-      if (e == cudaSuccess) e = launch_batch_base(t, s, b->max_runs, b->max_ny, b->side);
-    }
     if (e == cudaSuccess) e = launch_batch_march(t, s, b->grid_march, pert, b->stream);
     if (e == cudaSuccess) e = launch_batch_rfft(t, s, b->grid_rows, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    if (pert) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side2, b->ev_fork, 0);
+      if (e == cudaSuccess) e = launch_batch_base(t, s, b->max_runs, b->max_ny, b->side2);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_base, b->side2);
+    }
     if (e == cudaSuccess) e = launch_batch_mean(t, s, b->grid_mean, b->side);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
     if (e == cudaSuccess) e = launch_batch_modes(t, s, b->grid_tiles, b->stream);
     if (e == cudaSuccess) e = launch_batch_irfft(t, s, b->grid_rows, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    if (pert && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_base, 0);
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -1377,7 +1405,8 @@ ehd_status ehd_batch_create(int max_runs, size_t hbm_budget, int max_nx, int max
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_step, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_base, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking) != cudaSuccess) {
     batch_free(b);
     return fail(EHD_ECUDA, "stream/event creation failed");
   }

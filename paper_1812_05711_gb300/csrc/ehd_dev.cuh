@@ -225,20 +225,32 @@ struct BaseArgs {
   double* fout;        // [9][Ny] at t + 1
   double* gout;
   const double* EB;    // [Ny] base E_y at time t
-  double wp, wm, gwp, gwm, mub, rho0;
-  double* flux_acc;    // [2] FP64 totals of injected / collected charge (base part added)
+  const double* mom;   // [5][Ny] rho, rho_c, u_x, u_y, u_y + mu_b E_y at time t
+  double wp, wm, gwp, gwm, mub, rho0, eps;
+  double cp, cm;       // force factors 1 - wp / 2, 1 - wm / 2
+  double* flux_acc;    // [2] FP64 totals of the base's injected / collected charge
+  double* sums;        // [4][Ny] rho_c, rho, j_y, j_x of the state at t + 1 (out)
+  double* rhs;         // [Ny] its mean-mode right-hand side -Nx rho_c / eps (out)
+  double* loc;         // [2][Ny] chunk-local prefix sums of rhs (out)
+  double* chunk;       // [2][base_chunks(Ny)] chunk totals (out)
 };
 struct BasePoissonArgs {
   int Nx, Ny, wall_mode;
-  const double* f;     // [9][Ny] base state whose potential is solved
-  const double* g;
-  double eps, phi0;
-  double* rhs;         // [Ny] scratch: the mean-mode right-hand side
+  double phi0, mub;
+  const double* rhs;   // [Ny] mean-mode right-hand side of the state
+  const double* sums;  // [4][Ny] its rho_c, rho, j_y, j_x
+  const double* loc;   // [2][Ny] and the chunk sums of the right-hand side
+  const double* chunk;
   double* phiB;        // [Ny] base potential (out)
   double* EB;          // [Ny] base E_y (out)
   float* table;        // [Ny][4] march table (out)
+  double* mom;         // [5][Ny] moments for the state's base step (out)
 };
+// rows per chunk of the base kernels: chunks of a run's base state
+int base_chunks(int Ny);
 cudaError_t launch_base_step(const BaseArgs& a, cudaStream_t s);
+// row sums and right-hand side of the state fin / gin (fout, gout unused)
+cudaError_t launch_base_sums(const BaseArgs& a, cudaStream_t s);
 cudaError_t launch_base_poisson(const BasePoissonArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------- batches ---
@@ -250,7 +262,7 @@ struct BatchRunDesc {
   StepArgs sa[2];    // [p]: step from buffer p to 1 - p
   PoissonArgs pa;    // Poisson solve of the run (with its wall fluxes)
   BaseArgs ba[2];    // perturbation form: the base step from buffer p (ba[p].fin == nullptr otherwise)
-  BasePoissonArgs bp[2];  // and the potential of its result (buffer 1 - p)
+  BasePoissonArgs bp[2];  // and the potential of its result (bp[p].sums == nullptr otherwise)
   int cur0;          // buffer holding the state at the start of the tick
   int remaining;     // steps the run still takes in this tick
   int E;             // Nx / 64: warp-FFT shape

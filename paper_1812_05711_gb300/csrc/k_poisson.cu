@@ -661,7 +661,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   const T T_all = block_prefix_sum<R, NT>(v, j0, j1, ms);   // T_Ny
   const T T_last = (Ny >= 2) ? v[Ny - 2] : N::from_f(0.0f);  // T_{Ny-1}
   // wall values in spectral units: W = Nx phi0 at the injector, 0 at the collector
-  const T W = N::mul(N::from_f((float)a.Nx), N::from_f((float)a.phi0));
+  const T W = N::from((double)a.Nx * a.phi0);
   T Dm, Pm;  // D_{-1}, phi_{-1}
   if (a.wall_mode == 0) {
     // phi_{-1} + phi_0 = 2W, phi_Ny + phi_{Ny-1} = 0
@@ -748,186 +748,421 @@ __global__ void __launch_bounds__(kMeanThreads) k_batch_mean(BatchTables t, int 
 
 
 // --------------------------------------------------- perturbation form ---
-// One step of the x-uniform base state in FP64, one thread per row: the
-// moments (Eqs. 5-7, E_x = 0), the fluid TRT collision with the force
-// rho_c E_y (Eqs. 8, 10, 12, 13, 15) and the charge TRT collision with the
-// drift u + mu_b E (Eqs. 9, 11, 14), then streaming in y (an x-uniform state
-// does not change under the x shifts) with the wall rules: halfway
-// bounce-back of f, anti-bounce-back injection of rho0 with the wall-node
-// drift, zero-gradient outflow of g (Table I).  Each (population, row) of
-// t + 1 has one writer.  The two wall rows add their charge fluxes, times Nx,
-// to the run's FP64 totals.
+// One step of the x-uniform base state in FP64: the moments (Eqs. 5-7,
+// E_x = 0), the fluid TRT collision with the force rho_c E_y (Eqs. 8, 10,
+// 12, 13, 15) and the charge TRT collision with the drift u + mu_b E
+// (Eqs. 9, 11, 14), then streaming in y (an x-uniform state does not change
+// under the x shifts) with the wall rules: halfway bounce-back of f,
+// anti-bounce-back injection of rho0 with the wall-node drift, zero-gradient
+// outflow of g (Table I).  The two wall rows add their charge fluxes, times
+// Nx, to the base's own FP64 totals.
+//
+// A CTA of four warps takes kBaseRows rows; lane l holds row y0 - 1 + l, so
+// lanes 0 and 31 are the halo rows whose post-collision populations stream
+// into the CTA.  Warp w collides one population group -- {0, 1, 3}, {2, 4},
+// {5, 7}, {6, 8}: each with its opposite, as the TRT split needs -- so the
+// FP64 work of a row is spread over four warps, and the new populations are
+// pulled from shared memory.  The row moments (rho, rho_c, u, the drift
+// velocity) come from the potential kernel of the previous step, which has
+// E_y; the CTA sums the new rows' rho_c, rho, j_x, j_y in population order.
+// (FP64 runs at a small fraction of the FP32 rate on this GPU: the split and
+// the precomputed moments keep each warp's FP64 instruction count low.)
 namespace {
 __device__ __forceinline__ double bw(int i) { return i == 0 ? kW0 : (i < 5 ? kW1 : kW2); }
 __device__ __forceinline__ int bcx(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
 __device__ __forceinline__ int bcy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
 __device__ __forceinline__ int bopp(int i) { return i == 0 ? 0 : (i < 5 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
-__device__ __forceinline__ double beq(int i, double dens, double vx, double vy) {
-  const double cu = bcx(i) * vx + bcy(i) * vy;
-  return bw(i) * dens * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (vx * vx + vy * vy));
+// c_q . v with the lattice direction known at compile time
+template <int Q>
+__device__ __forceinline__ double bcdot(double vx, double vy) {
+  constexpr int cx = (Q == 1 || Q == 5 || Q == 8) ? 1 : ((Q == 3 || Q == 6 || Q == 7) ? -1 : 0);
+  constexpr int cy = (Q == 2 || Q == 5 || Q == 6) ? 1 : ((Q == 4 || Q == 7 || Q == 8) ? -1 : 0);
+  if constexpr (cx == 0 && cy == 0) return 0.0;
+  else if constexpr (cx == 0) return cy > 0 ? vy : -vy;
+  else if constexpr (cy == 0) return cx > 0 ? vx : -vx;
+  else return (cx > 0 ? vx : -vx) + (cy > 0 ? vy : -vy);
+}
+// equilibrium (Eq. 12 / 14) with |v|^2 passed in
+template <int Q>
+__device__ __forceinline__ double beq(double dens, double vx, double vy, double v2) {
+  const double cu = bcdot<Q>(vx, vy);
+  return bw(Q) * dens * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * v2);
+}
+constexpr int kBaseRows = 30;
+// the groups' populations: {0, 1, 3}, {2, 4}, {5, 7}, {6, 8}
+__device__ __forceinline__ int bgroup_pop(int grp, int k) {
+  constexpr int pops[4][3] = {{0, 1, 3}, {2, 4, -1}, {5, 7, -1}, {6, 8, -1}};
+  return pops[grp][k];
 }
 }  // namespace
 
-// One compiled body serves the single-run and the batch kernels (not
-// inlined: the two kernels then share its rounding bit for bit).
-__device__ __noinline__ void base_step_row(const BaseArgs& a, int y) {
+struct BaseSmem {
+  double fp[9][32], gp[9][32];  // post-collision populations of the CTA's rows
+  double nf[9][32], ng[9][32];  // populations of t + 1 of its output rows
+  double qin[3];                // injected-charge terms of the populations 2, 5, 6
+};
+
+// The TRT collision of the population pair (I, O = opposite of I; I == O
+// for the rest population).  The odd parts of the pair are equal and
+// opposite, so one set of half sums serves both.  The force has no x part
+// (E_x = 0 in an x-uniform state): F_i = w_i (3 (c_iy - u_y) + 9 (c_i.u) c_iy) F_y.
+struct BaseRow {
+  double rho, rc, ux, uy, vy, Fy, u2, v2;
+};
+template <int I, int O>
+__device__ __forceinline__ void base_collide_pair(const BaseArgs& a, const BaseRow& b, int y, BaseSmem& sm,
+                                                  int lane) {
   const int Ny = a.Ny;
-  double f[9], g[9];
-  double rho = 0, jx = 0, jy = 0, rc = 0;
-  for (int i = 0; i < 9; ++i) {
-    f[i] = a.fin[i * Ny + y];
-    g[i] = a.gin[i * Ny + y];
-    rho += f[i];
-    jx += bcx(i) * f[i];
-    jy += bcy(i) * f[i];
-    rc += g[i];
+  const double fI = a.fin[I * Ny + y], fO = a.fin[O * Ny + y];
+  const double gI = a.gin[I * Ny + y], gO = a.gin[O * Ny + y];
+  const double feqI = beq<I>(b.rho, b.ux, b.uy, b.u2), feqO = beq<O>(b.rho, b.ux, b.uy, b.u2);
+  const double geqI = beq<I>(b.rc, b.ux, b.vy, b.v2), geqO = beq<O>(b.rc, b.ux, b.vy, b.v2);
+  constexpr int cyI = (I == 2 || I == 5 || I == 6) ? 1 : ((I == 4 || I == 7 || I == 8) ? -1 : 0);
+  const double cuI = bcdot<I>(b.ux, b.uy);
+  // F_O = w (3 (-c_y - u_y) + 9 (-c.u)(-c_y)) F_y
+  double FiI, FiO;
+  if constexpr (cyI == 0) {
+    FiI = bw(I) * ((0.0 - b.uy) * 3.0 * b.Fy);
+    FiO = bw(O) * ((0.0 - b.uy) * 3.0 * b.Fy);
+  } else {
+    const double c = (double)cyI;
+    FiI = bw(I) * (((c - b.uy) * 3.0 + cuI * c * 9.0) * b.Fy);
+    FiO = bw(O) * (((-c - b.uy) * 3.0 + cuI * c * 9.0) * b.Fy);
   }
-  const double Ey = a.EB[y];
-  const double Fx = 0.0, Fy = rc * Ey;
-  const double ux = (jx + 0.5 * Fx) / rho, uy = (jy + 0.5 * Fy) / rho;
-  const double vx = ux, vy = uy + a.mub * Ey;
-  double fp[9], gp[9], feq[9], geq[9], Fi[9];
-  for (int i = 0; i < 9; ++i) {
-    feq[i] = beq(i, rho, ux, uy);
-    geq[i] = beq(i, rc, vx, vy);
-    const double cu = bcx(i) * ux + bcy(i) * uy;
-    const double ax = (bcx(i) - ux) * 3.0 + cu * bcx(i) * 9.0;
-    const double ay = (bcy(i) - uy) * 3.0 + cu * bcy(i) * 9.0;
-    Fi[i] = bw(i) * (ax * Fx + ay * Fy);
+  const double fpl = 0.5 * (fI + fO), fmi = 0.5 * (fI - fO);
+  const double epl = 0.5 * (feqI + feqO), emi = 0.5 * (feqI - feqO);
+  const double Fpl = 0.5 * (FiI + FiO), Fmi = 0.5 * (FiI - FiO);
+  const double ev = a.wp * (fpl - epl), od = a.wm * (fmi - emi);
+  const double Fe = a.cp * Fpl, Fo = a.cm * Fmi;
+  sm.fp[I][lane] = fI - ev - od + Fe + Fo;
+  const double gpl = 0.5 * (gI + gO), gmi = 0.5 * (gI - gO);
+  const double hpl = 0.5 * (geqI + geqO), hmi = 0.5 * (geqI - geqO);
+  const double gev = a.gwp * (gpl - hpl), god = a.gwm * (gmi - hmi);
+  sm.gp[I][lane] = gI - gev - god;
+  if constexpr (I != O) {
+    sm.fp[O][lane] = fO - ev + od + Fe - Fo;
+    sm.gp[O][lane] = gO - gev + god;
   }
-  for (int i = 0; i < 9; ++i) {
-    const int o = bopp(i);
-    const double fpl = 0.5 * (f[i] + f[o]), fmi = 0.5 * (f[i] - f[o]);
-    const double epl = 0.5 * (feq[i] + feq[o]), emi = 0.5 * (feq[i] - feq[o]);
-    const double Fpl = 0.5 * (Fi[i] + Fi[o]), Fmi = 0.5 * (Fi[i] - Fi[o]);
-    fp[i] = f[i] - a.wp * (fpl - epl) - a.wm * (fmi - emi) + (1.0 - 0.5 * a.wp) * Fpl + (1.0 - 0.5 * a.wm) * Fmi;
-    const double gpl = 0.5 * (g[i] + g[o]), gmi = 0.5 * (g[i] - g[o]);
-    const double hpl = 0.5 * (geq[i] + geq[o]), hmi = 0.5 * (geq[i] - geq[o]);
-    gp[i] = g[i] - a.gwp * (gpl - hpl) - a.gwm * (gmi - hmi);
-  }
-  double qin = 0.0, qout = 0.0;
-  for (int i = 0; i < 9; ++i) {
-    const int yt = y + bcy(i), o = bopp(i);
-    if (yt >= 0 && yt < Ny) {
-      a.fout[i * Ny + yt] = fp[i];
-      a.gout[i * Ny + yt] = gp[i];
-    } else if (yt < 0) {
-      // injector: bounce-back of f; anti-bounce-back of g with the wall drift
-      a.fout[o * Ny + y] = fp[i];
-      const double wvx = 0.0, wvy = a.mub * Ey;
-      const double cv = bcx(o) * wvx + bcy(o) * wvy;
-      const double even = bw(o) * a.rho0 * (1.0 + 4.5 * cv * cv - 1.5 * (wvx * wvx + wvy * wvy));
-      const double gn = -gp[i] + 2.0 * even;
-      a.gout[o * Ny + y] = gn;
-      qin += gn - gp[i];
-    } else {
-      // collector: bounce-back of f; the charge leaves
-      a.fout[o * Ny + y] = fp[i];
-      qout += gp[i];
-    }
-    if (y == Ny - 1 && bcy(i) < 0) {
-      // outflow: the down-movers entering the top row are the row's own
-      a.gout[i * Ny + y] = gp[i];
-      qout -= gp[i];
-    }
-  }
-  if (y == 0) a.flux_acc[0] += (double)a.Nx * qin;
-  if (y == Ny - 1) a.flux_acc[1] += (double)a.Nx * qout;
 }
 
-__global__ void __launch_bounds__(32) k_base_step(BaseArgs a) {
-  const int y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (y < a.Ny) base_step_row(a, y);
+// The mean mode of the base's Poisson equation is a double prefix sum of the
+// right-hand side s over the rows (S_j = sum_{k<=j} s_k, T_j = sum_{k<j} S_k;
+// see mean_mode_body).  It is split over chunks of kBaseRows rows: the warp
+// that holds a chunk (lanes 1 .. kBaseRows, s = 0 on the other lanes) keeps
+// per row the chunk-local sums Sl_j, Tl_j, and per chunk its totals sigma =
+// sum of s and tau = sum of Sl; the potential kernel adds the sums of the
+// chunks before.
+__device__ __forceinline__ void base_chunk_scan(double s, bool valid, int lane, int c, int y, double* loc,
+                                                double* chunk, int Ny) {
+  double S = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, S, o);
+    if (lane >= o) S += u;
+  }
+  const double Sm = valid ? S : 0.0;
+  double Ti = Sm;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, Ti, o);
+    if (lane >= o) Ti += u;
+  }
+  double Tl = __shfl_up_sync(0xffffffffu, Ti, 1);
+  if (lane == 0) Tl = 0.0;
+  if (valid) {
+    loc[y] = S;
+    loc[Ny + y] = Tl;
+  }
+  if (lane == 31) {
+    chunk[2 * c] = S;
+    chunk[2 * c + 1] = Ti;
+  }
+}
+
+__device__ __noinline__ void base_step_cta(const BaseArgs& a, int y0, BaseSmem& sm) {
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5, Ny = a.Ny;
+  const int y = y0 - 1 + lane;
+  const int npop = grp == 0 ? 3 : 2;
+  if (y >= 0 && y < Ny) {
+    BaseRow b;
+    b.rho = a.mom[y];
+    b.rc = a.mom[Ny + y];
+    b.ux = a.mom[2 * Ny + y];
+    b.uy = a.mom[3 * Ny + y];
+    b.vy = a.mom[4 * Ny + y];
+    b.Fy = b.rc * a.EB[y];
+    b.u2 = b.ux * b.ux + b.uy * b.uy;
+    b.v2 = b.ux * b.ux + b.vy * b.vy;
+    switch (grp) {
+      case 0:
+        base_collide_pair<0, 0>(a, b, y, sm, lane);
+        base_collide_pair<1, 3>(a, b, y, sm, lane);
+        break;
+      case 1: base_collide_pair<2, 4>(a, b, y, sm, lane); break;
+      case 2: base_collide_pair<5, 7>(a, b, y, sm, lane); break;
+      default: base_collide_pair<6, 8>(a, b, y, sm, lane); break;
+    }
+  }
+  __syncthreads();
+  const bool out = lane >= 1 && lane <= kBaseRows && y < Ny;
+  if (out) {
+    for (int k = 0; k < npop; ++k) {
+      const int i = bgroup_pop(grp, k), cy = bcy(i);
+      double nf, ng;
+      if (cy == 0) {
+        nf = sm.fp[i][lane];
+        ng = sm.gp[i][lane];
+      } else if (cy > 0) {
+        if (y >= 1) {
+          nf = sm.fp[i][lane - 1];
+          ng = sm.gp[i][lane - 1];
+        } else {
+          // injector: bounce-back of f; anti-bounce-back of g with the wall drift (0, mu_b E_y)
+          const int d = bopp(i);
+          nf = sm.fp[d][lane];
+          const double wvy = a.mub * a.EB[0];
+          const double cv = bcy(i) * wvy;
+          const double even = bw(i) * a.rho0 * (1.0 + 4.5 * cv * cv - 1.5 * (wvy * wvy));
+          ng = -sm.gp[d][lane] + 2.0 * even;
+          sm.qin[i == 2 ? 0 : (i == 5 ? 1 : 2)] = ng - sm.gp[d][lane];
+        }
+      } else {
+        if (y <= Ny - 2) {
+          nf = sm.fp[i][lane + 1];
+          ng = sm.gp[i][lane + 1];
+        } else {
+          // collector: bounce-back of f; the up-movers leave, the down-movers
+          // entering the top row are its own (zero-gradient outflow)
+          nf = sm.fp[bopp(i)][lane];
+          ng = sm.gp[i][lane];
+        }
+      }
+      a.fout[i * Ny + y] = nf;
+      a.gout[i * Ny + y] = ng;
+      sm.nf[i][lane] = nf;
+      sm.ng[i][lane] = ng;
+    }
+  }
+  __syncthreads();
+  if (grp == 2) {
+    double s = 0.0;
+    if (out) {
+      double rc = 0;
+      for (int i = 0; i < 9; ++i) rc += sm.ng[i][lane];
+      a.sums[y] = rc;
+      s = -(double)a.Nx * rc / a.eps;
+      a.rhs[y] = s;
+    }
+    base_chunk_scan(s, out, lane, y0 / kBaseRows, y, a.loc, a.chunk, Ny);
+  }
+  if (out) {
+    if (grp == 0) {
+      double rho = 0;
+      for (int i = 0; i < 9; ++i) rho += sm.nf[i][lane];
+      a.sums[Ny + y] = rho;
+    } else if (grp == 1) {
+      double jy = 0;
+      for (int i = 0; i < 9; ++i) jy += bcy(i) * sm.nf[i][lane];
+      a.sums[2 * Ny + y] = jy;
+    } else if (grp == 3) {
+      double jx = 0;
+      for (int i = 0; i < 9; ++i) jx += bcx(i) * sm.nf[i][lane];
+      a.sums[3 * Ny + y] = jx;
+    }
+    if (grp == 3 && y == 0) {
+      // injected charge: the down-movers 4, 7, 8 reflected into 2, 5, 6
+      double qin = 0.0;
+      for (int k = 0; k < 3; ++k) qin += sm.qin[k];
+      a.flux_acc[0] += (double)a.Nx * qin;
+    }
+    if (grp == 3 && y == Ny - 1) {
+      // collected charge: up-movers out, minus the outflow's down-movers, in population order
+      const double qout = ((((sm.gp[2][lane] - sm.gp[4][lane]) + sm.gp[5][lane]) + sm.gp[6][lane]) - sm.gp[7][lane]) -
+                          sm.gp[8][lane];
+      a.flux_acc[1] += (double)a.Nx * qout;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_base_step(BaseArgs a) {
+  __shared__ BaseSmem sm;
+  base_step_cta(a, blockIdx.x * kBaseRows, sm);
+}
+
+// Row sums of a base state (at creation and after a load): rho_c, rho, j_y,
+// the mean-mode right-hand side and its chunk sums, as the step leaves them
+// (one warp per chunk of kBaseRows rows).
+__global__ void __launch_bounds__(32) k_base_sums(BaseArgs a) {
+  const int lane = threadIdx.x, Ny = a.Ny, c = blockIdx.x;
+  const int y = c * kBaseRows - 1 + lane;
+  const bool valid = lane >= 1 && lane <= kBaseRows && y < Ny;
+  double s = 0.0;
+  if (valid) {
+    double rho = 0, jy = 0, jx = 0, rc = 0;
+    for (int i = 0; i < 9; ++i) rho += a.fin[i * Ny + y];
+    for (int i = 0; i < 9; ++i) jy += bcy(i) * a.fin[i * Ny + y];
+    for (int i = 0; i < 9; ++i) jx += bcx(i) * a.fin[i * Ny + y];
+    for (int i = 0; i < 9; ++i) rc += a.gin[i * Ny + y];
+    a.sums[y] = rc;
+    a.sums[Ny + y] = rho;
+    a.sums[2 * Ny + y] = jy;
+    a.sums[3 * Ny + y] = jx;
+    s = -(double)a.Nx * rc / a.eps;
+    a.rhs[y] = s;
+  }
+  base_chunk_scan(s, valid, lane, c, y, a.loc, a.chunk, Ny);
 }
 
 // Potential of the base state (the mean mode of Eqs. 18-20 with the wall
-// potentials: the FP64 double prefix sum of k_mean_mode on the base's row
-// sums), and the march table of the state: per row the base charge, the
-// base fluid velocity u_y (Eq. 7) and the base field E_y, in FP32.
-__device__ __noinline__ void base_poisson_body(const BasePoissonArgs& b, unsigned char* smem_raw,
-                                               MeanScratch<double, 512>& ms) {
-  const int Ny = b.Ny;
-  for (int j = threadIdx.x; j < Ny; j += 512) {
-    double rc = 0;
-    for (int i = 0; i < 9; ++i) rc += b.g[i * Ny + j];
-    b.rhs[j] = -(double)b.Nx * rc / b.eps;
+// potentials, from the chunk sums: each warp scans the chunk totals, takes
+// the wall conditions as mean_mode_body does and writes phi, E_y for its
+// chunk's rows), and the march table of the state: per row the base
+// charge, the base fluid velocity u_y (Eq. 7; its numerator in FP64, the
+// quotient in FP32) and the base field E_y.
+__device__ __noinline__ void base_potential_warp(const BasePoissonArgs& b, int c) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, Ny = b.Ny;
+  const int nch = (Ny + kBaseRows - 1) / kBaseRows;
+  const int K = (nch + 31) / 32;
+  const int c0 = min(lane * K, nch), c1 = min(c0 + K, nch);
+  // S0_c = sum of sigma over the chunks before c
+  double acc = 0.0;
+  for (int cc = c0; cc < c1; ++cc) acc += b.chunk[2 * cc];
+  double incl = acc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += u;
   }
-  __syncthreads();
-  PoissonArgs a{};
-  a.Nx = b.Nx;
-  a.Ny = Ny;
-  a.spec0 = b.rhs;
-  a.phibar = b.phiB;
-  a.Ebar = b.EB;
-  a.phi0 = b.phi0;
-  a.wall_mode = b.wall_mode;
-  a.flux_part = nullptr;
-  mean_mode_body<double, 512>(a, smem_raw, ms);
-  __syncthreads();
-  for (int j = threadIdx.x; j < Ny; j += 512) {
-    double rho = 0, jy = 0, rc = 0;
-    for (int i = 0; i < 9; ++i) {
-      const double fi = b.f[i * Ny + j];
-      rho += fi;
-      jy += bcy(i) * fi;
-      rc += b.g[i * Ny + j];
+  double s0 = __shfl_up_sync(FULL, incl, 1);
+  if (lane == 0) s0 = 0.0;
+  // T0_c = sum over the chunks before c of (rows x S0 + tau)
+  double uacc = 0.0;
+  {
+    double sc = s0;
+    for (int cc = c0; cc < c1; ++cc) {
+      const int n = min(kBaseRows, Ny - cc * kBaseRows);
+      uacc += (double)n * sc + b.chunk[2 * cc + 1];
+      sc += b.chunk[2 * cc];
     }
-    const double Ey = b.EB[j];
+  }
+  double uincl = uacc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(FULL, uincl, o);
+    if (lane >= o) uincl += u;
+  }
+  double t0 = __shfl_up_sync(FULL, uincl, 1);
+  if (lane == 0) t0 = 0.0;
+  // S0, T0 of chunk c and of the last chunk, from the lanes that hold them
+  double S0c = 0, T0c = 0, S0L = 0, T0L = 0;
+  {
+    double sc = s0, tc = t0;
+    for (int cc = c0; cc < c1; ++cc) {
+      if (cc == c) {
+        S0c = sc;
+        T0c = tc;
+      }
+      if (cc == nch - 1) {
+        S0L = sc;
+        T0L = tc;
+      }
+      const int n = min(kBaseRows, Ny - cc * kBaseRows);
+      tc += (double)n * sc + b.chunk[2 * cc + 1];
+      sc += b.chunk[2 * cc];
+    }
+  }
+  S0c = __shfl_sync(FULL, S0c, c / K);
+  T0c = __shfl_sync(FULL, T0c, c / K);
+  S0L = __shfl_sync(FULL, S0L, (nch - 1) / K);
+  T0L = __shfl_sync(FULL, T0L, (nch - 1) / K);
+  // wall conditions (as mean_mode_body): T_{Ny-1}, S_{Ny-1}, T_Ny
+  const int jL = (nch - 1) * kBaseRows;
+  const double S_last = S0L + b.loc[Ny - 1];
+  const double T_last = (T0L + (double)(Ny - 1 - jL) * S0L) + b.loc[Ny + Ny - 1];
+  const double T_all = T_last + S_last;
+  const double W = (double)b.Nx * b.phi0;
+  double Dm, Pm;
+  if (b.wall_mode == 0) {
+    const double num = (W + W) + (T_all + T_last);
+    Dm = -num * (1.0 / (2.0 * Ny));
+    Pm = W + -(Dm * 0.5);
+  } else {
+    Dm = -(W + T_all) * (1.0 / (double)(Ny + 1));
+    Pm = W;
+  }
+  const int j0 = c * kBaseRows, j = j0 + lane;
+  const bool valid = lane < kBaseRows && j < Ny;
+  const double Sj = valid ? S0c + b.loc[j] : 0.0;
+  double Sjm1 = __shfl_up_sync(FULL, Sj, 1);
+  if (lane == 0) Sjm1 = (j > 0) ? S0c : 0.0;
+  if (valid) {
+    const double Tj = (T0c + (double)(j - j0) * S0c) + b.loc[Ny + j];
+    const double phi = (Pm + (double)(j + 1) * Dm) + Tj;
+    const double ey = -0.5 * ((Dm + Dm) + (Sj + Sjm1));
+    const double inN = 1.0 / (double)b.Nx;
+    b.phiB[j] = phi * inN;
+    const double Ey = ey * inN;
+    b.EB[j] = Ey;
+    // moments of the state for its next base step (Eq. 7 with F = rho_c E_y e_y)
+    const double rc = b.sums[j], rho = b.sums[Ny + j], jy = b.sums[2 * Ny + j], jx = b.sums[3 * Ny + j];
+    const double ux = jx / rho, uy = (jy + 0.5 * (rc * Ey)) / rho;
+    b.mom[j] = rho;
+    b.mom[Ny + j] = rc;
+    b.mom[2 * Ny + j] = ux;
+    b.mom[3 * Ny + j] = uy;
+    b.mom[4 * Ny + j] = uy + b.mub * Ey;
     b.table[4 * j + 0] = (float)rc;
-    b.table[4 * j + 1] = (float)((jy + 0.5 * rc * Ey) / rho);
+    b.table[4 * j + 1] = (float)uy;
     b.table[4 * j + 2] = (float)Ey;
     b.table[4 * j + 3] = 0.0f;
   }
 }
 
-__global__ void __launch_bounds__(512) k_base_poisson(BasePoissonArgs b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ MeanScratch<double, 512> ms;
-  base_poisson_body(b, smem_raw, ms);
-}
+__global__ void __launch_bounds__(32) k_base_poisson(BasePoissonArgs b) { base_potential_warp(b, blockIdx.x); }
 
 // Batch: the base step of every perturbation-form member (CTA (x, r): rows
-// 32 x .. of member r), then one CTA per member for its potential.
-__global__ void __launch_bounds__(32) k_batch_base_step(BatchTables t, int step) {
+// kBaseRows x .. of member r), then one CTA per member for its potential.
+__global__ void __launch_bounds__(128) k_batch_base_step(BatchTables t, int step) {
+  __shared__ BaseSmem sm;
   const int r = blockIdx.y;
   if (r >= t.counts[0]) return;
   const BatchRunDesc& rd = t.runs[r];
   if (step >= rd.remaining) return;
   const BaseArgs& a = rd.ba[rd.cur0 ^ (step & 1)];
-  if (!a.fin) return;
-  const int y = blockIdx.x * blockDim.x + threadIdx.x;
-  if (y < a.Ny) base_step_row(a, y);
+  if (!a.fin || (int)blockIdx.x * kBaseRows >= a.Ny) return;
+  base_step_cta(a, blockIdx.x * kBaseRows, sm);
 }
 
-__global__ void __launch_bounds__(512) k_batch_base_poisson(BatchTables t, int step) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ MeanScratch<double, 512> ms;
-  const int n = t.counts[0];
-  for (int r = blockIdx.x; r < n; r += gridDim.x) {
-    const BatchRunDesc& rd = t.runs[r];
-    if (step >= rd.remaining) continue;
-    const BasePoissonArgs& b = rd.bp[rd.cur0 ^ (step & 1)];
-    if (!b.f) continue;
-    base_poisson_body(b, smem_raw, ms);
-    __syncthreads();
-  }
+__global__ void __launch_bounds__(32) k_batch_base_poisson(BatchTables t, int step) {
+  const int r = blockIdx.y;
+  if (r >= t.counts[0]) return;
+  const BatchRunDesc& rd = t.runs[r];
+  if (step >= rd.remaining) return;
+  const BasePoissonArgs& b = rd.bp[rd.cur0 ^ (step & 1)];
+  if (!b.sums || (int)blockIdx.x * kBaseRows >= b.Ny) return;
+  base_potential_warp(b, blockIdx.x);
 }
 
 cudaError_t launch_batch_base(const BatchTables& t, int step, int maxr, int max_ny, cudaStream_t s) {
-  k_batch_base_step<<<dim3((max_ny + 31) / 32, maxr), 32, 0, s>>>(t, step);
+  const int nch = (max_ny + kBaseRows - 1) / kBaseRows;
+  k_batch_base_step<<<dim3(nch, maxr), 128, 0, s>>>(t, step);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_batch_base_poisson<<<std::min(maxr, 152), 512, 2 * (size_t)max_ny * sizeof(double), s>>>(t, step);
+  k_batch_base_poisson<<<dim3(nch, maxr), 32, 0, s>>>(t, step);
   return cudaGetLastError();
 }
 
+int base_chunks(int Ny) { return (Ny + kBaseRows - 1) / kBaseRows; }
+
 cudaError_t launch_base_step(const BaseArgs& a, cudaStream_t s) {
-  k_base_step<<<(a.Ny + 31) / 32, 32, 0, s>>>(a);
+  k_base_step<<<base_chunks(a.Ny), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_base_sums(const BaseArgs& a, cudaStream_t s) {
+  k_base_sums<<<base_chunks(a.Ny), 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_base_poisson(const BasePoissonArgs& a, cudaStream_t s) {
-  k_base_poisson<<<1, 512, 2 * (size_t)a.Ny * sizeof(double), s>>>(a);
+  k_base_poisson<<<base_chunks(a.Ny), 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1044,6 +1279,7 @@ cudaError_t allow_max_dynamic_smem(K kernel) {
 template <class R>
 cudaError_t set_attrs_t() {
   cudaError_t e;
+
   if ((e = allow_max_dynamic_smem(k_rfft_rows<R>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_irfft_rows<R>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_irfft_rows<R, true>)) != cudaSuccess) return e;
@@ -1079,8 +1315,6 @@ cudaError_t poisson_set_attributes() {
   if (e != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_modes)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_batch_mean)) != cudaSuccess) return e;
-  if ((e = allow_max_dynamic_smem(k_base_poisson)) != cudaSuccess) return e;
-  if ((e = allow_max_dynamic_smem(k_batch_base_poisson)) != cudaSuccess) return e;
   e = set_attrs_t<double>();
   if (e != cudaSuccess) return e;
   return set_attrs_t<float>();
