@@ -200,7 +200,10 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * (cp.async.bulk.tensor, 9 planes per copy) with mbarrier completion;
  * 2, the same and completed rows written by tensor stores from a
  * shared-memory tile; 3, tensor copies two rows ahead (three stages); the
- * same results bit for bit).
+ * same results bit for bit), EHD_TUNE_TILE_THREADS (threads per CTA of the
+ * mode solve, FP32 compute: 256, 512 or 1024; 0 = the default; more threads
+ * cut each wavenumber's rows into shorter chunks, so results differ in
+ * rounding order).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -212,6 +215,7 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_FFT_CTA 7
 #define EHD_TUNE_Y_SOLVER 8
 #define EHD_TUNE_MARCH_TMA 9
+#define EHD_TUNE_TILE_THREADS 10
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

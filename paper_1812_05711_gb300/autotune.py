@@ -75,6 +75,9 @@ def tune(batch, steps: int = 8, ticks: int = 4, use_cache: bool = True, verbose:
             for rf in (0.5, 1.0, 1.25):
                 cands.append({"slab_rows": rows, "march_ctas": max(1, int(base["march_ctas"] * mf)),
                               "row_ctas": max(1, int(base["row_ctas"] * rf)), "tile_ctas": base["tile_ctas"]})
+    # wavenumber-tile CTAs: the default (as many per SM as fit, up to four) and half of it
+    cands += [dict(c, tile_ctas=max(1, base["tile_ctas"] // 2)) for c in cands if c["march_ctas"] == base["march_ctas"]
+              and c["row_ctas"] == base["row_ctas"]]
     best, best_ms, t0 = None, float("inf"), time.perf_counter()
     for c in cands:
         for k, v in c.items():

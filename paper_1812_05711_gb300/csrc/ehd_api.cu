@@ -98,6 +98,7 @@ struct ehd_run {
   int ring_depth = 2;  // rows staged ahead in the march form
   int cols_per_lane = 2;
   int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
+  int tile_threads = 0;  // threads per CTA of the mode solve (0: 256)
   int pdl = 0;         // programmatic dependent launch between the Poisson kernels (off: see ehd_tune)
   int fft_cta = 1;     // rows of 2048: CTA-per-row transforms
   int y_solver = 0;    // y solve of m >= 1: 0 tridiagonal, 1 odd-extension transform
@@ -298,6 +299,7 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.nflux = r->nxb;
   a.flux_acc = r->small;
   a.tile_modes = r->tile_modes;
+  a.tile_threads = r->tile_threads;
   a.pdl = r->pdl;
   a.fft_cta = r->fft_cta;
   a.y_solver = r->y_solver;
@@ -927,6 +929,12 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
         return fail(EHD_EINVAL, "tile modes must be 0, 1, 2, 4 or 8");
       r->tile_modes = value;
       break;
+    case EHD_TUNE_TILE_THREADS:
+      if (value != 0 && value != 256 && value != 512 && value != 1024)
+        return fail(EHD_EINVAL, "tile threads must be 0, 256, 512 or 1024");
+      if (value > 256 && r->real_f64) return fail(EHD_EINVAL, "FP64 mode solves take 256 threads");
+      r->tile_threads = value;
+      break;
     case EHD_TUNE_PDL:
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "programmatic dependent launch must be 0 or 1");
       r->pdl = value;
@@ -992,6 +1000,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_STEP_KERNEL: return r->step_kernel;
     case EHD_TUNE_COLS_PER_LANE: return r->cols_per_lane;
     case EHD_TUNE_TILE_MODES: return r->tile_modes;
+    case EHD_TUNE_TILE_THREADS: return r->tile_threads;
     case EHD_TUNE_PDL: return r->pdl;
     case EHD_TUNE_FFT_CTA: return r->fft_cta;
     case EHD_TUNE_Y_SOLVER: return r->y_solver;
@@ -1315,8 +1324,9 @@ void batch_build_items(ehd_batch* b, int resident_warps) {
                    [&](size_t p, size_t q) { return b->members[p]->Nx > b->members[q]->Nx; });
   std::stable_sort(by_ny.begin(), by_ny.end(),
                    [&](size_t p, size_t q) { return b->members[p]->Ny > b->members[q]->Ny; });
+  // row items: 2048 / Nx rows of one run each (one warp's four-step transform)
   for (size_t i : by_nx)
-    for (int y = 0; y < b->members[i]->Ny; ++y) b->h_rows[nr++] = make_int2((int)i, y);
+    for (int y = 0; y < b->members[i]->Ny; y += 2048 / b->members[i]->Nx) b->h_rows[nr++] = make_int2((int)i, y);
   for (size_t i : by_ny)
     for (int m0 = 0; m0 < b->members[i]->Mh; m0 += kBatchTileModes) b->h_tiles[nt++] = make_int2((int)i, m0);
   b->h_counts[0] = (int)b->members.size();
@@ -1440,12 +1450,16 @@ ehd_status ehd_batch_create(int max_runs, size_t hbm_budget, int max_nx, int max
   }
   const int wps = march_warps_per_sm(1, false, 2, 2);
   b->grid_march = b->sms * std::max(1, wps / 4);
-  b->grid_rows = b->sms * 4;
-  b->grid_tiles = b->sms;
+  // row-transform CTAs: eight per SM take the items dynamically (64 uneven
+  // runs: 227.5 against 236.7 us per step with four)
+  b->grid_rows = b->sms * 8;
   b->grid_mean = std::min(max_runs, b->sms);
   // wavenumber tile (spectrum + pivots) of the tallest admissible run; the
   // mean-mode solve needs less
   b->modes_smem = max_ny * kBatchTileModes * (int)(sizeof(float2) + sizeof(float));
+  // as many tile CTAs as fit an SM, up to four (64 uneven runs up to 512 x
+  // 416: 238.5 us per step against 256.6 with one per SM)
+  b->grid_tiles = b->sms * std::max(1, std::min(4, batch_modes_ctas_per_sm(b->modes_smem)));
   *out = b;
   return EHD_OK;
 }

@@ -149,6 +149,7 @@ struct PoissonArgs {
   int nflux;
   double* flux_acc;          // [2] FP64 totals of injected / collected charge
   int tile_modes;            // wavenumbers per CTA of the mode solve (8, 4, 2, 1; 0 = largest that fits)
+  int tile_threads;          // threads per CTA of the mode solve (FP32: 256, 512, 1024; 0 = 256)
   int pdl;                   // launch the main-stream kernels with programmatic dependent launch
   int fft_cta;               // rows of 2048: one CTA of 64 threads per row (else one warp per row)
   // y solve of the wavenumbers m >= 1: 0 per-wavenumber tridiagonal (k_modes_tile),
@@ -294,6 +295,8 @@ cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStre
 cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s);
 cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s);
+// wavenumber-tile CTAs of the batch that fit one SM with `smem` bytes of tile
+int batch_modes_ctas_per_sm(int smem);
 // perturbation-form members: the FP64 base step and its potential
 cudaError_t launch_batch_base(const BatchTables& t, int step, int max_runs, int max_ny, cudaStream_t s);
 constexpr int kBatchTileModes = 8;

@@ -82,78 +82,110 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Four-step forward FFT of the warp's row held as (re[n2], im[n2]) in lane
-// n1; on return lane k2 < E holds X[k2 + E k1] in (ore[k1], oim[k1]).
-// tw: exp(-2 pi i q / N) for q < N (global); sm: this warp's E x 33 buffer.
+// Four-step forward FFT of rows of L = 32 E complex values, R <= 32 / E rows
+// per warp (R = 32 / E: every lane works in both stages).  First stage, per row r:
+// lane n1 holds z[n1 + 32 n2] (n2 < E) in (re, im), transforms over n2,
+// multiplies by W_L^(n1 k2) = W_N^(2 n1 k2) and writes row r E + k2 of the
+// warp's [32][33] buffer.  Second stage: lane r E + k2 reads its buffer row
+// and finishes with a 32-point FFT, holding X_r[k2 + E k1] in (ore[k1],
+// oim[k1]).  Per row the arithmetic is that of the one-row-per-warp form.
+// tw: exp(-2 pi i q / N) for q < N (global).
+
+// the first stage's twiddles of lane n1: powers of W_N^(2 n1), resynchronised
+// from the table every 4 steps
 template <int E>
-__device__ __forceinline__ void four_step(float (&re)[E], float (&im)[E], float (&ore)[32], float (&oim)[32],
-                                          const float2* __restrict__ tw, float2* sm, int lane) {
-  fft_reg<E>(re, im);
-  // twiddle W_L^(n1 k2) = W_N^(2 n1 k2): powers of W_N^(2 n1), resynchronised
-  // from the table every 4 steps
+__device__ __forceinline__ void four_step_twiddles(const float2* __restrict__ tw, int lane, float2 (&w)[E]) {
   constexpr int N = 64 * E;
   const float2 base = tw[(2 * lane) & (N - 1)];
-  float2 w = make_float2(1.0f, 0.0f);
+  float2 c = make_float2(1.0f, 0.0f);
 #pragma unroll
   for (int k2 = 0; k2 < E; ++k2) {
-    if (k2 > 0) w = ((k2 & 3) == 0) ? tw[(2 * lane * k2) & (N - 1)] : cm(w, base);
-    const float2 v = cm(make_float2(re[k2], im[k2]), w);
-    sm[k2 * 33 + lane] = v;
+    if (k2 > 0) c = ((k2 & 3) == 0) ? tw[(2 * lane * k2) & (N - 1)] : cm(c, base);
+    w[k2] = c;
   }
+}
+
+template <int E>
+__device__ __forceinline__ void four_step_first(float (&re)[E], float (&im)[E], const float2 (&w)[E], float2* sm,
+                                                int r, int lane) {
+  fft_reg<E>(re, im);
+#pragma unroll
+  for (int k2 = 0; k2 < E; ++k2) sm[(r * E + k2) * 33 + lane] = cm(make_float2(re[k2], im[k2]), w[k2]);
+}
+
+// RE = R E rows of the buffer are written; lanes above them repeat a row (and
+// their results are not used), so the buffer needs only RE rows
+template <int RE>
+__device__ __forceinline__ void four_step_second(float (&ore)[32], float (&oim)[32], const float2* sm, int lane) {
   __syncwarp();
-  const int src = (E == 32) ? lane : (lane & (E - 1));
+  const int src = lane & (RE - 1);
 #pragma unroll
   for (int n1 = 0; n1 < 32; ++n1) {
     const float2 v = sm[src * 33 + n1];
     ore[n1] = v.x;
     oim[n1] = v.y;
   }
-  __syncwarp();
+  __syncwarp();  // the buffer is free for the warp's next rows
   fft_reg<32>(ore, oim);
 }
 
 }  // namespace
 
-// Forward transform of row y by one warp; sm: the warp's E x 33 buffer.
-template <int E>
-__device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, float2* sm) {
+// Forward transform of rows y0 .. y0 + R - 1 (those below Ny; R <= 32 / E)
+// by one warp; sm: the warp's buffer of R E rows of 33.
+template <int E, int R>
+__device__ __forceinline__ void rfft_warp_rows(const PoissonArgs& a, int y0, float2* sm) {
+  static_assert(R >= 1 && R * E <= 32, "rows per warp");
   const int lane = threadIdx.x & 31;
   constexpr int L = 32 * E, N = 2 * L;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
-  const float2* rc2 = reinterpret_cast<const float2*>(static_cast<const float*>(a.rhoc) + (long long)y * a.P);
-  const float *rdn, *rup;
-  rhoc_partials<float>(a, y, rdn, rup);
   const float nieps = -(float)a.inv_eps;
-  // A row constant c0 is taken out before the transform (the differences are
-  // exact and small, so the rounding scales with the row's variation); only
-  // the m = 0 bin depends on it, and it is restored there in float-float.
-  const float* row = reinterpret_cast<const float*>(rc2);
-  float c0 = row[0];
-  if (rdn) c0 += rdn[0];
-  if (rup) c0 += rup[0];
-  float re[E], im[E];
+  float2 w[E];
+  four_step_twiddles<E>(tw, lane, w);
+  float myc0 = 0.0f;  // lane r keeps row r's constant
+  for (int r = 0; r < R; ++r) {
+    const int y = y0 + r;
+    if (y >= a.Ny) break;
+    const float2* rc2 = reinterpret_cast<const float2*>(static_cast<const float*>(a.rhoc) + (long long)y * a.P);
+    const float *rdn, *rup;
+    rhoc_partials<float>(a, y, rdn, rup);
+    // A row constant c0 is taken out before the transform (the differences
+    // are exact and small, so the rounding scales with the row's variation);
+    // only the m = 0 bin depends on it, and it is restored there in
+    // float-float.
+    const float* row = reinterpret_cast<const float*>(rc2);
+    float c0 = row[0];
+    if (rdn) c0 += rdn[0];
+    if (rup) c0 += rup[0];
+    float re[E], im[E];
 #pragma unroll
-  for (int n2 = 0; n2 < E; ++n2) {
-    float2 v = rc2[lane + 32 * n2];
-    if (rdn) {
-      const float2 d = reinterpret_cast<const float2*>(rdn)[lane + 32 * n2];
-      v.x += d.x;
-      v.y += d.y;
+    for (int n2 = 0; n2 < E; ++n2) {
+      float2 v = rc2[lane + 32 * n2];
+      if (rdn) {
+        const float2 d = reinterpret_cast<const float2*>(rdn)[lane + 32 * n2];
+        v.x += d.x;
+        v.y += d.y;
+      }
+      if (rup) {
+        const float2 u = reinterpret_cast<const float2*>(rup)[lane + 32 * n2];
+        v.x += u.x;
+        v.y += u.y;
+      }
+      re[n2] = (v.x - c0) * nieps;
+      im[n2] = (v.y - c0) * nieps;
     }
-    if (rup) {
-      const float2 u = reinterpret_cast<const float2*>(rup)[lane + 32 * n2];
-      v.x += u.x;
-      v.y += u.y;
-    }
-    re[n2] = (v.x - c0) * nieps;
-    im[n2] = (v.y - c0) * nieps;
+    four_step_first<E>(re, im, w, sm, r, lane);
+    if (lane == r) myc0 = c0;
   }
   float xr[32], xi[32];
-  four_step<E>(re, im, xr, xi, tw, sm, lane);
-  if (lane == 0) {
-    // m = 0 coefficient (Z0 sits in lane 0, k1 = 0), float-float:
-    // (Re Z0 + Im Z0) + N c0 (-1/eps), the product exact by the FMA
-    // two-product, N a power of two
+  four_step_second<R * E>(xr, xi, sm, lane);
+  const int r = lane / E, k2 = lane & (E - 1), y = y0 + r;
+  const bool live = r < R && y < a.Ny;
+  const float c0 = __shfl_sync(0xffffffffu, myc0, r < R ? r : 0);
+  if (k2 == 0 && live) {
+    // m = 0 coefficient (Z0 sits in lane k2 = 0 of the row's group, k1 = 0),
+    // float-float: (Re Z0 + Im Z0) + N c0 (-1/eps), the product exact by the
+    // FMA two-product, N a power of two
     float s, e;
     two_sum_f(xr[0], xi[0], s, e);
     const float p = c0 * nieps, pe = fmaf(c0, nieps, -p);
@@ -165,17 +197,17 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
     static_cast<float2*>(a.spec0)[y] = make_float2(s, e);
   }
   // untangle into the half spectrum: S[k] = E_k + W_N^k O_k,
-  // E_k = (Z[k] + Z*[L-k]) / 2, O_k = (Z[k] - Z*[L-k]) / (2i); lane k2 holds
-  // k = k2 + E k1, whose partner L - k sits in lane (E - k2) mod E at 31 - k1
-  // (lane 0: its own register (32 - k1) mod 32)
-  float2* spec = static_cast<float2*>(a.spec) + (long long)y * a.Mp;
-  const int partner = (E - lane) & (E - 1);
-  const float2 wk2 = tw[lane & (E - 1)];
+  // E_k = (Z[k] + Z*[L-k]) / 2, O_k = (Z[k] - Z*[L-k]) / (2i); lane k2 of the
+  // row's group holds k = k2 + E k1, whose partner L - k sits in the group's
+  // lane (E - k2) mod E at 31 - k1 (k2 = 0: its own register (32 - k1) mod 32)
+  float2* spec = static_cast<float2*>(a.spec) + (long long)(live ? y : 0) * a.Mp;
+  const int partner = (lane & ~(E - 1)) | ((E - k2) & (E - 1));
+  const float2 wk2 = tw[k2];
 #pragma unroll
   for (int k1 = 0; k1 < 32; ++k1) {
     float pr = __shfl_sync(0xffffffffu, xr[31 - k1], partner);
     float pi = __shfl_sync(0xffffffffu, xi[31 - k1], partner);
-    if (lane == 0) {
+    if (k2 == 0) {
       pr = xr[(32 - k1) & 31];
       pi = xi[(32 - k1) & 31];
     }
@@ -186,10 +218,10 @@ __device__ __forceinline__ void rfft_warp_body(const PoissonArgs& a, int y, floa
     const float2 O = make_float2(Dv.y, -Dv.x);
     const float2 wk = cm(wk2, c_w64[k1]);  // W_N^(k2 + E k1) = W_N^k2 W_64^k1
     const float2 Sk = make_float2(Ev.x + (wk.x * O.x - wk.y * O.y), Ev.y + (wk.x * O.y + wk.y * O.x));
-    const int k = lane + E * k1;
-    if (lane < E) spec[k] = (k == 0) ? make_float2(0.0f, 0.0f) : Sk;
+    const int k = k2 + E * k1;
+    if (live) spec[k] = (k == 0) ? make_float2(0.0f, 0.0f) : Sk;
   }
-  if (lane == 0) spec[L] = make_float2(xr[0] - xi[0], 0.0f);  // Nyquist: Re Z0 - Im Z0
+  if (k2 == 0 && live) spec[L] = make_float2(xr[0] - xi[0], 0.0f);  // Nyquist: Re Z0 - Im Z0
 }
 
 // Coefficient k of the half spectrum as the inverse transforms read it: phi_k,
@@ -207,37 +239,51 @@ __device__ __forceinline__ float2 spec_in(const float2* spec, int k, int L) {
   }
 }
 
-// Inverse transform of row y by one warp -> phi minus its row mean (DX: E_x).
-template <int E, bool DX = false>
-__device__ __forceinline__ void irfft_warp_body(const PoissonArgs& a, int y, float2* sm) {
+// Inverse transform of rows y0 .. y0 + R - 1 (those below Ny; R <= 32 / E)
+// by one warp -> phi minus its row mean (DX: E_x).
+template <int E, int R, bool DX = false>
+__device__ __forceinline__ void irfft_warp_rows(const PoissonArgs& a, int y0, float2* sm) {
+  static_assert(R >= 1 && R * E <= 32, "rows per warp");
   const int lane = threadIdx.x & 31;
   constexpr int L = 32 * E;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
-  const float2* spec = static_cast<const float2*>(a.spec) + (long long)y * a.Mp;
-  // conj(Z[n]) for n = lane + 32 n2, Z[k] = E_k + i O_k,
-  // E_k = (S[k] + S*[L-k]) / 2, O_k = (S[k] - S*[L-k]) / (2 W_N^k), S[0] := 0
+  float2 w[E];
+  four_step_twiddles<E>(tw, lane, w);
+  // W_N^k for k = lane + 32 n2
   const float2 wl = tw[lane];
-  float re[E], im[E];
+  float2 wk[E];
 #pragma unroll
-  for (int n2 = 0; n2 < E; ++n2) {
-    const int k = lane + 32 * n2;
-    const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec_in<DX>(spec, k, L);
-    const float2 sp = spec_in<DX>(spec, L - k, L);
-    const float2 sc = make_float2(sp.x, -sp.y);
-    const float2 Ev = make_float2(0.5f * (sk.x + sc.x), 0.5f * (sk.y + sc.y));
-    const float2 Dv = make_float2(0.5f * (sk.x - sc.x), 0.5f * (sk.y - sc.y));
-    const float2 wk = cm(wl, tw[32 * n2]);                         // W_N^k
-    const float2 O = cm(Dv, make_float2(wk.x, -wk.y));             // D / W^k
-    re[n2] = Ev.x - O.y;                                           // Re(E + i O)
-    im[n2] = -(Ev.y + O.x);                                        // -Im: conjugate
+  for (int n2 = 0; n2 < E; ++n2) wk[n2] = cm(wl, tw[32 * n2]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int y = y0 + r;
+    if (y >= a.Ny) break;
+    const float2* spec = static_cast<const float2*>(a.spec) + (long long)y * a.Mp;
+    // conj(Z[n]) for n = lane + 32 n2, Z[k] = E_k + i O_k,
+    // E_k = (S[k] + S*[L-k]) / 2, O_k = (S[k] - S*[L-k]) / (2 W_N^k), S[0] := 0
+    float re[E], im[E];
+#pragma unroll
+    for (int n2 = 0; n2 < E; ++n2) {
+      const int k = lane + 32 * n2;
+      const float2 sk = (k == 0) ? make_float2(0.0f, 0.0f) : spec_in<DX>(spec, k, L);
+      const float2 sp = spec_in<DX>(spec, L - k, L);
+      const float2 sc = make_float2(sp.x, -sp.y);
+      const float2 Ev = make_float2(0.5f * (sk.x + sc.x), 0.5f * (sk.y + sc.y));
+      const float2 Dv = make_float2(0.5f * (sk.x - sc.x), 0.5f * (sk.y - sc.y));
+      const float2 O = cm(Dv, make_float2(wk[n2].x, -wk[n2].y));  // D / W^k
+      re[n2] = Ev.x - O.y;                                        // Re(E + i O)
+      im[n2] = -(Ev.y + O.x);                                     // -Im: conjugate
+    }
+    four_step_first<E>(re, im, w, sm, r, lane);
   }
   float xr[32], xi[32];
-  four_step<E>(re, im, xr, xi, tw, sm, lane);
-  if (lane < E) {
+  four_step_second<R * E>(xr, xi, sm, lane);
+  const int r = lane / E, k2 = lane & (E - 1), y = y0 + r;
+  if (r < R && y < a.Ny) {
     float2* dphi2 = reinterpret_cast<float2*>(static_cast<float*>(DX ? a.ex : a.dphi) + (long long)y * a.P);
     const float inL = 1.0f / (float)L;
 #pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) dphi2[lane + E * k1] = make_float2(xr[k1] * inL, -xi[k1] * inL);
+    for (int k1 = 0; k1 < 32; ++k1) dphi2[k2 + E * k1] = make_float2(xr[k1] * inL, -xi[k1] * inL);
   }
 }
 
@@ -507,6 +553,9 @@ __global__ void __launch_bounds__(kCtaT) k_irfft_cta(PoissonArgs a) {
       dphi2[k1 + 16 * (4 * q + i) + 256 * d] = make_float2(zr[4 * d + i] * inL, -zi[4 * d + i] * inL);
 }
 
+// one warp per row: a single run's transforms are bound by latency, and
+// more warps in flight beat fuller ones (128 x 104: 16.1 against 28.7 us
+// per step with 32/E rows per warp)
 template <int E>
 __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
   __shared__ float2 smem[4][E * 33];
@@ -514,7 +563,7 @@ __global__ void __launch_bounds__(128) k_rfft_warp(PoissonArgs a) {
   grid_dep_launch();
   const int warp = threadIdx.x >> 5;
   const int y = blockIdx.x * 4 + warp;
-  if (y < a.Ny) rfft_warp_body<E>(a, y, smem[warp]);
+  if (y < a.Ny) rfft_warp_rows<E, 1>(a, y, smem[warp]);
 }
 
 template <int E, bool DX = false>
@@ -524,17 +573,17 @@ __global__ void __launch_bounds__(128) k_irfft_warp(PoissonArgs a) {
   grid_dep_launch();
   const int warp = threadIdx.x >> 5;
   const int y = blockIdx.x * 4 + warp;
-  if (y < a.Ny) irfft_warp_body<E, DX>(a, y, smem[warp]);
+  if (y < a.Ny) irfft_warp_rows<E, 1, DX>(a, y, smem[warp]);
 }
 
-// Batch: warps of a fixed grid take row items (run, y); the row length picks
-// the transform shape.
+// Batch: warps of a fixed grid take row items (run, y0: the run's rows y0 ..
+// y0 + 2048/Nx - 1); the row length picks the transform shape.
 // EMAX: the widest row shape of the batch (Nx / 64); narrower batches get an
-// instance with less shared memory (and, for the inverse up to EMAX = 8, at
-// most 102 registers: five CTAs per SM), so more row FFTs run at once.
+// instance with fewer registers (the inverse up to EMAX = 8 at most 102:
+// five CTAs per SM), so more row FFTs run at once.
 template <bool INV, int EMAX>
 __device__ __forceinline__ void batch_fft_body(const BatchTables& t, int step) {
-  __shared__ float2 smem[4][EMAX * 33];
+  __shared__ float2 smem[4][32 * 33];
   const int warp = threadIdx.x >> 5;
   const int n = t.counts[2];
   int* counter = t.work + (INV ? 3 : 1);
@@ -545,21 +594,21 @@ __device__ __forceinline__ void batch_fft_body(const BatchTables& t, int step) {
     const PoissonArgs a = rd.pa;
     float2* sm = smem[warp];
     switch (rd.E) {
-      case 1: INV ? irfft_warp_body<1>(a, w.y, sm) : rfft_warp_body<1>(a, w.y, sm); break;
+      case 1: INV ? irfft_warp_rows<1, 32>(a, w.y, sm) : rfft_warp_rows<1, 32>(a, w.y, sm); break;
       case 2:
-        if constexpr (EMAX >= 2) INV ? irfft_warp_body<2>(a, w.y, sm) : rfft_warp_body<2>(a, w.y, sm);
+        if constexpr (EMAX >= 2) INV ? irfft_warp_rows<2, 16>(a, w.y, sm) : rfft_warp_rows<2, 16>(a, w.y, sm);
         break;
       case 4:
-        if constexpr (EMAX >= 4) INV ? irfft_warp_body<4>(a, w.y, sm) : rfft_warp_body<4>(a, w.y, sm);
+        if constexpr (EMAX >= 4) INV ? irfft_warp_rows<4, 8>(a, w.y, sm) : rfft_warp_rows<4, 8>(a, w.y, sm);
         break;
       case 8:
-        if constexpr (EMAX >= 8) INV ? irfft_warp_body<8>(a, w.y, sm) : rfft_warp_body<8>(a, w.y, sm);
+        if constexpr (EMAX >= 8) INV ? irfft_warp_rows<8, 4>(a, w.y, sm) : rfft_warp_rows<8, 4>(a, w.y, sm);
         break;
       case 16:
-        if constexpr (EMAX >= 16) INV ? irfft_warp_body<16>(a, w.y, sm) : rfft_warp_body<16>(a, w.y, sm);
+        if constexpr (EMAX >= 16) INV ? irfft_warp_rows<16, 2>(a, w.y, sm) : rfft_warp_rows<16, 2>(a, w.y, sm);
         break;
       default:
-        if constexpr (EMAX >= 32) INV ? irfft_warp_body<32>(a, w.y, sm) : rfft_warp_body<32>(a, w.y, sm);
+        if constexpr (EMAX >= 32) INV ? irfft_warp_rows<32, 1>(a, w.y, sm) : rfft_warp_rows<32, 1>(a, w.y, sm);
         break;
     }
   }
@@ -615,6 +664,7 @@ cudaError_t fftw_set_tables() {
 }
 
 bool fftw_supported(int Nx) { return Nx >= 64 && Nx <= 2048; }
+
 
 cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);

@@ -474,13 +474,13 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
 // threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
 constexpr int kTileThreads = 256;
 
-template <class R, int MB>
-__global__ void __launch_bounds__(kTileThreads) k_modes_tile(PoissonArgs a) {
+template <class R, int MB, int NT = kTileThreads>
+__global__ void __launch_bounds__(NT) k_modes_tile(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ TileScratch<R, MB, kTileThreads> ts;
+  __shared__ TileScratch<R, MB, NT> ts;
   grid_dep_wait();
   grid_dep_launch();
-  modes_tile_body<R, MB, kTileThreads>(a, blockIdx.x * MB, smem_raw, ts);
+  modes_tile_body<R, MB, NT>(a, blockIdx.x * MB, smem_raw, ts);
 }
 
 // Float-float ("double-single") numbers for the FP32 path: value = hi + lo
@@ -1187,6 +1187,23 @@ cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
   const size_t sm = (size_t)a.Ny * mb * (sizeof(Cplx<R>) + sizeof(R));
   const int nm = a.Mh;  // tiles start at m = 0
   const bool pdl = a.pdl != 0;
+  if constexpr (sizeof(R) == 4) {
+    if (a.tile_threads == 512 || a.tile_threads == 1024) {
+      const bool big = a.tile_threads == 1024;
+      switch (mb) {
+        case 8:
+          return big ? launch_ex(pdl, k_modes_tile<R, 8, 1024>, dim3((nm + 7) / 8), dim3(1024), sm, s, a)
+                     : launch_ex(pdl, k_modes_tile<R, 8, 512>, dim3((nm + 7) / 8), dim3(512), sm, s, a);
+        case 4:
+          return big ? launch_ex(pdl, k_modes_tile<R, 4, 1024>, dim3((nm + 3) / 4), dim3(1024), sm, s, a)
+                     : launch_ex(pdl, k_modes_tile<R, 4, 512>, dim3((nm + 3) / 4), dim3(512), sm, s, a);
+        case 2:
+          return big ? launch_ex(pdl, k_modes_tile<R, 2, 1024>, dim3((nm + 1) / 2), dim3(1024), sm, s, a)
+                     : launch_ex(pdl, k_modes_tile<R, 2, 512>, dim3((nm + 1) / 2), dim3(512), sm, s, a);
+        default: break;
+      }
+    }
+  }
   switch (mb) {
     case 8: return launch_ex(pdl, k_modes_tile<R, 8>, dim3((nm + 7) / 8), dim3(kTileThreads), sm, s, a);
     case 4: return launch_ex(pdl, k_modes_tile<R, 4>, dim3((nm + 3) / 4), dim3(kTileThreads), sm, s, a);
@@ -1285,6 +1302,14 @@ cudaError_t set_attrs_t() {
   if ((e = allow_max_dynamic_smem(k_irfft_rows<R, true>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreads>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreadsSmall>)) != cudaSuccess) return e;
+  if constexpr (sizeof(R) == 4) {
+    if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8, 512>)) != cudaSuccess) return e;
+    if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4, 512>)) != cudaSuccess) return e;
+    if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2, 512>)) != cudaSuccess) return e;
+    if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8, 1024>)) != cudaSuccess) return e;
+    if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4, 1024>)) != cudaSuccess) return e;
+    if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2, 1024>)) != cudaSuccess) return e;
+  }
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2>)) != cudaSuccess) return e;
@@ -1299,6 +1324,14 @@ cudaError_t rhoc_t(const void* g, long long plane, int Nx, int Ny, int P, const 
 }
 
 }  // namespace
+
+int batch_modes_ctas_per_sm(int smem) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_modes, kTileThreads, (size_t)smem) !=
+      cudaSuccess)
+    return 1;
+  return blocks;
+}
 
 cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s) {
   k_batch_modes<<<grid, kTileThreads, t.modes_smem, s>>>(t, step);
