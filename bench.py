@@ -49,7 +49,7 @@ K4_BYTES_PER_NODE = {"f32": 36 * 4 + 8, "f64": 36 * 8 + 16, "bf16": 36 * 2 + 8, 
 # the fused step kernel, from an ncu capture of the 2048 x 1680 FP32 channel;
 # keyed by a hash of the kernel's sources so that it reads null once the
 # kernel has changed since the capture.
-NCU_TRAFFIC = {("f32", "bca5d93e4c68231d"): 263.252480e6 + 211.006208e6}
+NCU_TRAFFIC = {("f32", "ac7f37d68fe9a1df"): 263.293952e6 + 211.490304e6}
 
 
 def _kernel_hash():
@@ -258,7 +258,10 @@ def run_ours(args):
     storage = args.storage
     w = wl.large_channel()
     cells = w.Nx * w.Ny
-    run = ehd.Run(*w.args(), storage=storage, amp=w.amp, phase=w.phase)
+    pert = 1 if getattr(args, "perturbation", False) else 0
+    if pert and storage == "f64":
+        raise SystemExit("--perturbation takes FP32 compute (storage f32, bf16 or f16)")
+    run = ehd.Run(*w.args(), storage=storage, amp=w.amp, phase=w.phase, perturbation=pert)
     h = run.handle
     stream = torch.cuda.ExternalStream(ehd.ehd_stream(h))
     f0, g0 = run.save()  # initial state, kept for the end-to-end leg
@@ -289,6 +292,10 @@ def run_ours(args):
     bytes_k4 = K4_BYTES_PER_NODE[storage] * cells
     peak, peak_kind = _peaks()
     achieved = bytes_k4 / (k4_ms * 1e-3) / 1e9
+    # whole coupled step: the step kernel's bytes plus phi read and rho_c written
+    # once more by the Poisson chain's transforms (160 B per node in FP32)
+    step_bytes = (K4_BYTES_PER_NODE[storage] + 8) * cells
+    step_achieved = step_bytes / (ms_max / args.steps * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned)
     pin_f = torch.empty(f0.shape, dtype=torch.float64, pin_memory=True).numpy()
@@ -327,16 +334,20 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": w.name, "Nx": w.Nx, "Ny": w.Ny, "T": round(w.T, 6), "C": w.C, "M": w.M,
                    "Fe": w.Fe, "Lambda": w.Lambda, "storage": storage, "compute": "f32" if storage != "f64" else "f64",
+                "form": "perturbation" if pert else ("shifted" if storage != "f64" else "plain"),
                    "per_rank": "one independent run", "l2": "state 495 MB > 129 MB L2, no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((storage, _kernel_hash())) if w.name == "channel-2048x1680" else None,
+                     "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((storage, _kernel_hash())) if w.name == "channel-2048x1680" and not pert else None,
                      "traffic_unit": "bytes per launch, ncu dram read + write", "kernel": "k_march2 (fused collide-stream)",
                      "bytes_per_node": K4_BYTES_PER_NODE[storage], "kernel_ms": k4_ms,
                      "peak_kind": f"{peak_kind} hbm_gbs", "poisson_ms": prof["poisson_ms"] / args.steps,
                      "charge_ms": prof["charge_ms"] / args.steps,
-                     "profiled_step_ms": prof["step_ms"] / args.steps},
+                     "profiled_step_ms": prof["step_ms"] / args.steps,
+                     "whole_step": {"bytes_per_node": K4_BYTES_PER_NODE[storage] + 8, "achieved": step_achieved,
+                                    "frac": step_achieved / peak}},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": (LAUNCHES_PER_STEP + 2 * pert) * args.steps,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "check": {"mass": diag["mass"], "charge": diag["charge"], "max_u": diag["max_u"]},
@@ -743,6 +754,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--perturbation", action="store_true",
+                    help="channel: the FP32 perturbation form (charge populations as departures from an FP64 "
+                         "x-uniform base state)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="channel",
                     choices=["channel", "batch", "serve", "fp64", "precision", "hydrostatic", "bifurcation",
