@@ -126,6 +126,13 @@ typedef struct {
                        central-difference E_x.  Batches take such runs
                        beside plain ones (their base states advance on the
                        batch's second stream). */
+  int dc_printed;   /* charge relaxation rates: 0 (default) D_c = cs2
+                       (tau_g- - 1/2), the antisymmetric rate carrying the
+                       charge flux; 1 Eq. 16 as printed, D_c = cs2 (tau_g+ -
+                       1/2), tau_g- then from lambda_g (Eq. 17), so the
+                       scheme's own diffusivity is cs2 lambda_g / (tau_g+ -
+                       1/2) rather than D_c.  For measuring what the printed
+                       assignment does to the results. */
 } ehd_options;
 
 /* Fill *opt with the defaults above. */

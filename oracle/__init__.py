@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
         ("Lambda", ctypes.c_double), ("Lambda_g", ctypes.c_double),
         ("u_ion", ctypes.c_double),
         ("wall_mode", ctypes.c_int), ("x_symbol", ctypes.c_int),
-        ("ex_spectral", ctypes.c_int),
+        ("ex_spectral", ctypes.c_int), ("dc_printed", ctypes.c_int),
         ("periodic_y", ctypes.c_int), ("no_poisson", ctypes.c_int),
         ("no_force", ctypes.c_int),
         ("ext_E", ctypes.c_double * 2), ("ext_F", ctypes.c_double * 2),
@@ -165,7 +165,7 @@ def _dp(a: np.ndarray):
 
 def setup(Nx, Ny, T, C, M, Fe, Lambda, Lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
           periodic_y=0, no_poisson=0, no_force=0, ext_E=(0.0, 0.0),
-          ext_F=(0.0, 0.0), x_symbol=0, ex_spectral=0) -> Params:
+          ext_F=(0.0, 0.0), x_symbol=0, ex_spectral=0, dc_printed=0) -> Params:
     p = Params()
     p.Nx, p.Ny = int(Nx), int(Ny)
     p.T, p.C, p.M, p.Fe = float(T), float(C), float(M), float(Fe)
@@ -173,6 +173,7 @@ def setup(Nx, Ny, T, C, M, Fe, Lambda, Lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
     p.wall_mode = int(wall_mode)
     p.x_symbol = int(x_symbol)
     p.ex_spectral = int(ex_spectral)
+    p.dc_printed = int(dc_printed)
     p.periodic_y, p.no_poisson, p.no_force = int(periodic_y), int(no_poisson), int(no_force)
     p.ext_E[0], p.ext_E[1] = float(ext_E[0]), float(ext_E[1])
     p.ext_F[0], p.ext_F[1] = float(ext_F[0]), float(ext_F[1])

@@ -135,10 +135,16 @@ int orc_setup(orc_params* p) {
    * printed names the symmetric rate, which would make the effective
    * diffusivity cs2 Lambda_g / (tau_g+ - 1/2) instead of the Dc of Eq. 26. */
   p->tau_p = p->nu / CS2 + 0.5;
-  p->taug_m = p->Dc / CS2 + 0.5;
   /* Eq. 17: Lambda = (tau+ - 1/2)(tau- - 1/2), same for the charge */
   p->tau_m = 0.5 + p->Lambda / (p->tau_p - 0.5);
-  p->taug_p = 0.5 + p->Lambda_g / (p->taug_m - 0.5);
+  if (p->dc_printed) {
+    /* Eq. 16 as printed: the symmetric charge rate carries D_c */
+    p->taug_p = p->Dc / CS2 + 0.5;
+    p->taug_m = 0.5 + p->Lambda_g / (p->taug_p - 0.5);
+  } else {
+    p->taug_m = p->Dc / CS2 + 0.5;
+    p->taug_p = 0.5 + p->Lambda_g / (p->taug_m - 0.5);
+  }
   if (orc_hydrostatic_params(p->rho0, p->eps, p->H, p->dphi0, &p->rho_a,
                              &p->y_a) != 0)
     return -1;

@@ -21,6 +21,9 @@ typedef struct {
                           symbol of the 3-point stencil (Eq. 24's form in x) */
   int ex_spectral;     /* E_x = -d phi / dx: 0 central difference, 1 spectral
                           (-i k_m times the x-transform of phi, Nyquist mode 0) */
+  int dc_printed;      /* charge rates: 0 D_c = cs2 (tau_g- - 1/2) (the reading
+                          used throughout), 1 Eq. 16 as printed, D_c = cs2
+                          (tau_g+ - 1/2), with Lambda_g then fixing tau_g- */
   /* hooks used only by the oracle's own pins (all zero for the method) */
   int periodic_y;      /* y periodic, no walls (requires no_poisson) */
   int no_poisson;      /* E = ext_E instead of -grad phi */

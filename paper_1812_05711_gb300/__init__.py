@@ -56,6 +56,7 @@ class Options(ctypes.Structure):
         ("x_symbol", ctypes.c_int),
         ("ex_spectral", ctypes.c_int),
         ("perturbation", ctypes.c_int),
+        ("dc_printed", ctypes.c_int),
     ]
 
 
@@ -273,7 +274,7 @@ def ehd_last_error() -> str:
 # ------------------------------------------------------------ convenience
 def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mode=0,
                  amp=(), phase=(), stream=None, step_kernel=-1, x_symbol=0, ex_spectral=0,
-                 perturbation=0) -> Options:
+                 perturbation=0, dc_printed=0) -> Options:
     o = ehd_default_options()
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     if compute is None:
@@ -294,6 +295,7 @@ def make_options(storage="f32", compute=None, lambda_g=1e-6, u_ion=2e-3, wall_mo
     o.x_symbol = int(x_symbol)
     o.ex_spectral = int(ex_spectral)
     o.perturbation = int(perturbation)
+    o.dc_printed = int(dc_printed)
     return o
 
 
@@ -305,11 +307,12 @@ class Run:
     may force "f32" on FP64 storage.  ``amp``/``phase``: Eq. 29 x-modes.
     ``perturbation=1`` (FP32 compute): the charge populations are stored and
     collided as departures from an x-uniform base state advanced in FP64.
+    ``dc_printed=1``: the charge rates of Eq. 16 as printed (D_c on tau_g+).
     """
 
     def __init__(self, Nx, Ny, T, C, M, Fe, Lambda, storage="f32", compute=None, lambda_g=1e-6,
                  u_ion=2e-3, wall_mode=0, amp=(), phase=(), stream=None, torch_stream=True, step_kernel=-1,
-                 x_symbol=0, ex_spectral=0, perturbation=0):
+                 x_symbol=0, ex_spectral=0, perturbation=0, dc_printed=0):
         self.Nx, self.Ny = int(Nx), int(Ny)
         self._stream_obj = None
         if stream is None and torch_stream:
@@ -317,7 +320,7 @@ class Run:
             self._stream_obj = torch.cuda.Stream()
             stream = self._stream_obj.cuda_stream
         opt = make_options(storage, compute, lambda_g, u_ion, wall_mode, amp, phase, stream, step_kernel, x_symbol,
-                           ex_spectral, perturbation)
+                           ex_spectral, perturbation, dc_printed)
         self.handle = ehd_create(Nx, Ny, T, C, M, Fe, Lambda, opt)
 
     # lifecycle

@@ -511,6 +511,7 @@ void ehd_default_options(ehd_options* o) {
   o->n_modes = 0;
   o->stream = nullptr;
   o->perturbation = 0;
+  o->dc_printed = 0;
 }
 
 const char* ehd_last_error(void) { return g_err.c_str(); }
@@ -615,8 +616,13 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   // charge flux relaxes with the antisymmetric rate, which carries Dc
   r->tau_p = 3.0 * r->nu + 0.5;
   r->tau_m = 0.5 + Lambda / (r->tau_p - 0.5);
-  r->taug_m = 3.0 * r->Dc + 0.5;
-  r->taug_p = 0.5 + o.lambda_g / (r->taug_m - 0.5);
+  if (o.dc_printed) {  // Eq. 16 as printed: the symmetric charge rate carries Dc
+    r->taug_p = 3.0 * r->Dc + 0.5;
+    r->taug_m = 0.5 + o.lambda_g / (r->taug_p - 0.5);
+  } else {
+    r->taug_m = 3.0 * r->Dc + 0.5;
+    r->taug_p = 0.5 + o.lambda_g / (r->taug_m - 0.5);
+  }
   if (r->tau_p > 50.0 || r->tau_m > 50.0 || r->taug_p > 50.0 || r->taug_m > 50.0) {
     ehd_status st0 = fail(EHD_EINVAL, "relaxation time above 50 (tau+ %.3g, tau- %.3g, tau_g+ %.3g, tau_g- %.3g)",
                           r->tau_p, r->tau_m, r->taug_p, r->taug_m);

@@ -390,6 +390,40 @@ def test_charge_diffusivity_and_drift(drift):
     assert np.log2(rel[-2] / rel[-1]) > 1.8, rel
 
 
+def test_charge_diffusivity_with_eq16_as_printed():
+    """Eq. 16 as printed (dc_printed = 1) hands D_c = mu_b dphi0 / Fe to the
+    symmetric charge rate, tau_g+ - 1/2 = D_c / cs2, and Lambda_g (Eq. 17)
+    then fixes tau_g-.  The scheme's diffusivity is cs2 (tau_g- - 1/2) =
+    cs2 Lambda_g / (tau_g+ - 1/2) either way: a charge wave decays at that
+    rate (second order in the wave's resolution), 3.3 times D_c here, which is
+    why the method's own reading gives D_c to tau_g-."""
+    cx, cy, w, opp = o.lattice()
+    rel = []
+    for L in (32, 64):
+        Dc, u_ion = 0.01, 0.01
+        p = o.setup(L, 4, 200, 10, 10, u_ion * 4 / Dc, 0.25, Lambda_g=3e-3, u_ion=u_ion, periodic_y=1,
+                    no_poisson=1, no_force=1, dc_printed=1)
+        assert p.taug_p - 0.5 == pytest.approx(3 * p.Dc, rel=1e-14)
+        assert (p.taug_p - 0.5) * (p.taug_m - 0.5) == pytest.approx(3e-3, rel=1e-14)
+        x = np.arange(L)
+        k = 2 * np.pi / L
+        rc = 1.0 + 1e-3 * np.cos(k * x)
+        f = w[:, None, None] * np.ones((9, 4, L))
+        g = w[:, None, None] * rc[None, None, :] * np.ones((9, 4, L))
+        s = o.state_from(p, f, g)
+        o.step(s, 50)
+        c0 = (o.fields(s)["rho_c"][0] - 1.0) @ np.exp(-1j * k * x)
+        D_eff = 3e-3 / (3 * p.Dc) / 3.0  # cs2 Lambda_g / (tau_g+ - 1/2)
+        n = int(0.3 / (D_eff * k * k))
+        o.step(s, n)
+        c1 = (o.fields(s)["rho_c"][0] - 1.0) @ np.exp(-1j * k * x)
+        D_m = -np.log(abs(c1 / c0)) / (n * k * k)
+        rel.append(abs(D_m / D_eff - 1))
+        assert D_m / p.Dc > 3.0
+    assert rel[-1] < 1e-3, rel
+    assert np.log2(rel[-2] / rel[-1]) > 1.8, rel
+
+
 # ------------------------------------------------------------ conservation ---
 def test_conservation_mass_and_charge_identity():
     """f: bounce-back and periodic streaming conserve mass exactly.  g: the
