@@ -186,12 +186,13 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * EHD_TUNE_COLS_PER_LANE (march form: 1 or 2 adjacent nodes per lane),
  * EHD_TUNE_TILE_MODES (wavenumbers per CTA of the mode solve: 1, 2, 4, 8;
  * 0 = the largest whose tile fits in shared memory; other widths change the
- * scans' chunking, so results then differ from batch members' in rounding), EHD_TUNE_PDL (1: the
- * Poisson kernels are launched with programmatic dependent launch, so each
- * is resident and waiting when its predecessor ends, which shortens steps of
- * small grids, the default up to 2^18 nodes; 0, the default above: plain
- * stream order, since early-resident CTAs unbalance the one-wave grids of
- * large runs), EHD_TUNE_FFT_CTA (FP32 rows
+ * scans' chunking, so results then differ from batch members' in rounding), EHD_TUNE_PDL (a mask
+ * of the Poisson kernels launched with programmatic dependent launch, so that
+ * each is resident and waiting when its predecessor ends: 1 the forward row
+ * transform, 2 the wavenumber solve, 4 the inverse transform; 7, the default
+ * up to 2^18 nodes, shortens steps of small grids; 3, the default above: the
+ * inverse transform's early-resident CTAs would crowd the wavenumber solve
+ * of large runs), EHD_TUNE_FFT_CTA (FP32 rows
  * of 2048: 1, the default, one CTA of 64 threads per row; 0, one warp per
  * row), EHD_TUNE_Y_SOLVER (the y solve of the wavenumbers m >= 1: 0, the
  * default, one tridiagonal per wavenumber (Eq. 18); 1, the literal form of

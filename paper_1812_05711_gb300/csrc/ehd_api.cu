@@ -705,10 +705,12 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     r->bmom = static_cast<double*>(run_alloc(r, 5 * (size_t)Ny * sizeof(double)));
   }
   r->step_kernel = (o.step_kernel >= 0) ? o.step_kernel : (r->real_f64 && !o.ex_spectral) ? 1 : 0;
-  // programmatic dependent launch of the Poisson kernels: on for grids of
-  // up to 2^18 nodes, whose steps are launch-latency bound (256 x 208: 17.4
-  // vs 18.0 us), off above (1024 x 840: 46.8 vs 44.2 us)
-  r->pdl = ((long long)Nx * Ny <= (1LL << 18)) ? 1 : 0;
+  // programmatic dependent launch of the Poisson kernels: all three for
+  // grids of up to 2^18 nodes, whose steps are launch-latency bound (256 x
+  // 208: 17.4 vs 18.0 us); above, the forward transform and the wavenumber
+  // solve only (2048 x 1680: 118.7 us against 119.6 without and 120.3 with
+  // the inverse transform too, whose early-resident CTAs crowd the solve)
+  r->pdl = ((long long)Nx * Ny <= (1LL << 18)) ? 7 : 3;
   r->cols_per_lane = 2;
   r->nstrips = march_strips(Nx, r->cols_per_lane);
   r->nxb = (r->step_kernel == 0) ? r->nstrips : step_flux_blocks(Nx);
@@ -942,7 +944,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       r->tile_threads = value;
       break;
     case EHD_TUNE_PDL:
-      if (value != 0 && value != 1) return fail(EHD_EINVAL, "programmatic dependent launch must be 0 or 1");
+      if (value < 0 || value > 7) return fail(EHD_EINVAL, "programmatic dependent launch: a mask of 1, 2 and 4");
       r->pdl = value;
       break;
     case EHD_TUNE_FFT_CTA:

@@ -685,14 +685,14 @@ bool fftw_supported(int Nx) { return Nx >= 64 && Nx <= 2048; }
 cudaError_t launch_rfft_warp(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
-    case 64: return launch_ex(a.pdl != 0, k_rfft_warp<1>, dim3(g), dim3(128), 0, s, a);
-    case 128: return launch_ex(a.pdl != 0, k_rfft_warp<2>, dim3(g), dim3(128), 0, s, a);
-    case 256: return launch_ex(a.pdl != 0, k_rfft_warp<4>, dim3(g), dim3(128), 0, s, a);
-    case 512: return launch_ex(a.pdl != 0, k_rfft_warp<8>, dim3(g), dim3(128), 0, s, a);
-    case 1024: return launch_ex(a.pdl != 0, k_rfft_warp<16>, dim3(g), dim3(128), 0, s, a);
+    case 64: return launch_ex((a.pdl & 1) != 0, k_rfft_warp<1>, dim3(g), dim3(128), 0, s, a);
+    case 128: return launch_ex((a.pdl & 1) != 0, k_rfft_warp<2>, dim3(g), dim3(128), 0, s, a);
+    case 256: return launch_ex((a.pdl & 1) != 0, k_rfft_warp<4>, dim3(g), dim3(128), 0, s, a);
+    case 512: return launch_ex((a.pdl & 1) != 0, k_rfft_warp<8>, dim3(g), dim3(128), 0, s, a);
+    case 1024: return launch_ex((a.pdl & 1) != 0, k_rfft_warp<16>, dim3(g), dim3(128), 0, s, a);
     case 2048:
-      if (a.fft_cta) return launch_ex(a.pdl != 0, k_rfft_cta, dim3(a.Ny), dim3(kCtaT), 0, s, a);
-      return launch_ex(a.pdl != 0, k_rfft_warp<32>, dim3(g), dim3(128), 0, s, a);
+      if (a.fft_cta) return launch_ex((a.pdl & 1) != 0, k_rfft_cta, dim3(a.Ny), dim3(kCtaT), 0, s, a);
+      return launch_ex((a.pdl & 1) != 0, k_rfft_warp<32>, dim3(g), dim3(128), 0, s, a);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -702,14 +702,14 @@ template <bool DX>
 cudaError_t irfft_warp_n(const PoissonArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)((a.Ny + 3) / 4);
   switch (a.Nx) {
-    case 64: return launch_ex(a.pdl != 0, k_irfft_warp<1, DX>, dim3(g), dim3(128), 0, s, a);
-    case 128: return launch_ex(a.pdl != 0, k_irfft_warp<2, DX>, dim3(g), dim3(128), 0, s, a);
-    case 256: return launch_ex(a.pdl != 0, k_irfft_warp<4, DX>, dim3(g), dim3(128), 0, s, a);
-    case 512: return launch_ex(a.pdl != 0, k_irfft_warp<8, DX>, dim3(g), dim3(128), 0, s, a);
-    case 1024: return launch_ex(a.pdl != 0, k_irfft_warp<16, DX>, dim3(g), dim3(128), 0, s, a);
+    case 64: return launch_ex((a.pdl & 4) != 0, k_irfft_warp<1, DX>, dim3(g), dim3(128), 0, s, a);
+    case 128: return launch_ex((a.pdl & 4) != 0, k_irfft_warp<2, DX>, dim3(g), dim3(128), 0, s, a);
+    case 256: return launch_ex((a.pdl & 4) != 0, k_irfft_warp<4, DX>, dim3(g), dim3(128), 0, s, a);
+    case 512: return launch_ex((a.pdl & 4) != 0, k_irfft_warp<8, DX>, dim3(g), dim3(128), 0, s, a);
+    case 1024: return launch_ex((a.pdl & 4) != 0, k_irfft_warp<16, DX>, dim3(g), dim3(128), 0, s, a);
     case 2048:
-      if (a.fft_cta) return launch_ex(a.pdl != 0, k_irfft_cta<DX>, dim3(a.Ny), dim3(kCtaT), 0, s, a);
-      return launch_ex(a.pdl != 0, k_irfft_warp<32, DX>, dim3(g), dim3(128), 0, s, a);
+      if (a.fft_cta) return launch_ex((a.pdl & 4) != 0, k_irfft_cta<DX>, dim3(a.Ny), dim3(kCtaT), 0, s, a);
+      return launch_ex((a.pdl & 4) != 0, k_irfft_warp<32, DX>, dim3(g), dim3(128), 0, s, a);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -212,7 +212,7 @@ size_t oddext_smem_bytes(int NE, bool real_f64) {
 cudaError_t launch_modes_oddext(const PoissonArgs& a, bool real_f64, cudaStream_t s) {
   if (a.Mh <= 1) return cudaSuccess;
   const dim3 grid(a.Mh - 1), block(kOddThreads);
-  const bool pdl = a.pdl != 0;
+  const bool pdl = (a.pdl & 2) != 0;
   bool small = true;  // every radix <= 7
   for (int k = 0; k < a.nfac; ++k) small = small && a.fac[k] <= 7;
   if (real_f64)

@@ -1186,7 +1186,7 @@ cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
   if (a.tile_modes > 0 && a.tile_modes < mb) mb = a.tile_modes;
   const size_t sm = (size_t)a.Ny * mb * (sizeof(Cplx<R>) + sizeof(R));
   const int nm = a.Mh;  // tiles start at m = 0
-  const bool pdl = a.pdl != 0;
+  const bool pdl = (a.pdl & 2) != 0;
   if constexpr (sizeof(R) == 4) {
     if (a.tile_threads == 512 || a.tile_threads == 1024) {
       const bool big = a.tile_threads == 1024;

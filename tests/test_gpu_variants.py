@@ -103,9 +103,10 @@ def test_launch_shape_knobs_keep_results():
         return F
 
     base = run_with()
-    pdl = run_with(pdl=1)
-    for k in base:
-        assert np.array_equal(base[k], pdl[k]), k
+    for mask in (1, 2, 4, 7):
+        pdl = run_with(pdl=mask)
+        for k in base:
+            assert np.array_equal(base[k], pdl[k]), (mask, k)
     p = o.setup(*w.args())
     for tune in (dict(fft_cta=0), dict(tile_modes=4), dict(tile_modes=1), dict(step_kernel=1)):
         e = _scaled_err(p, run_with(**tune), base)
