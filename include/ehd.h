@@ -211,7 +211,11 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * same results bit for bit), EHD_TUNE_TILE_THREADS (threads per CTA of the
  * mode solve, FP32 compute: 256, 512 or 1024; 0 = the default; more threads
  * cut each wavenumber's rows into shorter chunks, so results differ in
- * rounding order).
+ * rounding order), EHD_TUNE_TILE_CLUSTER (FP32 compute with 8 wavenumbers
+ * per tile: 1, each tile solved by a cluster of two CTAs that stage half the
+ * rows each and exchange their chunk maps through distributed shared memory;
+ * 0, the default, one CTA per tile, which is faster (2048 x 1680: 118.9-120.2
+ * against 121.5 us per step); the same results bit for bit).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -224,6 +228,7 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_Y_SOLVER 8
 #define EHD_TUNE_MARCH_TMA 9
 #define EHD_TUNE_TILE_THREADS 10
+#define EHD_TUNE_TILE_CLUSTER 11
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

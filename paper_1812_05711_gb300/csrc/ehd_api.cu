@@ -99,6 +99,7 @@ struct ehd_run {
   int cols_per_lane = 2;
   int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
   int tile_threads = 0;  // threads per CTA of the mode solve (0: 256)
+  int tile_cluster = 0;  // two-CTA clusters per wavenumber tile (FP32, 8 wavenumbers): off, slower
   int pdl = 0;         // programmatic dependent launch between the Poisson kernels (off: see ehd_tune)
   int fft_cta = 1;     // rows of 2048: CTA-per-row transforms
   int y_solver = 0;    // y solve of m >= 1: 0 tridiagonal, 1 odd-extension transform
@@ -300,6 +301,7 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.flux_acc = r->small;
   a.tile_modes = r->tile_modes;
   a.tile_threads = r->tile_threads;
+  a.tile_cluster = r->tile_cluster;
   a.pdl = r->pdl;
   a.fft_cta = r->fft_cta;
   a.y_solver = r->y_solver;
@@ -943,6 +945,10 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       if (value > 256 && r->real_f64) return fail(EHD_EINVAL, "FP64 mode solves take 256 threads");
       r->tile_threads = value;
       break;
+    case EHD_TUNE_TILE_CLUSTER:
+      if (value != 0 && value != 1) return fail(EHD_EINVAL, "tile cluster must be 0 or 1");
+      r->tile_cluster = value;
+      break;
     case EHD_TUNE_PDL:
       if (value < 0 || value > 7) return fail(EHD_EINVAL, "programmatic dependent launch: a mask of 1, 2 and 4");
       r->pdl = value;
@@ -1009,6 +1015,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_COLS_PER_LANE: return r->cols_per_lane;
     case EHD_TUNE_TILE_MODES: return r->tile_modes;
     case EHD_TUNE_TILE_THREADS: return r->tile_threads;
+    case EHD_TUNE_TILE_CLUSTER: return r->tile_cluster;
     case EHD_TUNE_PDL: return r->pdl;
     case EHD_TUNE_FFT_CTA: return r->fft_cta;
     case EHD_TUNE_Y_SOLVER: return r->y_solver;

@@ -150,6 +150,7 @@ struct PoissonArgs {
   double* flux_acc;          // [2] FP64 totals of injected / collected charge
   int tile_modes;            // wavenumbers per CTA of the mode solve (8, 4, 2, 1; 0 = largest that fits)
   int tile_threads;          // threads per CTA of the mode solve (FP32: 256, 512, 1024; 0 = 256)
+  int tile_cluster;          // FP32, 8 wavenumbers per tile: two-CTA clusters per tile (same bits)
   int pdl;                   // programmatic dependent launch, a mask: 1 forward transform, 2 wavenumber
                              // solve, 4 inverse transform
   int fft_cta;               // rows of 2048: one CTA of 64 threads per row (else one warp per row)

@@ -22,7 +22,11 @@
 //   k_irfft_rows  inverse of k_rfft_rows -> phi minus its row mean.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "ehd_dev.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ehd {
 
@@ -473,6 +477,117 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
 
 // threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
 constexpr int kTileThreads = 256;
+
+// The same solve by a cluster of two CTAs (on two SMs, or two slots of one):
+// CTA rank c stages and sweeps only the rows of chunks [16 c, 16 c + 16) --
+// half of the tile's shared memory and staging traffic per CTA, and twice
+// as many CTAs in flight.  The chunk maps of both halves are written into
+// both CTAs' scratch through distributed shared memory, so that each CTA
+// runs the single-CTA scan over all 32 chunk maps: chunk boundaries, the
+// per-chunk arithmetic and the scan order are those of modes_tile_body, and
+// the results are bit for bit the same (a batch, whose CTAs solve whole
+// tiles, gives a run the bits it gets alone).  Cluster barriers: after each
+// exchange of maps, and before the backward maps overwrite the peer's
+// forward ones.  Measured slower than one CTA per tile (2048 x 1680: 121.5
+// against 118.9-120.2 us per step; the three cluster barriers cost more than
+// the halved staging saves), so it is an option (EHD_TUNE_TILE_CLUSTER).
+template <int MB>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTileThreads) k_modes_tile2(PoissonArgs a) {
+  constexpr int NT = kTileThreads, CH = NT / MB, HALF = CH / 2;
+  static_assert(CH == 32, "one warp of chunk maps per wavenumber");
+  using R = float;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TileScratch<R, MB, NT> ts;
+  grid_dep_wait();
+  grid_dep_launch();
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  TileScratch<R, MB, NT>* peer = cl.map_shared_rank(&ts, rank ^ 1);
+  const int m0 = (blockIdx.x >> 1) * MB;
+  const int Ny = a.Ny, Mh = a.Mh, Mp = a.Mp;
+  const int C = (Ny + CH - 1) / CH;
+  const int R0 = min(HALF * rank * C, Ny), R1 = min(HALF * (rank + 1) * C, Ny);
+  const int rows = R1 - R0;
+  Cplx<R>* d = reinterpret_cast<Cplx<R>*>(smem_raw);                              // [rows][MB]
+  R* rt = reinterpret_cast<R*>(smem_raw + (size_t)HALF * C * MB * sizeof(Cplx<R>));  // [rows][MB]
+  Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec);
+  const R* __restrict__ rf = static_cast<const R*>(a.rfac);
+  {
+    constexpr int CB = 16, RB = 16;
+    constexpr int CPR = MB * (int)sizeof(Cplx<R>) / CB, RPR = MB * (int)sizeof(R) / RB;
+    constexpr int CE = CB / (int)sizeof(Cplx<R>), RE = RB / (int)sizeof(R);
+    for (int idx = threadIdx.x; idx < rows * CPR; idx += NT) {
+      const int j = idx / CPR, c = idx % CPR;
+      const int m = m0 + c * CE;
+      if (m < Mp) cp_async_chunk<CB>(d + j * MB + c * CE, spec + (long long)(R0 + j) * Mp + m);
+    }
+    for (int idx = threadIdx.x; idx < rows * RPR; idx += NT) {
+      const int j = idx / RPR, c = idx % RPR;
+      const int m = m0 + c * RE;
+      if (m < Mp) cp_async_chunk<RB>(rt + j * MB + c * RE, rf + (long long)(R0 + j) * Mp + m);
+    }
+    cp_async_all();
+  }
+  __syncthreads();
+  const int mo = threadIdx.x % MB, ch = threadIdx.x / MB;
+  const bool own = (ch / HALF) == rank;
+  const int j0 = min(ch * C, Ny), j1 = min(j0 + C, Ny);
+  if (own) {
+    R al = R(1);
+    Cplx<R> br = {R(0), R(0)};
+    for (int j = j0; j < j1; ++j) {
+      const R r = rt[(j - R0) * MB + mo];
+      const Cplx<R> dj = d[(j - R0) * MB + mo];
+      al = -r * al;
+      br = {r * (dj.re - br.re), r * (dj.im - br.im)};
+    }
+    ts.al[ch][mo] = al;
+    ts.br[ch][mo] = br;
+    peer->al[ch][mo] = al;
+    peer->br[ch][mo] = br;
+  }
+  cl.sync();
+  chunk_carries<R, MB, NT, false>(ts);
+  __syncthreads();
+  R ab = R(1);
+  Cplx<R> bb = {R(0), R(0)};
+  if (own) {
+    Cplx<R> x = ts.carry[ch][mo];
+    for (int j = j0; j < j1; ++j) {
+      const R r = rt[(j - R0) * MB + mo];
+      const Cplx<R> dj = d[(j - R0) * MB + mo];
+      x = {r * (dj.re - x.re), r * (dj.im - x.im)};
+      d[(j - R0) * MB + mo] = x;
+      bb = {bb.re + ab * x.re, bb.im + ab * x.im};
+      ab = -ab * r;
+    }
+  }
+  cl.sync();  // both CTAs have scanned the forward maps
+  if (own) {
+    ts.al[ch][mo] = ab;
+    ts.br[ch][mo] = bb;
+    peer->al[ch][mo] = ab;
+    peer->br[ch][mo] = bb;
+  }
+  cl.sync();
+  chunk_carries<R, MB, NT, true>(ts);
+  __syncthreads();
+  if (own) {
+    Cplx<R> x = ts.carry[ch][mo];
+    for (int j = j1 - 1; j >= j0; --j) {
+      const R r = rt[(j - R0) * MB + mo];
+      const Cplx<R> dj = d[(j - R0) * MB + mo];
+      x = {dj.re - r * x.re, dj.im - r * x.im};
+      d[(j - R0) * MB + mo] = x;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < rows * MB; idx += NT) {
+    const int j = idx / MB, mo2 = idx % MB;
+    const int m = m0 + mo2;
+    if (m >= 1 && m < Mh) spec[(long long)(R0 + j) * Mp + m] = d[idx];
+  }
+}
 
 template <class R, int MB, int NT = kTileThreads>
 __global__ void __launch_bounds__(NT) k_modes_tile(PoissonArgs a) {
@@ -1188,6 +1303,11 @@ cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
   const int nm = a.Mh;  // tiles start at m = 0
   const bool pdl = (a.pdl & 2) != 0;
   if constexpr (sizeof(R) == 4) {
+    if (a.tile_cluster && mb == 8 && a.tile_threads <= 256 && a.Ny >= 64) {
+      const int C = (a.Ny + 31) / 32;
+      const size_t sm2 = (size_t)16 * C * 8 * (sizeof(Cplx<R>) + sizeof(R));
+      return launch_ex(pdl, k_modes_tile2<8>, dim3(2 * ((nm + 7) / 8)), dim3(kTileThreads), sm2, s, a);
+    }
     if (a.tile_threads == 512 || a.tile_threads == 1024) {
       const bool big = a.tile_threads == 1024;
       switch (mb) {
@@ -1303,6 +1423,7 @@ cudaError_t set_attrs_t() {
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreads>)) != cudaSuccess) return e;
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreadsSmall>)) != cudaSuccess) return e;
   if constexpr (sizeof(R) == 4) {
+    if ((e = allow_max_dynamic_smem(k_modes_tile2<8>)) != cudaSuccess) return e;
     if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8, 512>)) != cudaSuccess) return e;
     if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4, 512>)) != cudaSuccess) return e;
     if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2, 512>)) != cudaSuccess) return e;

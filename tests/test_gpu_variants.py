@@ -114,6 +114,26 @@ def test_launch_shape_knobs_keep_results():
 
 
 @gpu
+@pytest.mark.parametrize("nx,ny", [(256, 100), (2048, 211)])
+def test_cluster_wavenumber_solve_same_bits(nx, ny):
+    """The two-CTA cluster form of the wavenumber solve (each CTA stages and
+    sweeps half of a tile's rows; the chunk maps are exchanged through
+    distributed shared memory and both CTAs run the whole scan) gives the
+    one-CTA form's results bit for bit, ragged row counts included."""
+    ehd = _ehd()
+    amp, ph = wl.roll(77, 1e-3)
+    out = []
+    for c in (0, 1):
+        r = ehd.Run(nx, ny, 190.0, 10, 10, 4000, 0.25, storage="f32", amp=amp, phase=ph)
+        ehd.ehd_tune(r.handle, "tile_cluster", c)
+        r.step(30)
+        out.append(r.fields())
+        r.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@gpu
 @pytest.mark.parametrize("storage,bound", [("f64", 1e-12), ("f32", 2e-5), ("bf16", 5e-2)])
 def test_spectral_ex_parity(storage, bound):
     """E_x = -d phi/dx from the x-spectrum of phi (-i k_m phi_m, Nyquist
