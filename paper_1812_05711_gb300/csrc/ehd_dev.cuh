@@ -75,8 +75,9 @@ template <class R> struct Cplx { R re, im; };
 // ----------------------------------------------------------- kernel args ---
 // Programmatic dependent launch.  A kernel launched with pdl = true may
 // start while the previous kernel of its stream is still running; it must
-// call grid_dep_wait() before touching anything that kernel writes or reads,
-// and calls grid_dep_launch() after that wait, so that when a kernel starts,
+// call grid_dep_wait() before touching anything that kernel writes or reads
+// (only tables that no kernel of the step writes may be read before it), and
+// calls grid_dep_launch() after that wait, so that when a kernel starts,
 // every kernel two or more launches back has completed.  Both instructions
 // are no-ops in a kernel launched without the attribute.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }

@@ -439,19 +439,21 @@ __device__ __forceinline__ void cta_fft1024(float (&re)[16], float (&im)[16], fl
 // Forward transform of row y (N = 2048) by one CTA of 64 threads.
 __global__ void __launch_bounds__(kCtaT) k_rfft_cta(PoissonArgs a) {
   __shared__ float2 sm[kSmemCta];
-  grid_dep_wait();
-  grid_dep_launch();
   const int t = threadIdx.x, y = blockIdx.x;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
+  // the twiddle tables are constant: loaded before the wait for the step
+  // kernel that writes the charge density (programmatic dependent launch)
+  float2 w1[16], wu[8];
+  cta_twiddles(tw, w1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) wu[j] = __ldg(tw + t + 64 * j);  // the untangle's W_N^k, k = t + 64 j
+  grid_dep_wait();
+  grid_dep_launch();
   const float* row = static_cast<const float*>(a.rhoc) + (long long)y * a.P;
   const float2* rc2 = reinterpret_cast<const float2*>(row);
   const float *rdn, *rup;
   rhoc_partials<float>(a, y, rdn, rup);
   const float nieps = -(float)a.inv_eps;
-  float2 w1[16], wu[8];
-  cta_twiddles(tw, w1);
-#pragma unroll
-  for (int j = 0; j < 8; ++j) wu[j] = __ldg(tw + t + 64 * j);  // the untangle's W_N^k, k = t + 64 j
   // A row constant c0 is taken out before the transform: the differences are
   // exact (Sterbenz) and small, so the transform's rounding scales with the
   // row's variation, and only the m = 0 bin depends on c0.

@@ -392,7 +392,10 @@ __device__ __forceinline__ void chunk_carries(TileScratch<R, MB, NT>& ts) {
 // One CTA solves wavenumbers m0 .. m0 + MB - 1 of run a (smem_raw: tile
 // storage, ts: chunk-map scratch).  The m = 0 column of tile 0 holds zeros
 // and is never stored.
-template <class R, int MB, int NT>
+// PDL: the kernel was launched with programmatic dependent launch; the
+// constant pivots are staged before the wait for the forward transform, the
+// spectrum after it.
+template <class R, int MB, int NT, bool PDL = false>
 __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, unsigned char* smem_raw,
                                                 TileScratch<R, MB, NT>& ts) {
   constexpr int CH = NT / MB;
@@ -412,15 +415,19 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
     constexpr int RPR = MB * (int)sizeof(R) / RB;        // chunks per row, pivots
     constexpr int CE = CB / (int)sizeof(Cplx<R>) > 0 ? CB / (int)sizeof(Cplx<R>) : 1;
     constexpr int RE = RB / (int)sizeof(R);
-    for (int idx = threadIdx.x; idx < Ny * CPR; idx += NT) {
-      const int j = idx / CPR, c = idx % CPR;
-      const int m = m0 + c * CE;
-      if (m < Mp) cp_async_chunk<CB>(d + j * MB + c * CE, spec + (long long)j * Mp + m);
-    }
     for (int idx = threadIdx.x; idx < Ny * RPR; idx += NT) {
       const int j = idx / RPR, c = idx % RPR;
       const int m = m0 + c * RE;
       if (m < Mp) cp_async_chunk<RB>(rt + j * MB + c * RE, rf + (long long)j * Mp + m);
+    }
+    if constexpr (PDL) {
+      grid_dep_wait();
+      grid_dep_launch();
+    }
+    for (int idx = threadIdx.x; idx < Ny * CPR; idx += NT) {
+      const int j = idx / CPR, c = idx % CPR;
+      const int m = m0 + c * CE;
+      if (m < Mp) cp_async_chunk<CB>(d + j * MB + c * CE, spec + (long long)j * Mp + m);
     }
     cp_async_all();
   }
@@ -593,9 +600,7 @@ template <class R, int MB, int NT = kTileThreads>
 __global__ void __launch_bounds__(NT) k_modes_tile(PoissonArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileScratch<R, MB, NT> ts;
-  grid_dep_wait();
-  grid_dep_launch();
-  modes_tile_body<R, MB, NT>(a, blockIdx.x * MB, smem_raw, ts);
+  modes_tile_body<R, MB, NT, true>(a, blockIdx.x * MB, smem_raw, ts);
 }
 
 // Float-float ("double-single") numbers for the FP32 path: value = hi + lo
