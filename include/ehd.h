@@ -189,10 +189,13 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * scans' chunking, so results then differ from batch members' in rounding), EHD_TUNE_PDL (a mask
  * of the Poisson kernels launched with programmatic dependent launch, so that
  * each is resident and waiting when its predecessor ends: 1 the forward row
- * transform, 2 the wavenumber solve, 4 the inverse transform; 7, the default
- * up to 2^18 nodes, shortens steps of small grids; 3, the default above: the
- * inverse transform's early-resident CTAs would crowd the wavenumber solve
- * of large runs), EHD_TUNE_FFT_CTA (FP32 rows
+ * transform, 2 the wavenumber solve, 4 the inverse transform, 8 the step
+ * kernel (march form: it stages its first rows' populations before waiting
+ * for phi); 7, the default up to 2^18 nodes, shortens steps of small grids;
+ * 3, the default above (2048 x 1680: 118.0 us against 121.9 with none, 118.2
+ * with 11, 119.8 with 15: the inverse transform's early-resident CTAs crowd
+ * the wavenumber solve of large runs); results are the same for every mask),
+ * EHD_TUNE_FFT_CTA (FP32 rows
  * of 2048: 1, the default, one CTA of 64 threads per row; 0, one warp per
  * row), EHD_TUNE_Y_SOLVER (the y solve of the wavenumbers m >= 1: 0, the
  * default, one tridiagonal per wavenumber (Eq. 18); 1, the literal form of

@@ -710,8 +710,9 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
   // programmatic dependent launch of the Poisson kernels: all three for
   // grids of up to 2^18 nodes, whose steps are launch-latency bound (256 x
   // 208: 17.4 vs 18.0 us); above, the forward transform and the wavenumber
-  // solve only (2048 x 1680: 118.7 us against 119.6 without and 120.3 with
-  // the inverse transform too, whose early-resident CTAs crowd the solve)
+  // solve only (2048 x 1680: 118.0 us against 121.9 without, 119.8 with the
+  // inverse transform and the step kernel too: the inverse transform's
+  // early-resident CTAs crowd the solve)
   r->pdl = ((long long)Nx * Ny <= (1LL << 18)) ? 7 : 3;
   r->cols_per_lane = 2;
   r->nstrips = march_strips(Nx, r->cols_per_lane);
@@ -950,7 +951,7 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       r->tile_cluster = value;
       break;
     case EHD_TUNE_PDL:
-      if (value < 0 || value > 7) return fail(EHD_EINVAL, "programmatic dependent launch: a mask of 1, 2 and 4");
+      if (value < 0 || value > 15) return fail(EHD_EINVAL, "programmatic dependent launch: a mask of 1, 2, 4 and 8");
       r->pdl = value;
       break;
     case EHD_TUNE_FFT_CTA:

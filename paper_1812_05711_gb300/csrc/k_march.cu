@@ -595,29 +595,22 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
   // carried rows, [k][j]: H (c_y = 0) of row r-1, U (c_y = +1) of rows r-1, r
   R Hm[6][2] = {}, Um[6][2] = {}, Uc[6][2] = {};
   R pm[2], pc[2];
-  {
-    const long long c = (long long)rs * P + xc;
-    pc[0] = dphi[c];
-    pc[1] = dphi[c + 1];
-    if (rs > 0) {
-      pm[0] = dphi[c - P];
-      pm[1] = dphi[c - P + 1];
-    } else {
-      pm[0] = gwall * pc[0];
-      pm[1] = gwall * pc[1];
-    }
-  }
   double qin = 0.0, qout = 0.0;
   bool bad = false;
   unsigned char* ring = warp_ring + (size_t)lane * SB;
   auto slot = [&](int stage, int s) { return ring + ((size_t)stage * SL + s) * 32 * SB; };
-  auto issue = [&](int row_y, int stage) {
+  // a row's populations (written by the previous step's march) ...
+  auto issue_pop = [&](int row_y, int stage) {
     const long long c = (long long)row_y * P + xc;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       cp_async_elem<2 * sizeof(S)>(slot(stage, i), fin + i * pl + c);
       cp_async_elem<2 * sizeof(S)>(slot(stage, 9 + i), gin + i * pl + c);
     }
+  };
+  // ... and its fields (written by the Poisson solve that just ended)
+  auto issue_fields = [&](int row_y, int stage) {
+    const long long c = (long long)row_y * P + xc;
     if (row_y + 1 < Ny) cp_async_elem<2 * sizeof(R)>(slot(stage, 18), dphi + c + P);
     if constexpr (SPECX) cp_async_elem<2 * sizeof(R)>(slot(stage, 20), static_cast<const R*>(a.ex) + c);
     if (lane == 1) {
@@ -633,9 +626,33 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
       cp_async_elem<4>(slot(stage, 19), rch + row_y - 1);
     }
   };
+  auto issue = [&](int row_y, int stage) {
+    issue_pop(row_y, stage);
+    issue_fields(row_y, stage);
+  };
+  // prologue: the first rows' populations, then (under programmatic
+  // dependent launch) the wait for the inverse transform that wrote phi,
+  // then the fields; with more than two stages the first group then holds
+  // all prologue rows, which only makes the first wait longer
+#pragma unroll
+  for (int k = 0; k < NST - 1; ++k)
+    if (rs + k <= re) issue_pop(rs + k, k);
+  grid_dep_wait();
+  {
+    const long long c = (long long)rs * P + xc;
+    pc[0] = dphi[c];
+    pc[1] = dphi[c + 1];
+    if (rs > 0) {
+      pm[0] = dphi[c - P];
+      pm[1] = dphi[c - P + 1];
+    } else {
+      pm[0] = gwall * pc[0];
+      pm[1] = gwall * pc[1];
+    }
+  }
 #pragma unroll
   for (int k = 0; k < NST - 1; ++k) {
-    if (rs + k <= re) issue(rs + k, k);
+    if (rs + k <= re) issue_fields(rs + k, k);
     cp_async_commit();
   }
   for (int r = rs; r <= re; ++r) {
@@ -942,6 +959,10 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
 template <class S, class R, int NSTAGE, bool SPECX = false, bool PERT = false>
 __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
   extern __shared__ __align__(16) unsigned char march_smem[];
+  // the forward transform (launched with programmatic dependent launch) may
+  // become resident as this one-wave grid's CTAs finish; it waits for the
+  // whole grid before it reads the charge density
+  grid_dep_launch();
   const int gw = blockIdx.x * 4 + (threadIdx.x >> 5);
   march2_body<S, R, NSTAGE, SPECX, PERT>(
       a, gw % a.nstrips, gw / a.nstrips,
@@ -1598,14 +1619,11 @@ cudaError_t march2_n(const StepArgs& a, cudaStream_t s) {
   const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
   const unsigned grid = (unsigned)((warps + 3) / 4);
   const size_t smem = 4 * March2Stages<S, R, NST, SPECX>::kBytesPerWarp;
+  const bool pdl = (a.pdl & 8) != 0;  // the step kernel waits for phi after staging its first rows
   if constexpr (sizeof(R) == 4 && !SPECX) {
-    if (a.base_tab) {
-      k_march2<S, R, NST, false, true><<<grid, 128, smem, s>>>(a);
-      return cudaGetLastError();
-    }
+    if (a.base_tab) return launch_ex(pdl, k_march2<S, R, NST, false, true>, dim3(grid), dim3(128), smem, s, a);
   }
-  k_march2<S, R, NST, SPECX><<<grid, 128, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_ex(pdl, k_march2<S, R, NST, SPECX>, dim3(grid), dim3(128), smem, s, a);
 }
 
 template <class S, class R>

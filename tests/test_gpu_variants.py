@@ -103,7 +103,7 @@ def test_launch_shape_knobs_keep_results():
         return F
 
     base = run_with()
-    for mask in (1, 2, 4, 7):
+    for mask in (1, 2, 4, 7, 8, 15):
         pdl = run_with(pdl=mask)
         for k in base:
             assert np.array_equal(base[k], pdl[k]), (mask, k)
