@@ -42,10 +42,13 @@ struct FftStage {
         const int u = b * LEN + k, v = u + LEN / 2;
         const float tr = re[v] * w.x - im[v] * w.y;
         const float ti = re[v] * w.y + im[v] * w.x;
-        re[v] = re[u] - tr;
-        im[v] = im[u] - ti;
-        re[u] += tr;
-        im[u] += ti;
+        // the pair's sum and difference as packed two-float adds
+        const float2 a = make_float2(re[u], im[u]);
+        const float2 lo = __fadd2_rn(a, make_float2(-tr, -ti)), hi = __fadd2_rn(a, make_float2(tr, ti));
+        re[v] = lo.x;
+        im[v] = lo.y;
+        re[u] = hi.x;
+        im[u] = hi.y;
       }
     }
     FftStage<M, LEN * 2>::run(re, im);
@@ -290,18 +293,27 @@ __device__ __forceinline__ void irfft_warp_rows(const PoissonArgs& a, int y0, fl
 // In-register 16-point forward DFT, natural order in and out, as 4 x 4:
 // X[k2 + 4 k1] = sum_n1 W_16^(n1 k2) W_4^(n1 k1) sum_n2 v[n1 + 4 n2] W_4^(n2 k2).
 // The twiddles are literal constants, so trivial products fold away.
+// The sums and differences on (re, im) pairs use the packed two-float adds of
+// this architecture (each pair rounded exactly as two scalar adds, so the
+// results are unchanged): 2048 x 1680 steps 116.8 against 117.9 us, with the
+// CTA transforms bounded to 80 registers so that their grid stays one wave.
 __device__ __forceinline__ void dft4(float& r0, float& i0, float& r1, float& i1, float& r2, float& i2, float& r3,
                                      float& i3) {
-  const float sr = r0 + r2, si = i0 + i2, dr = r0 - r2, di = i0 - i2;
-  const float tr = r1 + r3, ti = i1 + i3, ur = r1 - r3, ui = i1 - i3;
-  r0 = sr + tr;
-  i0 = si + ti;
-  r2 = sr - tr;
-  i2 = si - ti;
-  r1 = dr + ui;  // (d) - i (u)
-  i1 = di - ur;
-  r3 = dr - ui;  // (d) + i (u)
-  i3 = di + ur;
+  const float2 a0 = make_float2(r0, i0), a1 = make_float2(r1, i1), a2 = make_float2(r2, i2),
+               a3 = make_float2(r3, i3);
+  const float2 s = __fadd2_rn(a0, a2), d = __fadd2_rn(a0, make_float2(-a2.x, -a2.y));
+  const float2 t = __fadd2_rn(a1, a3), u = __fadd2_rn(a1, make_float2(-a3.x, -a3.y));
+  const float2 b0 = __fadd2_rn(s, t), b2 = __fadd2_rn(s, make_float2(-t.x, -t.y));
+  const float2 b1 = __fadd2_rn(d, make_float2(u.y, -u.x));  // (d) - i (u)
+  const float2 b3 = __fadd2_rn(d, make_float2(-u.y, u.x));  // (d) + i (u)
+  r0 = b0.x;
+  i0 = b0.y;
+  r1 = b1.x;
+  i1 = b1.y;
+  r2 = b2.x;
+  i2 = b2.y;
+  r3 = b3.x;
+  i3 = b3.y;
 }
 
 template <int M>  // multiply by W_16^M = exp(-2 pi i M / 16), M in {0..9}
@@ -420,24 +432,24 @@ __device__ __forceinline__ void cta_fft1024(float (&re)[16], float (&im)[16], fl
     float2 v[4];
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) v[qq] = sm[k1 * kPitchA + 4 * (4 * q + i) + (qq ^ q)];
-    // 4-point DFT over qq, W_4 = -i
-    const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-    const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-    const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-    const float2 d13 = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
-    zr[i] = s02.x + s13.x;
-    zi[i] = s02.y + s13.y;
-    zr[4 + i] = d02.x + d13.y;  // d02 - i d13
-    zi[4 + i] = d02.y - d13.x;
-    zr[8 + i] = s02.x - s13.x;
-    zi[8 + i] = s02.y - s13.y;
-    zr[12 + i] = d02.x - d13.y;  // d02 + i d13
-    zi[12 + i] = d02.y + d13.x;
+    // 4-point DFT over qq, W_4 = -i (packed two-float adds)
+    float zr0, zi0, zr1, zi1, zr2, zi2, zr3, zi3;
+    zr0 = v[0].x, zi0 = v[0].y, zr1 = v[1].x, zi1 = v[1].y;
+    zr2 = v[2].x, zi2 = v[2].y, zr3 = v[3].x, zi3 = v[3].y;
+    dft4(zr0, zi0, zr1, zi1, zr2, zi2, zr3, zi3);
+    zr[i] = zr0;
+    zi[i] = zi0;
+    zr[4 + i] = zr1;  // d02 - i d13
+    zi[4 + i] = zi1;
+    zr[8 + i] = zr2;
+    zi[8 + i] = zi2;
+    zr[12 + i] = zr3;  // d02 + i d13
+    zi[12 + i] = zi3;
   }
 }
 
 // Forward transform of row y (N = 2048) by one CTA of 64 threads.
-__global__ void __launch_bounds__(kCtaT) k_rfft_cta(PoissonArgs a) {
+__global__ void __launch_bounds__(kCtaT, 12) k_rfft_cta(PoissonArgs a) {
   __shared__ float2 sm[kSmemCta];
   const int t = threadIdx.x, y = blockIdx.x;
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
@@ -534,7 +546,7 @@ __global__ void __launch_bounds__(kCtaT) k_rfft_cta(PoissonArgs a) {
 
 // Inverse transform of row y (N = 2048) -> phi minus its row mean (DX: E_x).
 template <bool DX = false>
-__global__ void __launch_bounds__(kCtaT) k_irfft_cta(PoissonArgs a) {
+__global__ void __launch_bounds__(kCtaT, 12) k_irfft_cta(PoissonArgs a) {
   __shared__ float2 sm[kSmemCta];
   grid_dep_wait();
   grid_dep_launch();
