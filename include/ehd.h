@@ -218,7 +218,12 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * per tile: 1, each tile solved by a cluster of two CTAs that stage half the
  * rows each and exchange their chunk maps through distributed shared memory;
  * 0, the default, one CTA per tile, which is faster (2048 x 1680: 118.9-120.2
- * against 121.5 us per step); the same results bit for bit).
+ * against 121.5 us per step); the same results bit for bit), EHD_TUNE_TILE_TMA
+ * (FP32 compute with 8 wavenumbers per tile: 1, each tile's spectrum and
+ * pivots staged by tensor copies of 256-row boxes with mbarrier completion;
+ * 0, the default, by 16-byte cp.async chunks from all threads, which is
+ * faster for these 64- and 32-byte rows (2048 x 1680: 117.2-117.9 against
+ * 118.4 us per step); the same results bit for bit).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -232,6 +237,7 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_MARCH_TMA 9
 #define EHD_TUNE_TILE_THREADS 10
 #define EHD_TUNE_TILE_CLUSTER 11
+#define EHD_TUNE_TILE_TMA 12
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

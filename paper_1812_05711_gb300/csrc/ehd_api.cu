@@ -100,6 +100,9 @@ struct ehd_run {
   int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
   int tile_threads = 0;  // threads per CTA of the mode solve (0: 256)
   int tile_cluster = 0;  // two-CTA clusters per wavenumber tile (FP32, 8 wavenumbers): off, slower
+  int tile_tma = 0;      // wavenumber tiles staged by tensor copies (FP32, when the maps encode): off, slower
+  ModesTma mtma = {};
+  bool mtma_ok = false;
   int pdl = 0;         // programmatic dependent launch between the Poisson kernels (off: see ehd_tune)
   int fft_cta = 1;     // rows of 2048: CTA-per-row transforms
   int y_solver = 0;    // y solve of m >= 1: 0 tridiagonal, 1 odd-extension transform
@@ -302,6 +305,9 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.tile_modes = r->tile_modes;
   a.tile_threads = r->tile_threads;
   a.tile_cluster = r->tile_cluster;
+  a.tile_tma = r->tile_tma;
+  a.mtma = r->mtma_ok ? &r->mtma : nullptr;
+  a.err = r->err;
   a.pdl = r->pdl;
   a.fft_cta = r->fft_cta;
   a.y_solver = r->y_solver;
@@ -732,6 +738,8 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     return fail(EHD_ENOMEM, "device allocation failed");
   }
   r->err = reinterpret_cast<int*>(r->small + 16);
+  // tensor maps for staging the wavenumber tiles (FP32 compute)
+  if (!r->real_f64) r->mtma_ok = modes_tma_encode(&r->mtma, r->spec, r->rfac, Ny, r->Mp) == cudaSuccess;
   // tensor maps of the TMA march (FP32 storage and compute): one set per
   // buffer parity; the default form when they encode
   if (r->storage == EHD_STORE_F32 && !r->real_f64 && march_tma_supported(Nx)) {
@@ -950,6 +958,10 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       if (value != 0 && value != 1) return fail(EHD_EINVAL, "tile cluster must be 0 or 1");
       r->tile_cluster = value;
       break;
+    case EHD_TUNE_TILE_TMA:
+      if (value != 0 && value != 1) return fail(EHD_EINVAL, "tile tensor copies must be 0 or 1");
+      r->tile_tma = value;
+      break;
     case EHD_TUNE_PDL:
       if (value < 0 || value > 15) return fail(EHD_EINVAL, "programmatic dependent launch: a mask of 1, 2, 4 and 8");
       r->pdl = value;
@@ -1017,6 +1029,7 @@ int ehd_tune_get(ehd_run* r, int param) {
     case EHD_TUNE_TILE_MODES: return r->tile_modes;
     case EHD_TUNE_TILE_THREADS: return r->tile_threads;
     case EHD_TUNE_TILE_CLUSTER: return r->tile_cluster;
+    case EHD_TUNE_TILE_TMA: return r->tile_tma;
     case EHD_TUNE_PDL: return r->pdl;
     case EHD_TUNE_FFT_CTA: return r->fft_cta;
     case EHD_TUNE_Y_SOLVER: return r->y_solver;

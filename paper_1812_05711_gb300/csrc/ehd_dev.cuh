@@ -99,6 +99,18 @@ cudaError_t launch_ex(bool pdl, void (*kernel)(P...), dim3 grid, dim3 block, siz
   return cudaLaunchKernelEx(&c, kernel, static_cast<A&&>(args)...);
 }
 
+// Tensor maps of a run's spectrum [Ny][Mp] complex and pivots [Ny][Mp] (FP32)
+// for staging a tile of 8 wavenumbers: boxes of 256 rows and one box of the
+// last Ny % 256 rows.
+struct ModesTma {
+  CUtensorMap spec_full, spec_tail, rf_full, rf_tail;
+  int nfull, tail;
+};
+// a 2-D FP32 tensor map: inner x outer elements, rows row_bytes apart
+cudaError_t tma_encode_2d(CUtensorMap* m, const void* base, unsigned long long inner, unsigned long long outer,
+                          unsigned long long row_bytes, unsigned box_inner, unsigned box_outer);
+cudaError_t modes_tma_encode(ModesTma* t, const void* spec, const void* rfac, int Ny, int Mp);
+
 struct StepArgs {
   int Nx, Ny, P;
   long long plane;           // elements per population plane (Ny * P)
@@ -152,6 +164,9 @@ struct PoissonArgs {
   int tile_modes;            // wavenumbers per CTA of the mode solve (8, 4, 2, 1; 0 = largest that fits)
   int tile_threads;          // threads per CTA of the mode solve (FP32: 256, 512, 1024; 0 = 256)
   int tile_cluster;          // FP32, 8 wavenumbers per tile: two-CTA clusters per tile (same bits)
+  int tile_tma;              // FP32, 8 wavenumbers per tile: tiles staged by tensor copies (same bits)
+  const struct ModesTma* mtma;  // host pointer to the run's tensor maps of spec and rfac (or nullptr)
+  int* err;                  // device error word (bit 2: a bounded wait gave up)
   int pdl;                   // programmatic dependent launch, a mask: 1 forward transform, 2 wavenumber
                              // solve, 4 inverse transform
   int fft_cta;               // rows of 2048: one CTA of 64 threads per row (else one warp per row)

@@ -392,17 +392,17 @@ __device__ __forceinline__ void chunk_carries(TileScratch<R, MB, NT>& ts) {
 // One CTA solves wavenumbers m0 .. m0 + MB - 1 of run a (smem_raw: tile
 // storage, ts: chunk-map scratch).  The m = 0 column of tile 0 holds zeros
 // and is never stored.
+template <class R, int MB, int NT>
+__device__ __forceinline__ void modes_tile_sweeps(const PoissonArgs& a, int m0, Cplx<R>* d, const R* rt,
+                                                  TileScratch<R, MB, NT>& ts);
+
 // PDL: the kernel was launched with programmatic dependent launch; the
 // constant pivots are staged before the wait for the forward transform, the
 // spectrum after it.
 template <class R, int MB, int NT, bool PDL = false>
 __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, unsigned char* smem_raw,
                                                 TileScratch<R, MB, NT>& ts) {
-  constexpr int CH = NT / MB;
-  auto& s_al = ts.al;
-  auto& s_br = ts.br;
-  auto& s_carry = ts.carry;
-  const int Ny = a.Ny, Mh = a.Mh, Mp = a.Mp;
+  const int Ny = a.Ny, Mp = a.Mp;
   Cplx<R>* d = reinterpret_cast<Cplx<R>*>(smem_raw);                          // [Ny][MB]
   R* rt = reinterpret_cast<R*>(smem_raw + (size_t)Ny * MB * sizeof(Cplx<R>));  // [Ny][MB]
   Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec);
@@ -432,6 +432,20 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
     cp_async_all();
   }
   __syncthreads();
+  modes_tile_sweeps<R, MB, NT>(a, m0, d, rt, ts);
+}
+
+// The three sweeps of a staged tile (d: spectrum [Ny][MB], rt: reciprocal
+// pivots [Ny][MB]) and the store of its wavenumbers 1 <= m < Mh.
+template <class R, int MB, int NT>
+__device__ __forceinline__ void modes_tile_sweeps(const PoissonArgs& a, int m0, Cplx<R>* d, const R* rt,
+                                                  TileScratch<R, MB, NT>& ts) {
+  constexpr int CH = NT / MB;
+  auto& s_al = ts.al;
+  auto& s_br = ts.br;
+  auto& s_carry = ts.carry;
+  const int Ny = a.Ny, Mh = a.Mh, Mp = a.Mp;
+  Cplx<R>* spec = static_cast<Cplx<R>*>(a.spec);
   const int mo = threadIdx.x % MB, ch = threadIdx.x / MB;
   const int C = (Ny + CH - 1) / CH;
   const int j0 = min(ch * C, Ny), j1 = min(j0 + C, Ny);
@@ -484,6 +498,115 @@ __device__ __forceinline__ void modes_tile_body(const PoissonArgs& a, int m0, un
 
 // threads per CTA of the wavenumber solves: NT / MB chunks per wavenumber
 constexpr int kTileThreads = 256;
+
+// The same solve with the tile staged by tensor copies (FP32, 8 wavenumbers):
+// one thread issues a box of 256 rows x 8 pivots and of 256 rows x 8
+// complex values per copy (the last box holds the remaining rows) into the
+// layout the sweeps read, completing on two mbarriers, instead of the CTA
+// issuing 16-byte chunks with their address arithmetic.  The pivots (constant
+// per run) are requested before the wait for the forward transform.  Waits
+// are bounded: one that gives up sets bit 2 of the run's error word, waits
+// (bounded again) for the copies in flight and leaves the tile unsolved.
+// Measured slower than the CTA's own 16-byte chunks (2048 x 1680: 118.4
+// against 117.2-117.9 us per step: a box of 256 rows of 64 or 32 bytes is
+// fetched row by row by the SM's one copy engine), so it is an option
+// (EHD_TUNE_TILE_TMA).
+namespace mt {
+constexpr unsigned kWaitLimit = 1u << 22;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void load2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+}  // namespace mt
+
+// shared memory of the tensor-copy tile: spectrum [Ny][8] complex, pivots [Ny][8]
+__host__ __device__ constexpr size_t modes_tma_pivot_offset(int Ny) { return ((size_t)Ny * 64 + 127) / 128 * 128; }
+
+__global__ void __launch_bounds__(kTileThreads) k_modes_tile_tma(PoissonArgs a, const __grid_constant__ ModesTma tm) {
+  constexpr int MB = 8, NT = kTileThreads;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ TileScratch<float, MB, NT> ts;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  const int Ny = a.Ny, m0 = blockIdx.x * MB;
+  // tensor-copy destinations 128-byte aligned (the launch adds 128 bytes)
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  Cplx<float>* d = reinterpret_cast<Cplx<float>*>(base);
+  float* rt = reinterpret_cast<float*>(base + modes_tma_pivot_offset(Ny));
+  const unsigned mb_rf = mt::smem_u32(&mbar[0]), mb_sp = mt::smem_u32(&mbar[1]);
+  if (threadIdx.x == 0) {
+    mt::mbar_init(mb_rf);
+    mt::mbar_init(mb_sp);
+    mt::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mt::mbar_expect_tx(mb_rf, (unsigned)Ny * 32u);
+    for (int k = 0; k < tm.nfull; ++k)
+      mt::load2d(mt::smem_u32(rt + (size_t)k * 256 * MB), &tm.rf_full, m0, 256 * k, mb_rf);
+    if (tm.tail) mt::load2d(mt::smem_u32(rt + (size_t)tm.nfull * 256 * MB), &tm.rf_tail, m0, 256 * tm.nfull, mb_rf);
+  }
+  grid_dep_wait();  // the forward transform has written the spectrum
+  grid_dep_launch();
+  if (threadIdx.x == 0) {
+    mt::mbar_expect_tx(mb_sp, (unsigned)Ny * 64u);
+    for (int k = 0; k < tm.nfull; ++k)
+      mt::load2d(mt::smem_u32(d + (size_t)k * 256 * MB), &tm.spec_full, 2 * m0, 256 * k, mb_sp);
+    if (tm.tail) mt::load2d(mt::smem_u32(d + (size_t)tm.nfull * 256 * MB), &tm.spec_tail, 2 * m0, 256 * tm.nfull, mb_sp);
+  }
+  bool ok = mt::mbar_wait(mb_rf, 0u);
+  ok = mt::mbar_wait(mb_sp, 0u) && ok;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(a.err, 2);
+      mt::mbar_wait(mb_rf, 0u);  // the copies in flight land before the CTA leaves
+      mt::mbar_wait(mb_sp, 0u);
+    }
+    __syncthreads();
+    return;
+  }
+  modes_tile_sweeps<float, MB, NT>(a, m0, d, rt, ts);
+}
+
+cudaError_t modes_tma_encode(ModesTma* t, const void* spec, const void* rfac, int Ny, int Mp) {
+  *t = ModesTma{};
+  t->nfull = Ny / 256;
+  t->tail = Ny % 256;
+  cudaError_t e = cudaSuccess;
+  if (t->nfull > 0) {
+    if ((e = tma_encode_2d(&t->spec_full, spec, 2ull * Mp, Ny, 8ull * Mp, 16, 256)) != cudaSuccess) return e;
+    if ((e = tma_encode_2d(&t->rf_full, rfac, (unsigned long long)Mp, Ny, 4ull * Mp, 8, 256)) != cudaSuccess) return e;
+  }
+  if (t->tail > 0) {
+    if ((e = tma_encode_2d(&t->spec_tail, spec, 2ull * Mp, Ny, 8ull * Mp, 16, (unsigned)t->tail)) != cudaSuccess)
+      return e;
+    if ((e = tma_encode_2d(&t->rf_tail, rfac, (unsigned long long)Mp, Ny, 4ull * Mp, 8, (unsigned)t->tail)) !=
+        cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
 
 // The same solve by a cluster of two CTAs (on two SMs, or two slots of one):
 // CTA rank c stages and sweeps only the rows of chunks [16 c, 16 c + 16) --
@@ -1308,6 +1431,10 @@ cudaError_t launch_modes(const PoissonArgs& a, cudaStream_t s) {
   const int nm = a.Mh;  // tiles start at m = 0
   const bool pdl = (a.pdl & 2) != 0;
   if constexpr (sizeof(R) == 4) {
+    if (a.tile_tma && a.mtma && mb == 8 && a.tile_threads <= 256 && !a.tile_cluster) {
+      const size_t sm3 = modes_tma_pivot_offset(a.Ny) + (size_t)a.Ny * 32 + 128;
+      return launch_ex(pdl, k_modes_tile_tma, dim3((nm + 7) / 8), dim3(kTileThreads), sm3, s, a, *a.mtma);
+    }
     if (a.tile_cluster && mb == 8 && a.tile_threads <= 256 && a.Ny >= 64) {
       const int C = (a.Ny + 31) / 32;
       const size_t sm2 = (size_t)16 * C * 8 * (sizeof(Cplx<R>) + sizeof(R));
@@ -1429,6 +1556,7 @@ cudaError_t set_attrs_t() {
   if ((e = allow_max_dynamic_smem(k_mean_mode<R, kMeanThreadsSmall>)) != cudaSuccess) return e;
   if constexpr (sizeof(R) == 4) {
     if ((e = allow_max_dynamic_smem(k_modes_tile2<8>)) != cudaSuccess) return e;
+    if ((e = allow_max_dynamic_smem(k_modes_tile_tma)) != cudaSuccess) return e;
     if ((e = allow_max_dynamic_smem(k_modes_tile<R, 8, 512>)) != cudaSuccess) return e;
     if ((e = allow_max_dynamic_smem(k_modes_tile<R, 4, 512>)) != cudaSuccess) return e;
     if ((e = allow_max_dynamic_smem(k_modes_tile<R, 2, 512>)) != cudaSuccess) return e;

@@ -114,23 +114,27 @@ def test_launch_shape_knobs_keep_results():
 
 
 @gpu
-@pytest.mark.parametrize("nx,ny", [(256, 100), (2048, 211)])
-def test_cluster_wavenumber_solve_same_bits(nx, ny):
-    """The two-CTA cluster form of the wavenumber solve (each CTA stages and
-    sweeps half of a tile's rows; the chunk maps are exchanged through
-    distributed shared memory and both CTAs run the whole scan) gives the
-    one-CTA form's results bit for bit, ragged row counts included."""
+@pytest.mark.parametrize("nx,ny", [(64, 3), (256, 100), (2048, 211), (1024, 600)])
+def test_wavenumber_solve_forms_same_bits(nx, ny):
+    """The wavenumber solve's staging forms -- 16-byte cp.async chunks, tensor
+    copies of 256-row boxes (with a tail box for the last Ny % 256 rows), and
+    two-CTA clusters that each stage and sweep half of a tile's rows (the
+    chunk maps exchanged through distributed shared memory, both CTAs running
+    the whole scan) -- give the same results bit for bit, ragged row counts
+    included."""
     ehd = _ehd()
     amp, ph = wl.roll(77, 1e-3)
     out = []
-    for c in (0, 1):
+    for tune in (dict(tile_tma=0, tile_cluster=0), dict(tile_tma=1, tile_cluster=0), dict(tile_tma=0, tile_cluster=1)):
         r = ehd.Run(nx, ny, 190.0, 10, 10, 4000, 0.25, storage="f32", amp=amp, phase=ph)
-        ehd.ehd_tune(r.handle, "tile_cluster", c)
+        for k, v in tune.items():
+            ehd.ehd_tune(r.handle, k, v)
         r.step(30)
         out.append(r.fields())
         r.close()
     for k in out[0]:
-        assert np.array_equal(out[0][k], out[1][k]), k
+        assert np.array_equal(out[0][k], out[1][k]), ("tensor copies", k)
+        assert np.array_equal(out[0][k], out[2][k]), ("cluster", k)
 
 
 @gpu
