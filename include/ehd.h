@@ -384,11 +384,15 @@ void* ehd_batch_stream(ehd_batch* batch);
  * (rows per march warp item; 0 = chosen from the membership so the march
  * items fill about one wave), EHD_BATCH_MARCH_CTAS / EHD_BATCH_ROW_CTAS /
  * EHD_BATCH_TILE_CTAS (fixed grid of the persistent march, row-FFT and
- * wavenumber kernels).  Drops the captured graphs.  EHD_EINVAL otherwise. */
+ * wavenumber kernels), EHD_BATCH_PDL (a mask of the phase kernels launched
+ * with programmatic dependent launch: 1 the forward transforms, the default,
+ * 2 the wavenumber tiles, 4 the inverse transforms).  Drops the captured
+ * graphs.  EHD_EINVAL otherwise. */
 #define EHD_BATCH_SLAB_ROWS 1
 #define EHD_BATCH_MARCH_CTAS 2
 #define EHD_BATCH_ROW_CTAS 3
 #define EHD_BATCH_TILE_CTAS 4
+#define EHD_BATCH_PDL 5
 ehd_status ehd_batch_tune(ehd_batch* batch, int param, int value);
 
 /* Current value of a batch tuning parameter (-1 if unknown). */

@@ -434,7 +434,7 @@ def ehd_batch_stream(b) -> int:
     return lib().ehd_batch_stream(b) or 0
 
 
-BATCH_TUNE = {"slab_rows": 1, "march_ctas": 2, "row_ctas": 3, "tile_ctas": 4}
+BATCH_TUNE = {"slab_rows": 1, "march_ctas": 2, "row_ctas": 3, "tile_ctas": 4, "pdl": 5}
 
 
 def ehd_batch_tune(b, param, value):

@@ -296,6 +296,7 @@ struct BatchTables {
   int* work;                // device: items taken so far in this step's march, forward FFT,
                             // wavenumber and inverse FFT phases (zeroed before each step)
   int modes_smem;           // tile bytes for the largest admissible Ny (fixed per batch)
+  int pdl;                  // programmatic dependent launch: 1 forward transforms, 2 tiles, 4 inverse
   int emax;                 // largest admissible Nx / 64: the widest warp-FFT shape compiled in
 };
 

@@ -646,41 +646,49 @@ __device__ __forceinline__ void batch_fft_body(const BatchTables& t, int step) {
 
 template <int EMAX>
 __global__ void __launch_bounds__(128) k_batch_rfft(BatchTables t, int step) {
+  grid_dep_wait();  // programmatic dependent launch (t.pdl): the previous phase has ended
+  grid_dep_launch();
   batch_fft_body<false, EMAX>(t, step);
 }
 
 template <int EMAX>
 __global__ void __launch_bounds__(128) k_batch_irfft(BatchTables t, int step) {
+  grid_dep_wait();  // programmatic dependent launch (t.pdl): the previous phase has ended
+  grid_dep_launch();
   batch_fft_body<true, EMAX>(t, step);
 }
 
 template <int EMAX>
 __global__ void __launch_bounds__(128, 5) k_batch_irfft_narrow(BatchTables t, int step) {
+  grid_dep_wait();  // programmatic dependent launch (t.pdl): the previous phase has ended
+  grid_dep_launch();
   batch_fft_body<true, EMAX>(t, step);
 }
 
 cudaError_t launch_batch_rfft(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   switch (t.emax) {
-    case 1: k_batch_rfft<1><<<grid, 128, 0, s>>>(t, step); break;
-    case 2: k_batch_rfft<2><<<grid, 128, 0, s>>>(t, step); break;
-    case 4: k_batch_rfft<4><<<grid, 128, 0, s>>>(t, step); break;
-    case 8: k_batch_rfft<8><<<grid, 128, 0, s>>>(t, step); break;
-    case 16: k_batch_rfft<16><<<grid, 128, 0, s>>>(t, step); break;
-    default: k_batch_rfft<32><<<grid, 128, 0, s>>>(t, step); break;
+    case 1: e = launch_ex((t.pdl & 1) != 0, k_batch_rfft<1>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 2: e = launch_ex((t.pdl & 1) != 0, k_batch_rfft<2>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 4: e = launch_ex((t.pdl & 1) != 0, k_batch_rfft<4>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 8: e = launch_ex((t.pdl & 1) != 0, k_batch_rfft<8>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 16: e = launch_ex((t.pdl & 1) != 0, k_batch_rfft<16>, dim3(grid), dim3(128), 0, s, t, step); break;
+    default: e = launch_ex((t.pdl & 1) != 0, k_batch_rfft<32>, dim3(grid), dim3(128), 0, s, t, step); break;
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_batch_irfft(const BatchTables& t, int step, int grid, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   switch (t.emax) {
-    case 1: k_batch_irfft_narrow<1><<<grid, 128, 0, s>>>(t, step); break;
-    case 2: k_batch_irfft_narrow<2><<<grid, 128, 0, s>>>(t, step); break;
-    case 4: k_batch_irfft_narrow<4><<<grid, 128, 0, s>>>(t, step); break;
-    case 8: k_batch_irfft_narrow<8><<<grid, 128, 0, s>>>(t, step); break;
-    case 16: k_batch_irfft<16><<<grid, 128, 0, s>>>(t, step); break;
-    default: k_batch_irfft<32><<<grid, 128, 0, s>>>(t, step); break;
+    case 1: e = launch_ex((t.pdl & 4) != 0, k_batch_irfft_narrow<1>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 2: e = launch_ex((t.pdl & 4) != 0, k_batch_irfft_narrow<2>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 4: e = launch_ex((t.pdl & 4) != 0, k_batch_irfft_narrow<4>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 8: e = launch_ex((t.pdl & 4) != 0, k_batch_irfft_narrow<8>, dim3(grid), dim3(128), 0, s, t, step); break;
+    case 16: e = launch_ex((t.pdl & 4) != 0, k_batch_irfft<16>, dim3(grid), dim3(128), 0, s, t, step); break;
+    default: e = launch_ex((t.pdl & 4) != 0, k_batch_irfft<32>, dim3(grid), dim3(128), 0, s, t, step); break;
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t fftw_set_tables() {

@@ -978,6 +978,7 @@ __global__ void __launch_bounds__(128) k_march2(StepArgs a) {
 template <bool PERT>
 __global__ void __launch_bounds__(128, 3) k_batch_march(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char march_smem[];
+  grid_dep_launch();  // the forward transforms may take slots as this grid drains
   constexpr int NST = 2;
   unsigned char* ring = march_smem + (size_t)(threadIdx.x >> 5) * March2Stages<float, float, NST>::kBytesPerWarp;
   const int n = t.counts[1];

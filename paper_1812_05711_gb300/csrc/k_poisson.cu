@@ -952,6 +952,8 @@ __global__ void __launch_bounds__(NT) k_mean_mode(PoissonArgs a) {
 // Batch kernels: CTAs take (run, tile) items / one CTA per run.
 __global__ void __launch_bounds__(kTileThreads) k_batch_modes(BatchTables t, int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  grid_dep_wait();  // programmatic dependent launch (t.pdl): the forward transforms have ended
+  grid_dep_launch();
   __shared__ TileScratch<float, kBatchTileModes, kTileThreads> ts;
   __shared__ int s_it;
   const int n = t.counts[3];
@@ -1588,8 +1590,7 @@ int batch_modes_ctas_per_sm(int smem) {
 }
 
 cudaError_t launch_batch_modes(const BatchTables& t, int step, int grid, cudaStream_t s) {
-  k_batch_modes<<<grid, kTileThreads, t.modes_smem, s>>>(t, step);
-  return cudaGetLastError();
+  return launch_ex((t.pdl & 2) != 0, k_batch_modes, dim3(grid), dim3(kTileThreads), (size_t)t.modes_smem, s, t, step);
 }
 
 cudaError_t launch_batch_mean(const BatchTables& t, int step, int grid, cudaStream_t s) {
