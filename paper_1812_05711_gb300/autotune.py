@@ -14,8 +14,10 @@ import json
 import os
 import time
 
-from . import BATCH_TUNE, ehd_batch_stream, ehd_batch_tune, ehd_batch_tune_get
+from . import ehd_batch_stream, ehd_batch_tune, ehd_batch_tune_get
 
+# the launch shapes the tuner times (the batch's other settings stay as they are)
+SHAPES = ("slab_rows", "march_ctas", "row_ctas", "tile_ctas")
 CACHE = os.environ.get("EHD_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "ehd_gb300_tune.json"))
 
 
@@ -67,7 +69,7 @@ def tune(batch, steps: int = 8, ticks: int = 4, use_cache: bool = True, verbose:
         for k, v in db[key]["params"].items():
             ehd_batch_tune(batch.handle, k, v)
         return db[key]
-    base = {k: ehd_batch_tune_get(batch.handle, k) for k in BATCH_TUNE}
+    base = {k: ehd_batch_tune_get(batch.handle, k) for k in SHAPES}
     auto_rows = base["slab_rows"]
     cands = []
     for rows in sorted({max(4, auto_rows // 2), auto_rows, auto_rows * 2, 8, 12, 16, 24, 0}):
