@@ -51,6 +51,9 @@ class Request:
     after: int | None = None
     keep_state: bool = False  # report the final populations (f, g)
     u_ion: float | None = None  # lattice ion drift speed (None: the server's)
+    # 1: the FP32 perturbation form (charge populations as the departure from
+    # an FP64 x-uniform base state: growth rates of small rolls as in FP64)
+    perturbation: int = 0
 
 
 @dataclass
@@ -144,7 +147,8 @@ class Server:
             u_ion = self.u_ion if req.u_ion is None else req.u_ion
             cont = req.after is not None
             run = Run(req.Nx, req.Ny, req.T, req.C, req.M, req.Fe, req.Lambda, storage="f32",
-                      u_ion=u_ion, amp=[] if cont else req.amp, phase=[] if cont else req.phase)
+                      u_ion=u_ion, amp=[] if cont else req.amp, phase=[] if cont else req.phase,
+                      perturbation=req.perturbation)
             if cont:
                 run.load(*self.states.pop(req.after))
             first = req.steps - req.window if req.window else req.steps

@@ -25,7 +25,10 @@ def test_server_results_equal_solo_runs_and_respect_budget():
     reqs = []
     for k, (nx, T, C, steps) in enumerate(specs):
         a, ph = wl.roll(500 + k, 1e-3)
-        reqs.append(serve.Request(k, nx, wl.ny_for(nx), T, C, 10.0, 4000.0, 0.25, steps, a, ph, arrival=0.0))
+        # every third request in the FP32 perturbation form (its base state
+        # advances on the batch's third stream)
+        reqs.append(serve.Request(k, nx, wl.ny_for(nx), T, C, 10.0, 4000.0, 0.25, steps, a, ph, arrival=0.0,
+                                  perturbation=int(k % 3 == 1)))
     fp = ehd.ehd_footprint(256, wl.ny_for(256), 1)
     budget = fp + 2 * ehd.ehd_footprint(128, wl.ny_for(128), 1)  # forces queueing
     srv = serve.Server(budget, max_runs=3, tick_steps=6, max_nx=256, max_ny=wl.ny_for(256), u_ion=5e-3,
@@ -47,7 +50,7 @@ def test_server_results_equal_solo_runs_and_respect_budget():
     for res in results:
         q = reqs[res.rid]
         solo = ehd.Run(q.Nx, q.Ny, q.T, q.C, q.M, q.Fe, q.Lambda, storage="f32", u_ion=5e-3, amp=q.amp,
-                       phase=q.phase)
+                       phase=q.phase, perturbation=q.perturbation)
         solo.step(q.steps)
         d = solo.diagnostics()
         assert res.diagnostics["step"] == q.steps

@@ -12,11 +12,14 @@ import paper_1812_05711_gb300.serve as serve  # noqa: E402
 
 class FakeRun:
     _next = 0
+    created = []
 
     def __init__(self, Nx, Ny, *args, **kwargs):
         FakeRun._next += 1
         self.handle = FakeRun._next
         self.Nx, self.Ny = Nx, Ny
+        self.kwargs = kwargs
+        FakeRun.created.append(self)
         self.closed = False
         self.steps_done = 0
         self.loaded = None
@@ -172,3 +175,15 @@ def test_measurement_window_and_continuation(fakes):
     assert len(first_tick) == 2                # a and c together, b waiting
     with pytest.raises(ValueError):
         srv.submit(fakes.Request(9, 64, 64, 1.0, 1.0, 1.0, 1.0, 0.25, 4, after=77))
+
+
+def test_perturbation_form_requests(fakes):
+    """A request may ask for the FP32 perturbation form; the server creates
+    its run with it (the others keep the default form)."""
+    FakeRun.created.clear()
+    srv = fakes.Server(hbm_budget=10 ** 9, max_runs=4, tick_steps=2, max_nx=128, max_ny=128, clock=Clock())
+    a = fakes.Request(0, 64, 64, 150.0, 10.0, 10.0, 4000.0, 0.25, 4, perturbation=1)
+    b = fakes.Request(1, 64, 64, 180.0, 10.0, 10.0, 4000.0, 0.25, 4)
+    srv.serve([a, b], realtime=False)
+    forms = sorted(r.kwargs.get("perturbation") for r in FakeRun.created)
+    assert forms == [0, 1]
