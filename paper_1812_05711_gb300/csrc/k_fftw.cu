@@ -390,8 +390,9 @@ __device__ __forceinline__ int zpad(int k) { return k + 4 * (k >> 6); }
 // holds Z[k1 + 16 (4 q + i) + 256 d] in (zr[4 d + i], zi[4 d + i]).
 // The first pass's twiddles W_1024^(t k1), k1 = 1 .. 15 (table [k1][t] after
 // the first 2 L entries), loaded before the row so that their latency
-// overlaps the row's (with the forward's untangle twiddles likewise: 119.7
-// against 122.3 us per 2048 x 1680 step, 64-72 registers, still one wave).
+// overlaps the row's (119.7 against 122.3 us per 2048 x 1680 step; loading
+// the forward's untangle twiddles early too helped before the packed adds,
+// but with them it spills at the 80-register bound: 117.0 against 115.6 us).
 __device__ __forceinline__ void cta_twiddles(const float2* __restrict__ tw, float2 (&w1)[16]) {
   const float2* __restrict__ tw1 = tw + 2 * kCtaL;
   w1[0] = make_float2(1.0f, 0.0f);
@@ -455,10 +456,8 @@ __global__ void __launch_bounds__(kCtaT, 12) k_rfft_cta(PoissonArgs a) {
   const float2* __restrict__ tw = static_cast<const float2*>(a.tw);
   // the twiddle tables are constant: loaded before the wait for the step
   // kernel that writes the charge density (programmatic dependent launch)
-  float2 w1[16], wu[8];
+  float2 w1[16];
   cta_twiddles(tw, w1);
-#pragma unroll
-  for (int j = 0; j < 8; ++j) wu[j] = __ldg(tw + t + 64 * j);  // the untangle's W_N^k, k = t + 64 j
   grid_dep_wait();
   grid_dep_launch();
   const float* row = static_cast<const float*>(a.rhoc) + (long long)y * a.P;
@@ -521,7 +520,7 @@ __global__ void __launch_bounds__(kCtaT, 12) k_rfft_cta(PoissonArgs a) {
     const int k = t + 64 * j;  // 0 .. 511
     const float2 zk = sm[zpad(k)];
     const float2 zp = sm[zpad((kCtaL - k) & (kCtaL - 1))];
-    const float2 wk = wu[j];
+    const float2 wk = __ldg(tw + k);
     // E = (zk + conj zp) / 2, D = (zk - conj zp) / 2, O = -i D
     const float Er = 0.5f * (zk.x + zp.x), Ei = 0.5f * (zk.y - zp.y);
     const float Dr = 0.5f * (zk.x - zp.x), Di = 0.5f * (zk.y + zp.y);
