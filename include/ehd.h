@@ -223,7 +223,15 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * pivots staged by tensor copies of 256-row boxes with mbarrier completion;
  * 0, the default, by 16-byte cp.async chunks from all threads, which is
  * faster for these 64- and 32-byte rows (2048 x 1680: 117.2-117.9 against
- * 118.4 us per step); the same results bit for bit).
+ * 118.4 us per step); the same results bit for bit), EHD_TUNE_SLAB_SHIFT
+ * (march form with two columns per lane and cp.async staging: rows d by
+ * which the slab partition advances each step, 0..Ny; step k of the
+ * sequence (k = step number mod 16, the graph length) uses slabs that start
+ * at rows b S - (k d mod S), so each slab begins on the rows that the slab
+ * below it wrote last in the step before, which are then still in L2; 0
+ * keeps one partition; the default is 4 for runs whose populations exceed
+ * the L2 size and 0 otherwise; results differ in rounding order only, where
+ * a row's charge is summed from slab-boundary partials).
  * Drops the run's captured graphs.  EHD_EINVAL for an unknown parameter or
  * value. */
 #define EHD_TUNE_SLAB_ROWS 1
@@ -238,6 +246,7 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
 #define EHD_TUNE_TILE_THREADS 10
 #define EHD_TUNE_TILE_CLUSTER 11
 #define EHD_TUNE_TILE_TMA 12
+#define EHD_TUNE_SLAB_SHIFT 13
 ehd_status ehd_tune(ehd_run* run, int param, int value);
 
 /* Current value of a tuning parameter (-1 for an unknown one or NULL run). */

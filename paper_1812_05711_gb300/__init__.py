@@ -245,7 +245,7 @@ def ehd_poisson_noalloc(Nx, Ny, eps, phi0, wall_mode, rhoc_ptr: int, phi_ptr: in
 
 TUNE = {"slab_rows": 1, "ring_depth": 2, "step_kernel": 3, "cols_per_lane": 4, "tile_modes": 5, "pdl": 6, "fft_cta": 7,
         "y_solver": 8, "march_tma": 9, "tile_threads": 10,
-        "tile_cluster": 11, "tile_tma": 12}
+        "tile_cluster": 11, "tile_tma": 12, "slab_shift": 13}
 
 
 def ehd_tune(h, param, value: int):

@@ -49,6 +49,7 @@ Allocator g_alloc;
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr int kGraphSteps = 16;  // steps per captured graph (even: buffer parity)
+constexpr int kSlabShift = 4;    // default slab_shift of large runs (rows per step)
 
 size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
@@ -95,6 +96,7 @@ struct ehd_run {
   int rows = 1;        // rows per CTA of the node-parallel step kernel
   int step_kernel = 0; // 0 march form, 1 node-parallel push form
   int slab_rows = 4;   // rows per warp slab of the march form
+  int slab_shift = 0;  // rows the slab partition of the march form advances per step (see march_shift)
   int ring_depth = 2;  // rows staged ahead in the march form
   int cols_per_lane = 2;
   int tile_modes = 0;  // wavenumbers per CTA of the mode solve (0: largest that fits)
@@ -434,15 +436,29 @@ cudaError_t launch_march_run(const ehd_run* r, const StepArgs& sa, int cur) {
   return launch_march(sa, r->storage, r->real_f64, r->stream);
 }
 
+// Slab offset of the march form at position k of the step sequence (k = step
+// number mod the graph length).  The partition advances by slab_shift rows a
+// step, so that each slab of the next step starts on the rows that the last
+// step wrote last -- those are still in L2 when the next march begins, and
+// its first reads hit there instead of in HBM.  Which slab computes a row
+// changes only where partial charge sums are added (rounding order).
+int march_shift(const ehd_run* r, long k) {
+  if (r->slab_shift <= 0 || r->step_kernel != 0 || r->cols_per_lane != 2 || tma_form(r) || r->batch) return 0;
+  return (int)((k * (long)r->slab_shift) % r->slab_rows);
+}
+
 // One coupled step from buffer `cur`: collide+stream with the wall-flux
 // partials, then the Poisson solve of the new charge (which also adds the
 // fluxes to the FP64 totals).  The march form writes the new charge itself;
 // the node-parallel form needs the separate charge-moment kernel.
-cudaError_t enqueue_step(ehd_run* r, int cur) {
-  const StepArgs sa = step_args(r, cur);
+cudaError_t enqueue_step(ehd_run* r, int cur, long k) {
+  StepArgs sa = step_args(r, cur);
   if (r->step_kernel == 0) {
+    sa.slab_off = march_shift(r, k);
+    PoissonArgs pa = poisson_args(r, true);
+    pa.xoff = sa.slab_off;
     cudaError_t e = launch_march_run(r, sa, cur);
-    if (e == cudaSuccess) e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
+    if (e == cudaSuccess) e = launch_poisson(pa, r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join);
     if (e == cudaSuccess && r->pert) e = enqueue_base(r, cur);
     if (e == cudaSuccess && r->pert) e = cudaStreamWaitEvent(r->stream, r->ev_base, 0);
     return e;
@@ -458,7 +474,7 @@ ehd_status build_graph(ehd_run* r, int cur) {
   cudaError_t e = cudaSuccess;
   int c = cur;
   for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
-    e = enqueue_step(r, c);
+    e = enqueue_step(r, c, k);
     c = 1 - c;
   }
   cudaError_t e2 = cudaStreamEndCapture(r->stream, &g);
@@ -766,6 +782,14 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
         (long long)sms * march_warps_per_sm(r->storage, r->real_f64, r->cols_per_lane, r->ring_depth);
     long long rows = ((long long)Ny * r->nstrips + resident - 1) / resident;
     r->slab_rows = (int)std::max(4LL, std::min((long long)Ny, rows));
+    // populations larger than L2: the slab partition advances a step, so that
+    // the rows a step wrote last are read first by the next (see
+    // march_shift); only where the one extra slab per strip keeps one wave
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, r->device);
+    const long long slabs = (Ny + r->slab_rows - 1) / r->slab_rows + 1;
+    const long long pop_bytes = 36 * (long long)Ny * r->P * (long long)storage_bytes(r->storage);
+    if (pop_bytes > (long long)l2 && (long long)r->nstrips * slabs <= resident) r->slab_shift = kSlabShift;
   }
   // rows per CTA of the node-parallel kernel: keep >= ~4 CTAs per SM
   {
@@ -942,6 +966,10 @@ ehd_status ehd_tune(ehd_run* r, int param, int value) {
       if (value < std::min(4, r->Ny) || value > r->Ny) return fail(EHD_EINVAL, "slab rows must be in [min(4, Ny), Ny]");
       r->slab_rows = value;
       break;
+    case EHD_TUNE_SLAB_SHIFT:
+      if (value < 0 || value > r->Ny) return fail(EHD_EINVAL, "slab shift must be in [0, Ny]");
+      r->slab_shift = value;
+      break;
     case EHD_TUNE_RING_DEPTH:
       if (value != 2 && value != 3 && value != 4 && value != 6) return fail(EHD_EINVAL, "ring depth must be 2, 3, 4 or 6");
       if (value != 2 && r->ex_spectral) return fail(EHD_EINVAL, "spectral E_x runs keep ring depth 2");
@@ -1028,6 +1056,7 @@ int ehd_tune_get(ehd_run* r, int param) {
   if (!r) return -1;
   switch (param) {
     case EHD_TUNE_SLAB_ROWS: return r->slab_rows;
+    case EHD_TUNE_SLAB_SHIFT: return r->slab_shift;
     case EHD_TUNE_RING_DEPTH: return r->ring_depth;
     case EHD_TUNE_STEP_KERNEL: return r->step_kernel;
     case EHD_TUNE_COLS_PER_LANE: return r->cols_per_lane;
@@ -1065,7 +1094,7 @@ ehd_status ehd_step(ehd_run* r, long n) {
     r->step += kGraphSteps;
   }
   for (; n > 0; --n) {
-    EHD_CK(enqueue_step(r, r->cur));
+    EHD_CK(enqueue_step(r, r->cur, r->step % kGraphSteps));
     r->cur = 1 - r->cur;
     r->step += 1;
   }
@@ -1087,7 +1116,10 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
     if (e == cudaSuccess) e = cudaEventCreate(&x);
   for (long t = 0; t < n && e == cudaSuccess; ++t) {
     cudaEvent_t* E = &ev[(size_t)NE * t];
-    const StepArgs sa = step_args(r, r->cur);
+    StepArgs sa = step_args(r, r->cur);
+    sa.slab_off = march_shift(r, r->step % kGraphSteps);
+    PoissonArgs pa = poisson_args(r, true);
+    pa.xoff = sa.slab_off;
     const int nxt = 1 - r->cur;
     if (e == cudaSuccess) e = cudaEventRecord(E[0], r->stream);
     if (e == cudaSuccess)
@@ -1099,7 +1131,7 @@ ehd_status ehd_step_profile(ehd_run* r, long n, double* ms_out) {
                       r->rhoc, r->stream);
     if (e == cudaSuccess) e = cudaEventRecord(E[2], r->stream);
     if (e == cudaSuccess)
-      e = launch_poisson(poisson_args(r, true), r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join, E + 4);
+      e = launch_poisson(pa, r->real_f64, r->stream, r->side, r->ev_fork, r->ev_join, E + 4);
     if (e == cudaSuccess && r->pert) e = enqueue_base(r, r->cur);  // third stream, joined at the step's end
     if (e == cudaSuccess && r->pert) e = cudaStreamWaitEvent(r->stream, r->ev_base, 0);
     if (e == cudaSuccess) e = cudaEventRecord(E[3], r->stream);

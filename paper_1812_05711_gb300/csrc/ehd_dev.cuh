@@ -130,9 +130,11 @@ struct StepArgs {
   int wall_mode;
   // march form only
   void* rhoc_out;            // R [Ny][P]: rho_c of the new state (slab-boundary rows: partial, see rhoc_dn)
-  void* rhoc_dn;             // R [nslab][P]: row b*slab_rows - 1, charge of the populations pushed down by slab b
-  void* rhoc_up;             // R [nslab][P]: row b*slab_rows, charge of the populations pushed up by slab b - 1
+  void* rhoc_dn;             // R [nslab][P]: row y0(b) - 1, charge of the populations pushed down by slab b
+  void* rhoc_up;             // R [nslab][P]: row y0(b), charge of the populations pushed up by slab b - 1
   int slab_rows;             // rows per warp slab
+  int slab_off;              // slab b covers rows [b*slab_rows - slab_off, (b+1)*slab_rows - slab_off) within
+                             // [0, Ny), 0 <= slab_off < slab_rows (cp.async march, two columns per lane only)
   int nstrips;               // 32-column strips (30 owned columns each)
   int ring_depth;            // rows staged ahead by cp.async (2, 3, 4 or 6)
   int cols_per_lane;         // 1: 32-column strips (30 owned); 2: 64-column strips (60 owned)
@@ -147,6 +149,7 @@ struct PoissonArgs {
   const void* rhoc_dn;       // slab-boundary partials of the march form (see StepArgs), added to rhoc
   const void* rhoc_up;
   int xslab;                 // slab height of those partials; 0: rhoc is complete
+  int xoff;                  // slab_off of the step kernel that wrote them
   double inv_eps;            // 1 / eps
   void* spec;                // half spectrum, complex R [Ny][Mp]
   void* spec0;               // row sums (m = 0), [Ny]: double, or float (hi, lo) pairs when R = float
@@ -191,9 +194,11 @@ __device__ __forceinline__ void rhoc_partials(const PoissonArgs& a, int y, const
   dn = nullptr;
   up = nullptr;
   if (a.xslab > 0) {
-    const int S = a.xslab;
-    if ((y + 1) % S == 0 && y + 1 < a.Ny) dn = static_cast<const R*>(a.rhoc_dn) + (long long)((y + 1) / S) * a.P;
-    if (y % S == 0 && y > 0) up = static_cast<const R*>(a.rhoc_up) + (long long)(y / S) * a.P;
+    // slab b starts at row b S - off (b >= 1): row y closes a slab when
+    // y + 1 + off is a multiple of S and opens one when y + off is
+    const int S = a.xslab, yd = y + 1 + a.xoff, yu = y + a.xoff;
+    if (yd % S == 0 && y + 1 < a.Ny) dn = static_cast<const R*>(a.rhoc_dn) + (long long)(yd / S) * a.P;
+    if (yu % S == 0 && y > 0) up = static_cast<const R*>(a.rhoc_up) + (long long)(yu / S) * a.P;
   }
 }
 

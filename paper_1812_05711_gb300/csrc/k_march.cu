@@ -558,9 +558,11 @@ __device__ __forceinline__ void march2_body(const StepArgs& a, int strip, int sl
   constexpr int NST = NSTAGE, SL = St::kSlots, SB = St::kSlotBytes;
   const int lane = threadIdx.x & 31;
   const int Nx = a.Nx, Ny = a.Ny, P = a.P, ns = a.nstrips;
-  const int y0 = slab * a.slab_rows;
+  // slab b: rows [b S - off, (b + 1) S - off) clipped to the channel (slab 0
+  // is the short one when off > 0; see slab_off)
+  const int y0 = max(0, slab * a.slab_rows - a.slab_off);
   if (y0 >= Ny) return;  // whole warp
-  const int y1 = min(y0 + a.slab_rows, Ny);
+  const int y1 = min((slab + 1) * a.slab_rows - a.slab_off, Ny);
   const int xs = strip * 60;
   const int xc = (xs - 2 + 2 * lane + 2 * Nx) % Nx;  // even: the pair (xc, xc + 1)
   const bool owned = lane >= 1 && lane <= 30 && xs + 2 * (lane - 1) < Nx;
@@ -1635,7 +1637,8 @@ cudaError_t march_n(const StepArgs& a, cudaStream_t s) {
 
 template <class S, class R, int NST, bool SPECX = false>
 cudaError_t march2_n(const StepArgs& a, cudaStream_t s) {
-  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_rows - 1) / a.slab_rows);
+  if (a.slab_off < 0 || a.slab_off >= a.slab_rows) return cudaErrorInvalidValue;
+  const long long warps = (long long)a.nstrips * ((a.Ny + a.slab_off + a.slab_rows - 1) / a.slab_rows);
   const unsigned grid = (unsigned)((warps + 3) / 4);
   const size_t smem = 4 * March2Stages<S, R, NST, SPECX>::kBytesPerWarp;
   const bool pdl = (a.pdl & 8) != 0;  // the step kernel waits for phi after staging its first rows

@@ -85,3 +85,13 @@ def test_batch_queries_reject_null():
     assert L.ehd_batch_admits(None, 128, 104, 1) == -1
     assert L.ehd_batch_memory(None, None, None) == -1
     assert "NULL" in ehd.ehd_last_error()
+
+
+def test_tune_names_match_the_header():
+    """The binding's tuning names carry the header's parameter ids
+    (EHD_TUNE_* for runs, EHD_BATCH_* for batches), one for one."""
+    src = open(os.path.join(ROOT, "include", "ehd.h")).read()
+    run = {k.lower(): int(v) for k, v in re.findall(r"#define EHD_TUNE_([A-Z_]+) (\d+)", src)}
+    bat = {k.lower(): int(v) for k, v in re.findall(r"#define EHD_BATCH_([A-Z_]+) (\d+)", src)}
+    assert run == ehd.TUNE
+    assert bat == ehd.BATCH_TUNE

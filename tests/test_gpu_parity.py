@@ -310,6 +310,77 @@ def test_slab_heights_fp64_parity(slab):
 
 
 @gpu
+@pytest.mark.parametrize("slab,shift", [(5, 1), (5, 2), (4, 3), (17, 4), (17, 16), (51, 7)])
+def test_slab_shift_fp64_parity(slab, shift):
+    """The march form with a slab partition that advances `shift` rows each
+    step (slab b of step k starts at row b S - (k shift mod S)): every offset
+    of the cycle occurs, including a one-row slab at the injector (offset
+    S - 1) and one at the collector, and the run keeps the oracle's state
+    through graph replays and single steps alike (120 = 7 x 16 + 8 steps)."""
+    w = wl.small_channel(64, seed=29)
+    ehd, p, s, run = _pair(w, u_ion=5e-3)
+    ehd.ehd_tune(run.handle, "step_kernel", 0)  # plain FP64 defaults to the push form
+    ehd.ehd_tune(run.handle, "slab_rows", slab)
+    ehd.ehd_tune(run.handle, "slab_shift", shift)
+    assert ehd.ehd_tune_get(run.handle, "slab_shift") == shift
+    run.step(120)
+    o.step(s, 120)
+    e = _errors(p, run.fields(), o.fields(s))
+    assert max(e.values()) <= 1e-12, (slab, shift, e)
+    F = o.fields(s)
+    assert run.diagnostics()["charge"] == pytest.approx(F["rho_c"].sum(), rel=1e-13)
+
+
+@gpu
+@pytest.mark.parametrize("pert", [0, 1])
+def test_slab_shift_fp32_parity_and_graph_replay(pert):
+    """FP32 (shifted storage, and the perturbation form) with an advancing
+    slab partition: within the FP32 bar of the oracle after 1000 steps at
+    128 x 104, and 16 steps replayed from the captured graph equal 16 single
+    steps bit for bit (both take the offsets of steps 0..15)."""
+    ehd = _ehd()
+    w = wl.plain_fp64_channel()
+    p = o.setup(*w.args())
+    s = o.init_state(p, w.amp, w.phase)
+
+    def mk():
+        r = ehd.Run(*w.args(), storage="f32", amp=w.amp, phase=w.phase, perturbation=pert)
+        ehd.ehd_tune(r.handle, "slab_rows", 9)
+        ehd.ehd_tune(r.handle, "slab_shift", 4)
+        return r
+
+    r1, r2 = mk(), mk()
+    r1.step(16)
+    for _ in range(16):
+        r2.step(1)
+    a, b = r1.save(), r2.save()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(r1.fields()["phi"], r2.fields()["phi"])
+    r2.close()
+    r1.step(1000 - 16)
+    o.step(s, 1000)
+    e = _errors(p, r1.fields(), o.fields(s))
+    assert max(e.values()) <= 2e-5, (pert, e)
+    r1.close()
+
+
+@gpu
+def test_slab_shift_default_only_beyond_l2():
+    """The advancing partition is on by default only where the populations
+    exceed L2 (2048 x 1680 FP32: 495 MB) and off for runs that fit (128 x
+    104), whose results stay those of one fixed partition."""
+    ehd = _ehd()
+    big = wl.large_channel()
+    small = wl.plain_fp64_channel()
+    r = ehd.Run(*big.args(), storage="f32", amp=big.amp, phase=big.phase)
+    assert ehd.ehd_tune_get(r.handle, "slab_shift") > 0
+    r.close()
+    r = ehd.Run(*small.args(), storage="f32", amp=small.amp, phase=small.phase)
+    assert ehd.ehd_tune_get(r.handle, "slab_shift") == 0
+    r.close()
+
+
+@gpu
 def test_c1_plain_fp64_10000_steps_vs_oracle():
     """The plain FP64 configuration run to its full length: 128 x 104,
     T = 200, 10,000 coupled steps on the GPU and in the oracle.  Every field
