@@ -281,6 +281,13 @@ StepArgs step_args(const ehd_run* r, int cur) {
   return a;
 }
 
+// float-float split of a host constant: hi = fl32(v), lo = fl32(v - hi)
+// (v - hi is exact in FP64), as the device forms it from a double
+void split_ff(double v, float* f) {
+  f[0] = (float)v;
+  f[1] = (float)(v - (double)f[0]);
+}
+
 // with_flux: the charge density comes from a step (wall-flux partials
 // pending, and the march form's slab-boundary partials when it ran)
 PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
@@ -305,6 +312,10 @@ PoissonArgs poisson_args(const ehd_run* r, bool with_flux) {
   a.phibar = r->phibar;
   a.Ebar = r->Ebar;
   a.phi0 = r->pert ? 0.0 : r->phi0;  // perturbation form: the base carries the wall potentials
+  a.mW = (double)r->Nx * a.phi0;
+  a.mC = (r->wall_mode == 0) ? 1.0 / (2.0 * r->Ny) : 1.0 / (double)(r->Ny + 1);
+  split_ff(a.mW, a.mWf);
+  split_ff(a.mC, a.mCf);
   a.wall_mode = r->wall_mode;
   a.flux_part = with_flux ? r->flux_part : nullptr;
   a.nflux = r->nxb;

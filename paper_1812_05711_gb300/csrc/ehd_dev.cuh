@@ -160,6 +160,12 @@ struct PoissonArgs {
   void* phibar;              // row-mean potential [Ny]: double, or float (hi, lo) pairs when R = float
   void* Ebar;                // R [Ny]
   double phi0;               // injector potential (collector is 0)
+  // mean-mode (m = 0) constants, formed on the host: the injector wall value
+  // W = Nx phi0 in spectral units and the closure factor 1 / (2 Ny) (walls
+  // halfway) or 1 / (Ny + 1) (walls on nodes); in FP64 and split into
+  // float-float (hi, lo) pairs, hi = fl32(v), lo = fl32(v - hi)
+  double mW, mC;
+  float mWf[2], mCf[2];
   int wall_mode;
   const double* flux_part;   // [2][nflux] wall-flux partials of the last step, or nullptr
   int nflux;

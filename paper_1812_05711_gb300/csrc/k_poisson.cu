@@ -767,6 +767,8 @@ struct MeanNum<double> {
   using T = double;
   __device__ static T from(double v) { return v; }
   __device__ static T from_f(float v) { return (double)v; }
+  __device__ static T from_i(int v) { return (double)v; }
+  __device__ static T pair(double d, float, float) { return d; }
   __device__ static double to(T v) { return v; }
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static T mul(T a, T b) { return a * b; }
@@ -779,6 +781,10 @@ struct MeanNum<float> {
   using T = ff;
   __device__ static T from(double v) { return ff_from(v); }
   __device__ static T from_f(float v) { return {v, 0.0f}; }
+  // exact for |v| <= 2^24, and then equal to ff_from((double)v)
+  __device__ static T from_i(int v) { return {(float)v, 0.0f}; }
+  // a constant the host split into (hi, lo): equal to ff_from(d)
+  __device__ static T pair(double, float hi, float lo) { return {hi, lo}; }
   __device__ static double to(T v) { return ff_to(v); }
   __device__ static T add(T a, T b) { return ff_add(a, b); }
   __device__ static T mul(T a, T b) { return ff_mul(a, b); }
@@ -861,25 +867,30 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   T* v = reinterpret_cast<T*>(smem_raw);  // [Ny]: s, then S, then T
   const int Ny = a.Ny, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (a.flux_part) {
-    // FP64 totals of the wall fluxes: a shuffle tree over the strips
+    // FP64 totals of the wall fluxes: a shuffle tree over the strips, in the
+    // warps that hold partials (the others' totals would be +0, whose
+    // addition changes nothing; FP64 issue is slow on this part)
+    const int nfw = min(NW, (a.nflux + 31) / 32);
     double qi = 0.0, qo = 0.0;
-    for (int b = t; b < a.nflux; b += NT) {
-      qi += a.flux_part[b];
-      qo += a.flux_part[a.nflux + b];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      qi += __shfl_down_sync(0xffffffffu, qi, o);
-      qo += __shfl_down_sync(0xffffffffu, qo, o);
+    if (warp < nfw) {
+      for (int b = t; b < a.nflux; b += NT) {
+        qi += a.flux_part[b];
+        qo += a.flux_part[a.nflux + b];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        qi += __shfl_down_sync(0xffffffffu, qi, o);
+        qo += __shfl_down_sync(0xffffffffu, qo, o);
+      }
     }
     auto& fq = ms.fq;
-    if (lane == 0) {
+    if (lane == 0 && warp < nfw) {
       fq[0][warp] = qi;
       fq[1][warp] = qo;
     }
     sub_sync<NT>();
     if (t == 0) {
       double si = 0.0, so = 0.0;
-      for (int w = 0; w < NW; ++w) {
+      for (int w = 0; w < nfw; ++w) {
         si += fq[0][w];
         so += fq[1][w];
       }
@@ -903,17 +914,18 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   for (int j = j0; j < j1; ++j) Sv[j] = v[j];
   const T T_all = block_prefix_sum<R, NT>(v, j0, j1, ms);   // T_Ny
   const T T_last = (Ny >= 2) ? v[Ny - 2] : N::from_f(0.0f);  // T_{Ny-1}
-  // wall values in spectral units: W = Nx phi0 at the injector, 0 at the collector
-  const T W = N::from((double)a.Nx * a.phi0);
+  // wall values in spectral units: W = Nx phi0 at the injector, 0 at the
+  // collector; W and the closure factor come from the host
+  const T W = N::pair(a.mW, a.mWf[0], a.mWf[1]);
   T Dm, Pm;  // D_{-1}, phi_{-1}
   if (a.wall_mode == 0) {
-    // phi_{-1} + phi_0 = 2W, phi_Ny + phi_{Ny-1} = 0
+    // phi_{-1} + phi_0 = 2W, phi_Ny + phi_{Ny-1} = 0: D_{-1} = -(2W + T_Ny + T_{Ny-1}) / (2 Ny)
     const T num = N::add(N::add(W, W), N::add(T_all, T_last));
-    Dm = N::mul(N::neg(num), N::from(1.0 / (2.0 * Ny)));
+    Dm = N::mul(N::neg(num), N::pair(a.mC, a.mCf[0], a.mCf[1]));
     Pm = N::add(W, N::neg(N::mul(Dm, N::from_f(0.5f))));
   } else {
-    // phi_{-1} = W, phi_Ny = 0
-    Dm = N::mul(N::neg(N::add(W, T_all)), N::from(1.0 / (double)(Ny + 1)));
+    // phi_{-1} = W, phi_Ny = 0: D_{-1} = -(W + T_Ny) / (Ny + 1)
+    Dm = N::mul(N::neg(N::add(W, T_all)), N::pair(a.mC, a.mCf[0], a.mCf[1]));
     Pm = W;
   }
   // phi_j = phi_{-1} + (j+1) D_{-1} + T_j,  E_j = -(2 D_{-1} + S_j + S_{j-1}) / 2
@@ -923,7 +935,7 @@ __device__ __forceinline__ void mean_mode_body(const PoissonArgs& a, unsigned ch
   for (int j = j0; j < j1; ++j) {
     const T Tj = (j > 0) ? v[j - 1] : N::from_f(0.0f);
     const T Sj = Sv[j], Sjm1 = (j > 0) ? Sv[j - 1] : N::from_f(0.0f);
-    const T phi = N::add(N::add(Pm, N::mul(N::from((double)(j + 1)), Dm)), Tj);
+    const T phi = N::add(N::add(Pm, N::mul(N::from_i(j + 1), Dm)), Tj);
     const T ey = N::mul(mhalf, N::add(N::add(Dm, Dm), N::add(Sj, Sjm1)));
     const T pc = N::mul(phi, inN), ec = N::mul(ey, inN);
     if constexpr (sizeof(R) == 8) {
@@ -981,7 +993,7 @@ __global__ void __launch_bounds__(kMeanThreads) k_batch_mean(BatchTables t, int 
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
     const BatchRunDesc& rd = t.runs[r];
     if (step >= rd.remaining) continue;
-    const PoissonArgs a = rd.pa;
+    const PoissonArgs& a = rd.pa;
     if (a.Ny <= kMeanSmallRows) {  // the same thread count as the run alone
       if (threadIdx.x < kMeanThreadsSmall) mean_mode_body<float, kMeanThreadsSmall>(a, smem_raw, ms_small);
     } else {
