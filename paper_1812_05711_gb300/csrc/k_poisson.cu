@@ -481,18 +481,18 @@ __device__ __forceinline__ void modes_tile_sweeps(const PoissonArgs& a, int m0, 
   __syncthreads();
   chunk_carries<R, MB, NT, true>(ts);  // value just above each chunk, from the top down
   __syncthreads();
+  // backward evaluation, each solved value stored as it is formed (a warp's
+  // store covers 8 wavenumbers of 4 rows, 64 contiguous bytes each); the
+  // stores issue while the sweep's dependent chain waits
   x = s_carry[ch][mo];
+  const int m = m0 + mo;
+  const bool put = m >= 1 && m < Mh;
+  Cplx<R>* col = spec + m;
   for (int j = j1 - 1; j >= j0; --j) {
     const R r = rt[j * MB + mo];
     const Cplx<R> dj = d[j * MB + mo];
     x = {dj.re - r * x.re, dj.im - r * x.im};
-    d[j * MB + mo] = x;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < Ny * MB; idx += NT) {
-    const int j = idx / MB, mo2 = idx % MB;
-    const int m = m0 + mo2;
-    if (m >= 1 && m < Mh) spec[(long long)j * Mp + m] = d[idx];
+    if (put) col[(long long)j * Mp] = x;
   }
 }
 
