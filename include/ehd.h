@@ -191,10 +191,13 @@ ehd_status ehd_step_profile(ehd_run* run, long n, double* ms_out);
  * each is resident and waiting when its predecessor ends: 1 the forward row
  * transform, 2 the wavenumber solve, 4 the inverse transform, 8 the step
  * kernel (march form: it stages its first rows' populations before waiting
- * for phi); 7, the default up to 2^18 nodes, shortens steps of small grids;
- * 3, the default above (2048 x 1680: 118.0 us against 121.9 with none, 118.2
- * with 11, 119.8 with 15: the inverse transform's early-resident CTAs crowd
- * the wavenumber solve of large runs); results are the same for every mask),
+ * for phi); the default is 7 up to 2^18 nodes and from 2^21 (2048 x 1680:
+ * 114.1 us per step against 114.3 with 11, 114.7 with 3, 116.9 with none),
+ * 11 between them (1024 x 840: 41.2 against 41.7 with 7) and 11 for
+ * perturbation-form runs at every size (2048 x 1680: 120.2 against 121.1
+ * with 3 and 135.4 with 7, whose early-resident inverse-transform CTAs
+ * starve the base chain on the third stream); results are the same for
+ * every mask),
  * EHD_TUNE_FFT_CTA (FP32 rows
  * of 2048: 1, the default, one CTA of 64 threads per row; 0, one warp per
  * row), EHD_TUNE_Y_SOLVER (the y solve of the wavenumbers m >= 1: 0, the

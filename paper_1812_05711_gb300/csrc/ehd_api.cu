@@ -745,13 +745,19 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     r->bmom = static_cast<double*>(run_alloc(r, 5 * (size_t)Ny * sizeof(double)));
   }
   r->step_kernel = (o.step_kernel >= 0) ? o.step_kernel : (r->real_f64 && !o.ex_spectral) ? 1 : 0;
-  // programmatic dependent launch of the Poisson kernels: all three for
-  // grids of up to 2^18 nodes, whose steps are launch-latency bound (256 x
-  // 208: 17.4 vs 18.0 us); above, the forward transform and the wavenumber
-  // solve only (2048 x 1680: 118.0 us against 121.9 without, 119.8 with the
-  // inverse transform and the step kernel too: the inverse transform's
-  // early-resident CTAs crowd the solve)
-  r->pdl = ((long long)Nx * Ny <= (1LL << 18)) ? 7 : 3;
+  // programmatic dependent launch (mask of EHD_TUNE_PDL), as measured per
+  // step: all three Poisson kernels (7) for up to 2^18 nodes (512 x 416:
+  // 20.1 us against 20.7 with 3) and from 2^21 (2048 x 1680: 114.1 against
+  // 114.3 with 11, 114.7 with 3, 116.9 with none); between them the forward
+  // transform, the wavenumber solve and the step kernel (11; 1024 x 840: 41.2
+  // against 41.7 with 7, 42.4 with 3).  Perturbation-form runs take 11 at
+  // every size (512 x 416: 28.9 against 29.5 with 7; 2048 x 1680: 120.2
+  // against 121.1 with 3 and 135.4 with 7, whose early-resident inverse
+  // transform CTAs starve the base chain on the third stream)
+  {
+    const long long nodes = (long long)Nx * Ny;
+    r->pdl = (r->pert || (nodes > (1LL << 18) && nodes < (1LL << 21))) ? 11 : 7;
+  }
   r->cols_per_lane = 2;
   r->nstrips = march_strips(Nx, r->cols_per_lane);
   r->nxb = (r->step_kernel == 0) ? r->nstrips : step_flux_blocks(Nx);

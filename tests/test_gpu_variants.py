@@ -93,8 +93,8 @@ def test_launch_shape_knobs_keep_results():
     amp, ph = wl.roll(23, 1e-2)
     w = wl.Workload("knobs-2048x40", 2048, 40, 190.0, amp=amp, phase=ph)
 
-    def run_with(**tune):
-        r = ehd.Run(*w.args(), storage="f32", amp=w.amp, phase=w.phase)
+    def run_with(pert=0, **tune):
+        r = ehd.Run(*w.args(), storage="f32", amp=w.amp, phase=w.phase, perturbation=pert)
         for k, v in tune.items():
             ehd.ehd_tune(r.handle, k, v)
         r.step(40)
@@ -103,10 +103,16 @@ def test_launch_shape_knobs_keep_results():
         return F
 
     base = run_with()
-    for mask in (1, 2, 4, 7, 8, 15):
+    for mask in (0, 1, 2, 3, 4, 7, 8, 11, 15):
         pdl = run_with(pdl=mask)
         for k in base:
             assert np.array_equal(base[k], pdl[k]), (mask, k)
+    # the perturbation form (default mask 11; its base chain on a third stream)
+    pbase = run_with(pert=1)
+    for mask in (0, 3, 7, 15):
+        pdl = run_with(pert=1, pdl=mask)
+        for k in pbase:
+            assert np.array_equal(pbase[k], pdl[k]), ("perturbation", mask, k)
     p = o.setup(*w.args())
     for tune in (dict(fft_cta=0), dict(tile_modes=4), dict(tile_modes=1), dict(step_kernel=1)):
         e = _scaled_err(p, run_with(**tune), base)
