@@ -803,10 +803,10 @@ ehd_status ehd_create(int Nx, int Ny, double T, double C, double M, double Fe, d
     // the rows a step wrote last are read first by the next (see
     // march_shift); only where the one extra slab per strip keeps one wave
     int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, r->device);
+    const bool l2_known = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, r->device) == cudaSuccess && l2 > 0;
     const long long slabs = (Ny + r->slab_rows - 1) / r->slab_rows + 1;
     const long long pop_bytes = 36 * (long long)Ny * r->P * (long long)storage_bytes(r->storage);
-    if (pop_bytes > (long long)l2 && (long long)r->nstrips * slabs <= resident) r->slab_shift = kSlabShift;
+    if (l2_known && pop_bytes > (long long)l2 && (long long)r->nstrips * slabs <= resident) r->slab_shift = kSlabShift;
   }
   // rows per CTA of the node-parallel kernel: keep >= ~4 CTAs per SM
   {
